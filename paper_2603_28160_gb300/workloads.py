@@ -1,0 +1,252 @@
+"""Seeded synthetic workloads: tool and process parameter sets.
+
+This module only produces inputs -- tool geometry, cutting conditions, the
+tool path (pass start points and step counts) and the sampling grid. It holds
+none of the surface-generation arithmetic, so both the CUDA library and the
+CPU oracle consume its output without sharing any computation.
+
+The named workloads follow the configurations the surface generator is
+measured on:
+
+* ``slot_flat_d6``      flat end mill D=6, 2 flutes, one straight slot,
+                        1x1 mm at 5 um (200x200 cells)
+* ``raster_ball_d10``   ball end mill D=10, 4 flutes, runout 5 um, lead 15,
+                        12 raster passes, 5x5 mm at 1 um (5000x5000 cells)
+* ``floor_flat_d12``    flat end mill D=12, 3 flutes with 35/38/41 deg helix,
+                        runout 8 um, 20x20 mm at 2 um (10000x10000 cells)
+* ``lhs_batch``         Latin-hypercube batch of uneven patches
+* ``poisson_stream``    request stream drawn from the batch distribution
+
+Every patch origin is shifted from the pass centre-line by a generic
+sub-cell amount (``CELL_OFFSET``) so that no systematic family of edge points
+(the tool axis, a tooth crossing the centre-line) lies exactly on a sampling
+boundary, where the paper's closed boundary intervals leave the cell ambiguous.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+MAX_TEETH = 16
+# generic sub-cell offsets of the patch origin relative to the pass centre-line
+CELL_OFFSET = (0.318309886183791, 0.367879441171442)
+
+
+@dataclass
+class ToolSpec:
+    kind: str                     # "flat" or "ball"
+    diameter: float               # mm
+    n_teeth: int
+    helix_deg: List[float]        # one per tooth
+    tooth_deg: Optional[List[float]] = None  # angular positions; None = even pitch
+    runout_mm: float = 0.0        # spindle-axis offset, rotates with the tool
+    runout_phase_deg: float = 0.0
+    n_edge: int = 50              # flank (flat) / meridian (ball) points
+    n_end: int = 0                # flat bottom-edge points (0 or >= 2)
+
+    def teeth_angles(self) -> List[float]:
+        if self.tooth_deg is not None:
+            return list(self.tooth_deg)
+        return [360.0 * k / self.n_teeth for k in range(self.n_teeth)]
+
+    def helix(self) -> List[float]:
+        h = list(self.helix_deg)
+        if len(h) == 1:
+            h = h * self.n_teeth
+        return h
+
+
+@dataclass
+class ProcessSpec:
+    fz: float                     # feed per tooth, mm
+    rpm: float
+    rot_step_deg: float           # spindle angle per time step
+    ap: float                     # axial depth of cut, mm
+    pass_x0: float                # tool reference x at the first step of each pass
+    pass_y0: float                # y of pass 0
+    steps_per_pass: int
+    x0: float                     # grid origin (corner of cell 0,0)
+    y0: float
+    pitch: float                  # sampling interval
+    nx: int
+    ny: int
+    n_passes: int = 1
+    ae: float = 0.0               # step-over, +Y
+    phase0_deg: float = 0.0
+    rot_sense: int = 1
+    lead_deg: float = 0.0
+    tilt_deg: float = 0.0
+    stock_z: float = 0.0
+    precision: str = "fp64"       # "fp64" or "fp32"
+
+    def replace(self, **kw) -> "ProcessSpec":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def trajectory_steps(self) -> int:
+        return self.n_passes * self.steps_per_pass
+
+
+@dataclass
+class Workload:
+    name: str
+    tool: ToolSpec
+    process: ProcessSpec
+    note: str = ""
+
+    @property
+    def trajectory_points(self) -> int:
+        """Every (time step, tooth, edge point) triple of the tool path."""
+        per_tooth = self.tool.n_edge + (self.tool.n_end if self.tool.kind == "flat" else 0)
+        return self.process.trajectory_steps * self.tool.n_teeth * per_tooth
+
+
+def plan_passes(tool: ToolSpec, fz: float, rot_step_deg: float, width: float,
+                centre_x: float, first_y: float, ap: float, pitch: float):
+    """Tool path: straight passes along +X, centred on the patch, long enough
+    that the whole tool (radius D/2 plus runout plus depth) clears the patch at
+    both ends. Returns (pass_x0, pass_y0, steps_per_pass)."""
+    steps_per_rev = int(round(360.0 / rot_step_deg))
+    feed_per_step = tool.n_teeth * fz / steps_per_rev
+    overtravel = 0.5 * tool.diameter + tool.runout_mm + ap + 2.0 * pitch
+    half_steps = int(math.ceil((0.5 * width + overtravel) / feed_per_step))
+    pass_x0 = centre_x - half_steps * feed_per_step
+    return pass_x0, first_y, 2 * half_steps + 1
+
+
+def _patch(width_x: float, width_y: float, pitch: float, centre=(0.0, 0.0)):
+    nx = int(round(width_x / pitch))
+    ny = int(round(width_y / pitch))
+    x0 = centre[0] - 0.5 * nx * pitch + CELL_OFFSET[0] * pitch
+    y0 = centre[1] - 0.5 * ny * pitch + CELL_OFFSET[1] * pitch
+    return x0, y0, nx, ny
+
+
+def slot_flat_d6(precision: str = "fp64") -> Workload:
+    """Flat end mill D=6 mm, 2 flutes, helix 30 deg, no runout, one straight
+    slot at fz=0.1 mm/tooth, 1000 rpm, ap=1 mm in 50 axial points, 0.5 deg
+    per step; 1x1 mm patch at 5 um, stock z=0."""
+    pitch = 0.005
+    tool = ToolSpec("flat", 6.0, 2, [30.0], n_edge=50,
+                    n_end=int(math.ceil(3.0 / (pitch / 2))))
+    x0, y0, nx, ny = _patch(1.0, 1.0, pitch)
+    px, py, spp = plan_passes(tool, 0.1, 0.5, nx * pitch, 0.0, 0.0, 1.0, pitch)
+    proc = ProcessSpec(fz=0.1, rpm=1000, rot_step_deg=0.5, ap=1.0, pass_x0=px, pass_y0=py,
+                       steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx, ny=ny,
+                       precision=precision)
+    return Workload("slot_flat_d6", tool, proc)
+
+
+def raster_ball_d10(precision: str = "fp32", width: float = 5.0, pitch: float = 0.001,
+                    n_passes: int = 12, n_edge: int = 200, rot_step_deg: float = 0.1) -> Workload:
+    """Ball end mill D=10, 4 flutes, helix 30 deg, radial runout 5 um at 30 deg,
+    lead 15 / tilt 0; 12 parallel passes, fz=0.08, ae=0.3, 6000 rpm, ap=0.2
+    (not stated by the configuration; chosen), 200 points along the edge,
+    0.1 deg per step; 5x5 mm at 1 um. Keyword arguments shrink it for tests."""
+    tool = ToolSpec("ball", 10.0, 4, [30.0], runout_mm=0.005, runout_phase_deg=30.0,
+                    n_edge=n_edge)
+    x0, y0, nx, ny = _patch(width, width, pitch)
+    ae = 0.3
+    first_y = -0.5 * (n_passes - 1) * ae
+    px, py, spp = plan_passes(tool, 0.08, rot_step_deg, nx * pitch, 0.0, first_y, 0.2, pitch)
+    proc = ProcessSpec(fz=0.08, rpm=6000, rot_step_deg=rot_step_deg, ap=0.2, pass_x0=px,
+                       pass_y0=py, steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx,
+                       ny=ny, n_passes=n_passes, ae=ae, lead_deg=15.0, precision=precision)
+    return Workload("raster_ball_d10", tool, proc)
+
+
+def floor_flat_d12(seed: int = 2603, precision: str = "fp32", width: float = 20.0,
+                   pitch: float = 0.002, rot_step_deg: float = 0.05) -> Workload:
+    """Flat end mill D=12, 3 flutes with unequal helix 35/38/41 deg, runout
+    8 um; floor finishing over 20x20 mm at 2 um, fz ~ U[0.04, 0.15] from the
+    seed, 300 axial points, 0.05 deg per step. ap=0.5 and ae=0.4 D with passes
+    covering the patch are chosen (not stated by the configuration)."""
+    rng = np.random.default_rng(seed)
+    fz = float(rng.uniform(0.04, 0.15))
+    D = 12.0
+    tool = ToolSpec("flat", D, 3, [35.0, 38.0, 41.0], runout_mm=0.008, runout_phase_deg=0.0,
+                    n_edge=300, n_end=int(math.ceil((D / 2) / (pitch / 2))))
+    x0, y0, nx, ny = _patch(width, width, pitch)
+    ae = 0.4 * D
+    n_passes = int(math.ceil((width + D) / ae))
+    first_y = -0.5 * (n_passes - 1) * ae
+    px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, first_y, 0.5, pitch)
+    proc = ProcessSpec(fz=fz, rpm=6000, rot_step_deg=rot_step_deg, ap=0.5, pass_x0=px,
+                       pass_y0=py, steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx,
+                       ny=ny, n_passes=n_passes, ae=ae, precision=precision)
+    return Workload("floor_flat_d12", tool, proc)
+
+
+def _lhs(rng: np.random.Generator, n: int, dims: int) -> np.ndarray:
+    """Latin hypercube sample in [0,1)^dims: one point per stratum per axis."""
+    u = rng.random((n, dims))
+    out = np.empty((n, dims))
+    for d in range(dims):
+        out[:, d] = (rng.permutation(n) + u[:, d]) / n
+    return out
+
+
+def lhs_batch(n: int = 4096, seed: int = 4096, precision: str = "fp32",
+              rot_step_deg: float = 0.1, n_edge: int = 200,
+              side_range=(0.5, 4.0), pitch_range_um=(1.0, 5.0)) -> List[Workload]:
+    """Seeded Latin-hypercube batch: ball or flat end, D in [4,16] mm, 2-6
+    flutes, helix [20,45] deg, runout [0,15] um with phase [0,360), lead and
+    tilt [0,20] deg, fz [0.03,0.2] mm, ae [0.1,1.0] mm; square patches 0.5-4 mm
+    at 1-5 um pitch; 0.1 deg per step and 200 edge points (chosen). Depth of
+    cut ap = 0.2 mm (chosen); passes cover the patch."""
+    rng = np.random.default_rng(seed)
+    X = _lhs(rng, n, 12)
+    out = []
+    for i in range(n):
+        x = X[i]
+        kind = "ball" if x[0] < 0.5 else "flat"
+        D = 4.0 + 12.0 * x[1]
+        N = 2 + int(x[2] * 5)
+        helix = 20.0 + 25.0 * x[3]
+        runout = 0.015 * x[4]
+        rphase = 360.0 * x[5]
+        lead = 20.0 * x[6]
+        tilt = 20.0 * x[7]
+        fz = 0.03 + 0.17 * x[8]
+        ae = 0.1 + 0.9 * x[9]
+        side = side_range[0] + (side_range[1] - side_range[0]) * x[10]
+        pitch = 1e-3 * (pitch_range_um[0] + (pitch_range_um[1] - pitch_range_um[0]) * x[11])
+        ap = 0.2
+        n_end = int(math.ceil((D / 2) / (pitch / 2))) if kind == "flat" else 0
+        tool = ToolSpec(kind, D, N, [helix], runout_mm=runout, runout_phase_deg=rphase,
+                        n_edge=n_edge, n_end=n_end)
+        x0, y0, nx, ny = _patch(side, side, pitch)
+        n_passes = int(math.ceil(side / ae)) + 1
+        first_y = -0.5 * (n_passes - 1) * ae
+        px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, first_y, ap, pitch)
+        proc = ProcessSpec(fz=fz, rpm=6000, rot_step_deg=rot_step_deg, ap=ap, pass_x0=px,
+                           pass_y0=py, steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch,
+                           nx=nx, ny=ny, n_passes=n_passes, ae=ae, lead_deg=lead,
+                           tilt_deg=tilt, precision=precision)
+        out.append(Workload("lhs_%d" % i, tool, proc))
+    return out
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int = 5) -> np.ndarray:
+    """Seeded Poisson process: arrival times (s) of n requests."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+
+
+def mixed_precision(workloads: List[Workload], fp64_fraction: float = 0.3,
+                    seed: int = 6) -> List[Workload]:
+    """Mark a seeded fraction of the requests as FP64, the rest FP32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for w in workloads:
+        prec = "fp64" if rng.random() < fp64_fraction else "fp32"
+        out.append(Workload(w.name, w.tool, w.process.replace(precision=prec), w.note))
+    return out
