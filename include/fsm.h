@@ -1,0 +1,278 @@
+/*
+ * fsm.h -- C ABI of the GB300 forward-solution-method (FSM) surface generator.
+ *
+ * The library predicts the 3D topography left by a milling tool (Section 2 of
+ * "An efficient open-source framework for high-fidelity 3D surface topography
+ * and roughness prediction in milling", arXiv 2603.28160) and reduces it to
+ * roughness indicators (Section 4.1.2). Every step of the computation runs in
+ * CUDA kernels for sm_103a; the host only validates descriptors and launches.
+ *
+ * Conventions shared by all entry points
+ *   - Lengths in mm, angles in degrees.
+ *   - Height maps are row-major H[ny][nx]: row k is along +Y_W (step-over),
+ *     column i along +X_W (feed). Cell (i,k) covers
+ *     [x0 + i*pitch, x0 + (i+1)*pitch) x [y0 + k*pitch, y0 + (k+1)*pitch)
+ *     (the sampling boundaries of Eq. eq_sampling_boundaries, read as
+ *     half-open so that every point belongs to exactly one cell).
+ *   - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *     data_ptr()); `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream). All enqueueing calls are asynchronous on that stream.
+ *   - Every function returns an fsm_status; no C++ exception crosses the ABI.
+ *     After an error, fsm_last_error(ctx) returns a message for the calling
+ *     thread's most recent failure on that context.
+ *   - Handles are opaque and owned by the library; descriptors are copied at
+ *     creation, so the caller may free them afterwards.
+ */
+#ifndef FSM_H
+#define FSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSM_MAX_TEETH 16
+#define FSM_MAX_PROFILES 16
+
+typedef enum {
+    FSM_OK = 0,
+    FSM_PENDING = 1,          /* fsm_poll: the request has not finished */
+    FSM_E_INVALID = -1,       /* a descriptor or argument failed validation */
+    FSM_E_NOMEM = -2,         /* device memory or the admission budget ran out */
+    FSM_E_CUDA = -3,          /* a CUDA runtime call failed */
+    FSM_E_TIMEOUT = -4,       /* fsm_poll waited timeout_ms without completion */
+    FSM_E_CANCELLED = -5,     /* the request was cancelled */
+    FSM_E_STATE = -6          /* wrong call order (e.g. unknown ticket) */
+} fsm_status;
+
+enum { FSM_TOOL_FLAT = 0, FSM_TOOL_BALL = 1 };
+enum { FSM_FP64 = 0, FSM_FP32 = 1 };
+
+typedef struct fsm_ctx fsm_ctx;
+typedef struct fsm_tool fsm_tool;
+typedef struct fsm_process fsm_process;
+
+/* Cutting tool (Section 2.1, Eq. eq_point_p_equation and
+ * eq_cutting_edge_to_tool, generalised from round inserts to end mills).
+ *   kind      FSM_TOOL_FLAT: bottom edge (h = 0, r in [0, D/2], n_end points)
+ *             plus flank (r = D/2, h in [0, ap], n_edge points).
+ *             FSM_TOOL_BALL: n_edge points uniform in polar angle on the
+ *             sphere of radius D/2, over the cap that can reach the depth of
+ *             cut for the process's lead/tilt.
+ *   helix_deg per tooth; the edge at height h lags the tooth position by
+ *             h tan(helix) / (D/2) radians against the rotation.
+ *   tooth_deg angular position of each tooth (tooth K sits -tooth_deg[K]
+ *             from the spindle reference, the sign of Eq. eq_tool_to_spindle).
+ *   runout    spindle-axis offset of radius runout_mm at runout_phase_deg in
+ *             the rotating frame.
+ * Validation: 1 <= n_teeth <= 16, n_edge >= 2, n_end == 0 or >= 2 (flat),
+ * n_end == 0 (ball), D > 0, runout >= 0, all values finite. */
+typedef struct {
+    int32_t kind;
+    int32_t n_teeth;
+    int32_t n_edge;
+    int32_t n_end;
+    double diameter;
+    double helix_deg[FSM_MAX_TEETH];
+    double tooth_deg[FSM_MAX_TEETH];
+    double runout_mm;
+    double runout_phase_deg;
+} fsm_tool_desc;
+
+/* Cutting conditions, tool path and sampling grid (Sections 2.1-2.2).
+ *   Time is discretised by the spindle angle: step s has phase index
+ *   m = s mod S (S = 360/rot_step_deg, an integer) and spindle angle
+ *   phase0_deg + rot_sense * m * rot_step_deg. The feed per step is
+ *   n_teeth * fz / S along +X_W (Eq. eq_spindle_to_workpiece).
+ *   Pass p (0 <= p < n_passes) covers global steps
+ *   [p*steps_per_pass, (p+1)*steps_per_pass); its tool reference point starts
+ *   at (pass_x0, pass_y0 + p*ae) and the spindle keeps turning between
+ *   passes. The tool reference height is chosen so the lowest position any
+ *   edge point reaches in a revolution is stock_z - ap.
+ *   lead_deg leans the tool axis toward +X_W, tilt_deg toward +Y_W.
+ *   precision FSM_FP64 (double heights, all arithmetic FP64) or FSM_FP32
+ *   (float heights; edge poses in FP32 tile-local coordinates, FP64 for the
+ *   spindle phase, the path position and near-boundary re-binning).
+ * Validation: fz, ap, pitch > 0; 360/rot_step_deg integral; rot_sense = +-1;
+ * n_passes >= 1; steps_per_pass >= 1; n_passes*steps_per_pass < 2^31;
+ * 1 <= nx, ny <= 65535*256; finite values. rpm only labels time. */
+typedef struct {
+    double fz;
+    double rpm;
+    double rot_step_deg;
+    double phase0_deg;
+    int32_t rot_sense;
+    int32_t n_passes;
+    double ap;
+    double lead_deg;
+    double tilt_deg;
+    double ae;
+    double pass_x0;
+    double pass_y0;
+    int64_t steps_per_pass;
+    double stock_z;
+    double x0;
+    double y0;
+    double pitch;
+    int32_t nx;
+    int32_t ny;
+    int32_t precision;
+    int32_t reserved;
+} fsm_process_desc;
+
+/* Optional launch overrides and counters for fsm_predict_surface.
+ *   tile_x, tile_y    shared-memory tile in cells (0 = library default)
+ *   block_threads     threads per CTA (0 = default)
+ *   d_counters        NULL, or device int64_t[4] the sweep ADDS to:
+ *                     [0] edge-point poses evaluated,
+ *                     [1] cutting evaluations: inside the patch and below the
+ *                         stock surface (the points the per-cell minimum runs
+ *                         over),
+ *                     [2] cutting points re-binned in FP64 (FP32 path),
+ *                     [3] shared-memory atomic updates issued. */
+typedef struct {
+    int32_t tile_x;
+    int32_t tile_y;
+    int32_t block_threads;
+    int32_t ctas_per_sm;
+    int64_t* d_counters;
+} fsm_predict_opts;
+
+/* Areal (ISO 25178-2) and line (ISO 4287) roughness of one height map,
+ * Section 4.1.2. Mean plane = arithmetic mean; no form removal, no S/L
+ * filter. Ssk = Sku = NaN when Sq == 0. Profiles: n_rows rows at
+ * k_r = floor((2r+1) ny / (2 n_rows)) (along the feed) and n_cols columns at
+ * i_c = floor((2c+1) nx / (2 n_cols)) (across the feed). Ra = mean |z - mean|
+ * of the profile; Rz = mean over 5 consecutive segments
+ * [floor(q L/5), floor((q+1) L/5)) of (max - min), NaN when L < 5. */
+typedef struct {
+    double n, mean, zmin, zmax;
+    double Sa, Sq, Sp, Sv, Sz, Ssk, Sku;
+    int32_t n_rows, n_cols;
+    int32_t row_index[FSM_MAX_PROFILES], col_index[FSM_MAX_PROFILES];
+    double Ra_row[FSM_MAX_PROFILES], Rz_row[FSM_MAX_PROFILES];
+    double Ra_col[FSM_MAX_PROFILES], Rz_col[FSM_MAX_PROFILES];
+} fsm_roughness_out;
+
+/* ---------------------------------------------------------------------- */
+/* Context and handles                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `device`. Fails with FSM_E_CUDA if
+ * the device cannot be used (no GPU, or the library was not built for it). */
+fsm_status fsm_create_context(int device, fsm_ctx** out);
+fsm_status fsm_destroy_context(fsm_ctx* ctx);
+
+/* Message for the calling thread's last failure on ctx (never NULL; ctx may
+ * be NULL for failures of fsm_create_context). Valid until the next call. */
+const char* fsm_last_error(fsm_ctx* ctx);
+
+/* Validate and copy a tool description (Section 3.2 "tool geometry module":
+ * the geometry is fixed at construction). */
+fsm_status fsm_create_tool(fsm_ctx* ctx, const fsm_tool_desc* desc, fsm_tool** out);
+fsm_status fsm_destroy_tool(fsm_ctx* ctx, fsm_tool* tool);
+
+/* Validate and copy cutting conditions, tool path and grid. */
+fsm_status fsm_set_process(fsm_ctx* ctx, const fsm_process_desc* desc, fsm_process** out);
+fsm_status fsm_destroy_process(fsm_ctx* ctx, fsm_process* proc);
+
+/* ---------------------------------------------------------------------- */
+/* Single surface                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Predict one height map: build the edge, phase and path tables on the
+ * device (Section 2.2), sweep every edge point of every time step into a
+ * shared-memory tile of the grid keeping the per-cell minimum height
+ * (Section 2.3, Eq. eq_sampling_boundaries), and store the tiles.
+ *   d_heights  caller-owned device buffer of ny*nx doubles (FSM_FP64) or
+ *              floats (FSM_FP32), 16-byte aligned for vector stores (any
+ *              alignment works, slower). Every cell is written; cells no edge
+ *              point reaches keep stock_z.
+ *   opts       NULL for defaults.
+ * Scratch: stream-ordered device allocations (cudaMallocAsync) freed on the
+ * same stream. Asynchronous; errors of the enqueue are returned, kernel
+ * faults surface at the next synchronisation. */
+fsm_status fsm_predict_surface(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc,
+                               void* d_heights, const fsm_predict_opts* opts, void* stream);
+
+/* Roughness of a device height map (FSM_FP64 doubles or FSM_FP32 floats),
+ * computed on the device in FP64 with a fixed reduction order (results do not
+ * depend on launch timing). Writes one fsm_roughness_out to DEVICE memory
+ * d_out (caller-owned). 0 <= n_rows, n_cols <= 16. Asynchronous. */
+fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx,
+                         int32_t ny, int32_t n_rows, int32_t n_cols, fsm_roughness_out* d_out,
+                         void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched prediction                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Predict n surfaces of mixed tools, grids and precisions in one persistent
+ * launch (plus one planning launch and, if d_rough != NULL, the roughness
+ * launches). tools[i], procs[i] describe surface i; d_heights[i] is a HOST
+ * array of n device pointers (each sized as in fsm_predict_surface);
+ * d_rough NULL or a device array of n fsm_roughness_out (10 row and 10 column
+ * profiles each). Work is distributed over (surface, tile) items by a device
+ * queue. Asynchronous; stream-ordered scratch. */
+fsm_status fsm_predict_batch(fsm_ctx* ctx, int32_t n, const fsm_tool* const* tools,
+                             const fsm_process* const* procs, void* const* d_heights,
+                             fsm_roughness_out* d_rough, const fsm_predict_opts* opts,
+                             void* stream);
+
+/* A prepared batch for repeated launches and CUDA-graph capture: the
+ * descriptors, table space and scratch of n surfaces are laid out once in a
+ * device buffer owned by the batch (synchronous upload at creation).
+ * fsm_batch_run then enqueues only a memset and kernel launches (planning,
+ * the persistent sweep per precision, roughness), so a stream capture of it
+ * replays as a CUDA graph. Runs of one batch must not overlap in time (they
+ * share its scratch). Arguments as for fsm_predict_batch. */
+typedef struct fsm_batch fsm_batch;
+fsm_status fsm_batch_create(fsm_ctx* ctx, int32_t n, const fsm_tool* const* tools,
+                            const fsm_process* const* procs, void* const* d_heights,
+                            fsm_roughness_out* d_rough, const fsm_predict_opts* opts,
+                            fsm_batch** out);
+fsm_status fsm_batch_run(fsm_ctx* ctx, fsm_batch* batch, void* stream);
+fsm_status fsm_batch_destroy(fsm_ctx* ctx, fsm_batch* batch);
+
+/* ---------------------------------------------------------------------- */
+/* Served requests (continuous batching)                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Start a request server on ctx. Requests are admitted while the device
+ * memory they need (height map + tables + scratch) fits in budget_bytes;
+ * admitted requests are batched into launches on n_streams streams as they
+ * arrive, so work of several batches overlaps on the device. One server per
+ * context. */
+fsm_status fsm_server_start(fsm_ctx* ctx, size_t budget_bytes, int32_t n_streams,
+                            int32_t max_batch);
+fsm_status fsm_server_stop(fsm_ctx* ctx);
+
+/* Queue one prediction (+ roughness). The tool and process are copied.
+ * *ticket identifies the request for fsm_poll. Requests larger than the
+ * budget fail with FSM_E_NOMEM. */
+fsm_status fsm_submit(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc,
+                      uint64_t* ticket);
+
+/* Result of a served request. heights is a library-owned device buffer valid
+ * until fsm_release_result; rough is a host copy. Latencies in seconds from
+ * submission. */
+typedef struct {
+    void* d_heights;
+    int32_t precision, nx, ny, status;
+    fsm_roughness_out rough;
+    double queue_s, latency_s;
+} fsm_result;
+
+/* Wait up to timeout_ms (0 = just check, <0 = forever) for a request.
+ * Returns FSM_OK with *out filled, FSM_PENDING, or an error. */
+fsm_status fsm_poll(fsm_ctx* ctx, uint64_t ticket, int32_t timeout_ms, fsm_result* out);
+
+/* Return a finished request's device memory to the admission budget. */
+fsm_status fsm_release_result(fsm_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

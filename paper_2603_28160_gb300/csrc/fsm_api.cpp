@@ -1,0 +1,331 @@
+// fsm_api.cpp -- C ABI of the FSM surface generator: validation, plan
+// layout and launches. No arithmetic of the method runs here; the host only
+// copies descriptors into per-surface plans, sizes stream-ordered scratch and
+// enqueues kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fsm.h"
+#include "fsm_host.h"
+#include "fsm_internal.h"
+
+using fsm::Surface;
+
+namespace {
+thread_local std::string g_err;
+}  // namespace
+
+namespace fsm {
+
+fsm_status fail(fsm_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+fsm_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(FSM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool finite(double v) { return isfinite(v) != 0; }
+
+static int64_t steps_per_rev(double step_deg) {
+    if (!(step_deg > 0.0) || !finite(step_deg)) return -1;
+    const double r = 360.0 / step_deg;
+    const int64_t S = (int64_t)llround(r);
+    if (S < 1 || fabs(r - (double)S) > 1e-9 * (double)S || S > (1 << 22)) return -1;
+    return S;
+}
+
+static fsm_status check_tool(const fsm_tool_desc* t) {
+    if (!t) return fail(FSM_E_INVALID, "tool descriptor is NULL");
+    if (t->kind != FSM_TOOL_FLAT && t->kind != FSM_TOOL_BALL) return fail(FSM_E_INVALID, "unknown tool kind");
+    if (t->n_teeth < 1 || t->n_teeth > FSM_MAX_TEETH) return fail(FSM_E_INVALID, "n_teeth must be 1..16");
+    if (t->n_edge < 2) return fail(FSM_E_INVALID, "n_edge must be >= 2");
+    if (t->kind == FSM_TOOL_FLAT && (t->n_end < 0 || t->n_end == 1))
+        return fail(FSM_E_INVALID, "n_end must be 0 or >= 2");
+    if (t->kind == FSM_TOOL_BALL && t->n_end != 0) return fail(FSM_E_INVALID, "a ball end has n_end == 0");
+    if ((int64_t)t->n_teeth * (t->n_edge + t->n_end) > (1 << 22))
+        return fail(FSM_E_INVALID, "too many edge points");
+    if (!(t->diameter > 0.0) || !finite(t->diameter)) return fail(FSM_E_INVALID, "diameter must be > 0");
+    if (!(t->runout_mm >= 0.0) || !finite(t->runout_mm) || !finite(t->runout_phase_deg))
+        return fail(FSM_E_INVALID, "runout must be finite and >= 0");
+    for (int k = 0; k < t->n_teeth; ++k)
+        if (!finite(t->helix_deg[k]) || !finite(t->tooth_deg[k]) || fabs(t->helix_deg[k]) >= 89.0)
+            return fail(FSM_E_INVALID, "helix/tooth angles must be finite, |helix| < 89");
+    return FSM_OK;
+}
+
+static fsm_status check_process(const fsm_process_desc* p) {
+    if (!p) return fail(FSM_E_INVALID, "process descriptor is NULL");
+    const double vals[] = {p->fz, p->rpm, p->rot_step_deg, p->phase0_deg, p->ap, p->lead_deg, p->tilt_deg,
+                           p->ae, p->pass_x0, p->pass_y0, p->stock_z, p->x0, p->y0, p->pitch};
+    for (double v : vals)
+        if (!finite(v)) return fail(FSM_E_INVALID, "non-finite process value");
+    if (!(p->fz > 0.0)) return fail(FSM_E_INVALID, "fz must be > 0");
+    if (!(p->ap > 0.0)) return fail(FSM_E_INVALID, "ap must be > 0");
+    if (!(p->pitch > 0.0)) return fail(FSM_E_INVALID, "pitch must be > 0");
+    if (steps_per_rev(p->rot_step_deg) < 0) return fail(FSM_E_INVALID, "360/rot_step_deg must be an integer");
+    if (p->rot_sense != 1 && p->rot_sense != -1) return fail(FSM_E_INVALID, "rot_sense must be +1 or -1");
+    if (p->n_passes < 1) return fail(FSM_E_INVALID, "n_passes must be >= 1");
+    if (p->steps_per_pass < 1) return fail(FSM_E_INVALID, "steps_per_pass must be >= 1");
+    if ((double)p->n_passes * (double)p->steps_per_pass >= 2147483647.0)
+        return fail(FSM_E_INVALID, "n_passes * steps_per_pass must be < 2^31");
+    if (p->nx < 1 || p->ny < 1 || p->nx > 65535 * 256 || p->ny > 65535 * 256)
+        return fail(FSM_E_INVALID, "grid size out of range");
+    if ((double)p->nx * (double)p->ny > 4.0e9) return fail(FSM_E_INVALID, "grid larger than 4e9 cells");
+    if (fabs(p->lead_deg) >= 89.0 || fabs(p->tilt_deg) >= 89.0) return fail(FSM_E_INVALID, "|lead|, |tilt| < 89");
+    if (p->precision != FSM_FP64 && p->precision != FSM_FP32) return fail(FSM_E_INVALID, "unknown precision");
+    return FSM_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o) {
+    Shape s;
+    s.tile_x = 128;
+    s.tile_y = p.precision == FSM_FP64 ? 64 : 128;
+    s.threads = 256;
+    if (o) {
+        if (o->tile_x > 0) s.tile_x = o->tile_x;
+        if (o->tile_y > 0) s.tile_y = o->tile_y;
+        if (o->block_threads > 0) s.threads = o->block_threads;
+    }
+    return s;
+}
+
+// Copy the descriptors into a device plan; table pointers relative to base.
+size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh, Surface* s,
+                    char* base) {
+    memset(s, 0, sizeof *s);
+    s->kind = t.kind;
+    s->n_teeth = t.n_teeth;
+    s->n_edge = t.n_edge;
+    s->n_end = t.kind == FSM_TOOL_FLAT ? t.n_end : 0;
+    s->diameter = t.diameter;
+    s->runout_mm = t.runout_mm;
+    s->runout_phase_deg = t.runout_phase_deg;
+    for (int k = 0; k < FSM_MAX_TEETH; ++k) {
+        s->helix_deg[k] = t.helix_deg[k];
+        s->tooth_deg[k] = t.tooth_deg[k];
+    }
+    s->fz = p.fz;
+    s->rot_step_deg = p.rot_step_deg;
+    s->phase0_deg = p.phase0_deg;
+    s->rot_sense = p.rot_sense;
+    s->n_passes = p.n_passes;
+    s->ap = p.ap;
+    s->lead_deg = p.lead_deg;
+    s->tilt_deg = p.tilt_deg;
+    s->ae = p.ae;
+    s->pass_x0 = p.pass_x0;
+    s->pass_y0 = p.pass_y0;
+    s->steps_per_pass = (int32_t)p.steps_per_pass;
+    s->S = (int32_t)steps_per_rev(p.rot_step_deg);
+    s->stock_z = p.stock_z;
+    s->x0 = p.x0;
+    s->y0 = p.y0;
+    s->pitch = p.pitch;
+    s->nx = p.nx;
+    s->ny = p.ny;
+    s->precision = p.precision;
+    s->E = s->n_edge + s->n_end;
+    s->tile_x = sh.tile_x;
+    s->tile_y = sh.tile_y;
+    s->ntx = (p.nx + sh.tile_x - 1) / sh.tile_x;
+    s->nty = (p.ny + sh.tile_y - 1) / sh.tile_y;
+    const size_t NE = (size_t)s->n_teeth * (size_t)s->E;
+    const size_t G = (size_t)s->n_teeth * (size_t)((s->E + 31) / 32);
+    size_t off = 0;
+    s->tool32 = (float4*)(base + off);
+    off += align256(NE * 4 * sizeof(float4));
+    s->tool64 = (double*)(base + off);
+    off += align256(NE * 9 * sizeof(double));
+    s->ph32 = (float2*)(base + off);
+    off += align256((size_t)s->S * sizeof(float2));
+    s->ph64 = (double2*)(base + off);
+    off += align256((size_t)s->S * sizeof(double2));
+    s->groups = (float4*)(base + off);
+    off += align256(G * sizeof(float4));
+    return off;
+}
+
+size_t surface_overhead_bytes(const fsm_tool_desc& t, const fsm_process_desc& p) {
+    Surface s;
+    const Shape sh = pick_shape(p, nullptr);
+    return align256(sizeof(Surface)) + fill_surface(t, p, sh, &s, nullptr) + 64 * 1024;
+}
+
+}  // namespace fsm
+
+using namespace fsm;
+
+extern "C" {
+
+const char* fsm_last_error(fsm_ctx*) { return g_err.c_str(); }
+
+fsm_status fsm_create_context(int device, fsm_ctx** out) {
+    if (!out) return fail(FSM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(FSM_E_INVALID, "no such CUDA device");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor < 100)
+        return fail(FSM_E_CUDA, "the library is built for sm_103a (Blackwell Ultra)");
+    // make sure our kernels are loadable on this device
+    size_t smem = fsm::sweep_smem_bytes(FSM_FP32, 8, 8, 256);
+    if (fsm::sweep_blocks_per_sm(FSM_FP32, 256, smem) <= 0) {
+        cudaGetLastError();
+        return fail(FSM_E_CUDA, "kernel image not loadable on this device");
+    }
+    fsm_ctx* c = new fsm_ctx();
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = c;
+    return FSM_OK;
+}
+
+fsm_status fsm_destroy_context(fsm_ctx* ctx) {
+    if (!ctx) return fail(FSM_E_INVALID, "ctx is NULL");
+    if (ctx->server) fsm_server_stop(ctx);
+    delete ctx;
+    return FSM_OK;
+}
+
+fsm_status fsm_create_tool(fsm_ctx* ctx, const fsm_tool_desc* desc, fsm_tool** out) {
+    if (!ctx || !out) return fail(FSM_E_INVALID, "ctx/out is NULL");
+    fsm_status st = check_tool(desc);
+    if (st != FSM_OK) return st;
+    fsm_tool* t = new fsm_tool();
+    t->d = *desc;
+    *out = t;
+    return FSM_OK;
+}
+
+fsm_status fsm_destroy_tool(fsm_ctx*, fsm_tool* tool) {
+    delete tool;
+    return FSM_OK;
+}
+
+fsm_status fsm_set_process(fsm_ctx* ctx, const fsm_process_desc* desc, fsm_process** out) {
+    if (!ctx || !out) return fail(FSM_E_INVALID, "ctx/out is NULL");
+    fsm_status st = check_process(desc);
+    if (st != FSM_OK) return st;
+    fsm_process* p = new fsm_process();
+    p->d = *desc;
+    *out = p;
+    return FSM_OK;
+}
+
+fsm_status fsm_destroy_process(fsm_ctx*, fsm_process* proc) {
+    delete proc;
+    return FSM_OK;
+}
+
+}  // extern "C"
+
+namespace fsm {
+
+// Launch configuration of the sweep for one precision; checks shared memory.
+fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* smem, int* blocks_per_sm) {
+    if (sh.threads < 32 || sh.threads > 1024 || (sh.threads & 31))
+        return fail(FSM_E_INVALID, "block_threads must be a multiple of 32 in 32..1024");
+    if (sh.tile_x < 4 || sh.tile_y < 1 || (sh.tile_x & 3)) return fail(FSM_E_INVALID, "tile_x must be a multiple of 4");
+    *smem = sweep_smem_bytes(precision, sh.tile_x, sh.tile_y, sh.threads);
+    if (*smem + 1024 > ctx->smem_optin) return fail(FSM_E_INVALID, "tile does not fit in shared memory");
+    int b = sweep_blocks_per_sm(precision, sh.threads, *smem);
+    if (b <= 0) {
+        cudaGetLastError();
+        return fail(FSM_E_CUDA, "sweep kernel cannot be resident with this configuration");
+    }
+    *blocks_per_sm = b;
+    return FSM_OK;
+}
+
+fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
+                       const fsm_predict_opts* opts, cudaStream_t st) {
+    const Shape sh = pick_shape(p, opts);
+    size_t smem = 0;
+    int bps = 0;
+    fsm_status rc = sweep_config(ctx, p.precision, sh, &smem, &bps);
+    if (rc != FSM_OK) return rc;
+    Surface s;
+    const size_t surf_bytes = align256(sizeof(Surface));
+    size_t table_bytes = fill_surface(t, p, sh, &s, nullptr);
+    void* ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, surf_bytes + table_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (tables)");
+    fill_surface(t, p, sh, &s, (char*)ws + surf_bytes);
+    s.heights = d_heights;
+    Surface* d_s = (Surface*)ws;
+    if ((e = launch_plan(d_s, 1, &s, st)) != cudaSuccess) {
+        cudaFreeAsync(ws, st);
+        return cuda_fail(e, "plan kernel");
+    }
+    const int tiles = s.ntx * s.nty;
+    const int grid = std::min(tiles, ctx->sm_count * bps);
+    e = launch_sweep_shaped(p.precision, d_s, 1, nullptr, tiles, nullptr,
+                            opts ? (long long*)opts->d_counters : nullptr, grid, sh.threads, smem, st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return FSM_OK;
+}
+
+fsm_status roughness_one(fsm_ctx*, const void* d_h, int precision, int nx, int ny, int n_rows, int n_cols,
+                         fsm_roughness_out* d_out, cudaStream_t st) {
+    RoughJob jb;
+    jb.h = d_h;
+    jb.n = (size_t)nx * (size_t)ny;
+    jb.nx = nx;
+    jb.ny = ny;
+    jb.n_rows = n_rows;
+    jb.n_cols = n_cols;
+    jb.out = d_out;
+    char* ws = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&ws, roughness_one_ws_bytes(jb.n), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (roughness)");
+    e = launch_roughness_one(precision, jb, ws, st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "roughness kernels");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return FSM_OK;
+}
+
+}  // namespace fsm
+
+extern "C" {
+
+fsm_status fsm_predict_surface(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc, void* d_heights,
+                               const fsm_predict_opts* opts, void* stream) {
+    if (!ctx || !tool || !proc) return fail(FSM_E_INVALID, "ctx/tool/proc is NULL");
+    if (!d_heights) return fail(FSM_E_INVALID, "d_heights is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return fsm::predict_one(ctx, tool->d, proc->d, d_heights, opts, (cudaStream_t)stream);
+}
+
+fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx, int32_t ny,
+                         int32_t n_rows, int32_t n_cols, fsm_roughness_out* d_out, void* stream) {
+    if (!ctx || !d_heights || !d_out) return fail(FSM_E_INVALID, "ctx/d_heights/d_out is NULL");
+    if (precision != FSM_FP64 && precision != FSM_FP32) return fail(FSM_E_INVALID, "unknown precision");
+    if (nx < 1 || ny < 1) return fail(FSM_E_INVALID, "nx, ny must be >= 1");
+    if (n_rows < 0 || n_cols < 0 || n_rows > FSM_MAX_PROFILES || n_cols > FSM_MAX_PROFILES)
+        return fail(FSM_E_INVALID, "0 <= n_rows, n_cols <= 16");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return fsm::roughness_one(ctx, d_heights, precision, nx, ny, n_rows, n_cols, d_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// fsm_host.h -- host-side handles and helpers shared by the C ABI files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/fsm.h"
+#include "fsm_device.cuh"
+
+struct fsm_tool {
+    fsm_tool_desc d;
+};
+struct fsm_process {
+    fsm_process_desc d;
+};
+
+namespace fsm {
+struct Server;
+}
+
+struct fsm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    std::mutex mu;
+    fsm::Server* server = nullptr;
+};
+
+namespace fsm {
+
+// A pinned host staging buffer whose reuse waits for its last copy.
+struct PinnedSlot {
+    void* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    cudaError_t ensure(size_t bytes) {
+        cudaError_t e = cudaSuccess;
+        if (!done) {
+            if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) return e;
+        } else if ((e = cudaEventSynchronize(done)) != cudaSuccess) {
+            return e;
+        }
+        if (cap < bytes) {
+            if (host) cudaFreeHost(host);
+            host = nullptr;
+            cap = 0;
+            if ((e = cudaMallocHost(&host, bytes + bytes / 2)) != cudaSuccess) return e;
+            cap = bytes + bytes / 2;
+        }
+        return e;
+    }
+    void release() {
+        if (done) cudaEventSynchronize(done);
+        if (host) cudaFreeHost(host);
+        if (done) cudaEventDestroy(done);
+        host = nullptr;
+        done = nullptr;
+        cap = 0;
+    }
+};
+
+fsm_status fail(fsm_status st, const std::string& msg);
+fsm_status cuda_fail(cudaError_t e, const char* what);
+
+struct Shape {
+    int tile_x, tile_y, threads;
+};
+
+size_t align256(size_t v);
+Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o);
+// Fill a device plan from the descriptors. Table pointers are laid out from
+// `base`; returns the table bytes (call with base = NULL to size).
+size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh, Surface* s,
+                    char* base);
+fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* smem, int* blocks_per_sm);
+fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
+                       const fsm_predict_opts* opts, cudaStream_t st);
+fsm_status roughness_one(fsm_ctx* ctx, const void* d_h, int precision, int nx, int ny, int n_rows, int n_cols,
+                         fsm_roughness_out* d_out, cudaStream_t st);
+
+// Device bytes one surface needs beyond its height map (tables + scratch).
+size_t surface_overhead_bytes(const fsm_tool_desc& t, const fsm_process_desc& p);
+
+// One-shot batch on stream-ordered scratch; `slot` (optional) stages the
+// upload in pinned memory.
+fsm_status predict_batch_descs(fsm_ctx* ctx, int n, const fsm_tool_desc* const* td,
+                               const fsm_process_desc* const* pd, void* const* d_heights,
+                               fsm_roughness_out* d_rough, const fsm_predict_opts* opts, cudaStream_t st,
+                               PinnedSlot* slot);
+
+}  // namespace fsm

@@ -1,0 +1,40 @@
+// fsm_internal.h -- launchers shared by the C ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/fsm.h"
+#include "fsm_device.cuh"
+
+namespace fsm {
+
+// Build tables and derived values of n surfaces (one block each). If `one`
+// is not NULL it is copied into d_surfs[0] first (n must be 1).
+cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_t st);
+
+size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads);
+int sweep_blocks_per_sm(int precision, int threads, size_t smem);
+cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
+                                const int* d_tile_base, int total_tiles, int* d_queue,
+                                long long* d_counters, int grid, int threads, size_t smem,
+                                cudaStream_t st);
+
+// Roughness of a set of maps of one precision. Map j is cut into
+// ceil(n/kChunk) chunks; d_chunk_base[j] is its first chunk (n_jobs+1
+// entries). d_part: 7 * total_chunks doubles of scratch. max_profiles = the
+// largest n_rows + n_cols of any job.
+constexpr size_t kChunk = 32768;
+struct RoughJob {
+    const void* h;
+    size_t n;
+    int nx, ny, n_rows, n_cols;
+    fsm_roughness_out* out;
+};
+cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_jobs, const int* d_chunk_base,
+                                  int total_chunks, int max_profiles, double* d_part, cudaStream_t st);
+// One map; d_ws of roughness_one_ws_bytes(n) bytes (256-aligned).
+size_t roughness_one_ws_bytes(size_t n);
+cudaError_t launch_roughness_one(int precision, const RoughJob& jb, char* d_ws, cudaStream_t st);
+
+}  // namespace fsm

@@ -1,0 +1,869 @@
+// fsm_kernels.cu -- sm_103a kernels of the FSM surface generator.
+//
+//   plan_kernel      edge, phase and path tables of each surface in FP64
+//                    (Section 2.2 discretisation; Section 3.2 "tool geometry"
+//                    and "kinematics" modules precompute points and trig)
+//   sweep_kernel<T>  persistent tile sweep (Section 2.3 and the "surface
+//                    computation module" of Section 3.2): a tile of the height
+//                    map lives in shared memory, every edge point that can
+//                    land in the tile below the stock is evaluated, binned by
+//                    the sampling boundaries of Eq. eq_sampling_boundaries and
+//                    folded in with a shared-memory atomicMin on an
+//                    order-preserving integer encoding of its height
+//   moments / profiles  FP64 roughness reductions (Section 4.1.2)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string.h>
+
+#include <type_traits>
+
+#include "fsm_device.cuh"
+#include "fsm_internal.h"
+
+namespace fsm {
+
+// ===========================================================================
+// Planning
+// ===========================================================================
+__device__ __forceinline__ double deg2rad(double d) { return d * (3.14159265358979323846 / 180.0); }
+
+__global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surface one, int use_one) {
+    const int sidx = blockIdx.x;
+    if (sidx >= n) return;
+    Surface* sf = surfs + sidx;
+    if (use_one) {  // a single surface arrives by value (graph-capture friendly)
+        if (threadIdx.x == 0) *sf = one;
+        __syncthreads();
+    }
+    __shared__ double A[9];
+    __shared__ double kap[2];
+    __shared__ float red_lo[256], red_rx[256], red_ry[256];
+    const int tid = threadIdx.x;
+    const int N = sf->n_teeth, E = sf->E, S = sf->S;
+    const double R = 0.5 * sf->diameter;
+    const double sigma = (double)sf->rot_sense;
+    const double dth = deg2rad(sf->rot_step_deg);
+    if (tid == 0) {
+        double L = deg2rad(sf->lead_deg), T = deg2rad(sf->tilt_deg);
+        double cL = cos(L), sL = sin(L), cT = cos(T), sT = sin(T);
+        // A = Rx(-tilt) Ry(lead): the tool axis leans toward +X by lead, +Y by tilt
+        A[0] = cL;        A[1] = 0.0; A[2] = sL;
+        A[3] = -sT * sL;  A[4] = cT;  A[5] = sT * cL;
+        A[6] = -cT * sL;  A[7] = -sT; A[8] = cT * cL;
+        double tau = acos(fmin(1.0, A[8]));
+        double c = fmin(1.0, fmax(-1.0, (R - sf->ap) / R));
+        double half = acos(c);
+        kap[0] = fmax(0.0, tau - half);
+        kap[1] = fmin(0.5 * 3.14159265358979323846, tau + half);
+    }
+    __syncthreads();
+    const int NE = N * E;
+    float lo_min = 3.0e38f, rx = 0.f, ry = 0.f;
+    for (int idx = tid; idx < NE; idx += blockDim.x) {
+        const int K = idx / E, j = idx - K * E;
+        double r, h;
+        if (sf->kind == 0) {  // flat: bottom edge then flank
+            if (j < sf->n_end) {
+                r = R * ((double)j / (double)(sf->n_end - 1));
+                h = 0.0;
+            } else {
+                r = R;
+                h = sf->ap * ((double)(j - sf->n_end) / (double)(sf->n_edge - 1));
+            }
+        } else {              // ball: uniform in polar angle over the engaged cap
+            double kappa = kap[0] + (kap[1] - kap[0]) * ((double)j / (double)(E - 1));
+            r = R * sin(kappa);
+            h = R * (1.0 - cos(kappa));
+        }
+        double psi = h * tan(deg2rad(sf->helix_deg[K])) / R;   // helix lag
+        double alpha = -deg2rad(sf->tooth_deg[K]) - sigma * psi;
+        double lam = deg2rad(sf->runout_phase_deg);
+        double qx = r * cos(alpha) + sf->runout_mm * cos(lam);
+        double qy = r * sin(alpha) + sf->runout_mm * sin(lam);
+        double qz = h;
+        double u[3], v[3], w[3];
+        for (int d = 0; d < 3; ++d) {
+            u[d] = A[3 * d] * qx + A[3 * d + 1] * qy;
+            v[d] = A[3 * d + 1] * qx - A[3 * d] * qy;
+            w[d] = A[3 * d + 2] * qz;
+        }
+        double* t64 = sf->tool64;
+        t64[0 * NE + idx] = u[0]; t64[1 * NE + idx] = u[1]; t64[2 * NE + idx] = u[2];
+        t64[3 * NE + idx] = v[0]; t64[4 * NE + idx] = v[1]; t64[5 * NE + idx] = v[2];
+        t64[6 * NE + idx] = w[0]; t64[7 * NE + idx] = w[1]; t64[8 * NE + idx] = w[2];
+        float amp[3], mph[3];
+        for (int d = 0; d < 3; ++d) {
+            double a = sqrt(u[d] * u[d] + v[d] * v[d]);
+            double delta = atan2(v[d], u[d]);
+            // Theta_m - delta = sense*dth*(m - mph)
+            double m = sigma * (delta - deg2rad(sf->phase0_deg)) / dth;
+            m = fmod(m, (double)S);
+            if (m < 0.0) m += (double)S;
+            amp[d] = (float)a;
+            mph[d] = (float)m;
+        }
+        float4* t32 = sf->tool32 + 4 * (size_t)idx;
+        t32[0] = make_float4((float)u[0], (float)v[0], (float)w[0], (float)u[2]);
+        t32[1] = make_float4((float)u[1], (float)v[1], (float)w[1], (float)v[2]);
+        t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
+        t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
+        double zlow = w[2] - sqrt(u[2] * u[2] + v[2] * v[2]);
+        lo_min = fminf(lo_min, (float)zlow);
+        rx = fmaxf(rx, (float)(fabs(w[0]) + sqrt(u[0] * u[0] + v[0] * v[0])));
+        ry = fmaxf(ry, (float)(fabs(w[1]) + sqrt(u[1] * u[1] + v[1] * v[1])));
+    }
+    red_lo[tid] = lo_min;
+    red_rx[tid] = rx;
+    red_ry[tid] = ry;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            red_lo[tid] = fminf(red_lo[tid], red_lo[tid + o]);
+            red_rx[tid] = fmaxf(red_rx[tid], red_rx[tid + o]);
+            red_ry[tid] = fmaxf(red_ry[tid], red_ry[tid + o]);
+        }
+        __syncthreads();
+    }
+    // z_ref needs the exact FP64 lowest point: recompute it deterministically
+    __shared__ double zlo_exact;
+    if (tid == 0) {
+        double best = 1e300;
+        for (int idx = 0; idx < NE; ++idx) {
+            double uz = sf->tool64[2 * NE + idx], vz = sf->tool64[5 * NE + idx],
+                   wz = sf->tool64[8 * NE + idx];
+            double zl = wz - sqrt(uz * uz + vz * vz);
+            if (zl < best) best = zl;
+        }
+        zlo_exact = best;
+    }
+    // phase table
+    for (int m = tid; m < S; m += blockDim.x) {
+        double th = deg2rad(sf->phase0_deg + sigma * ((double)m * sf->rot_step_deg));
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        sf->ph64[m] = make_double2(cs, sn);
+        sf->ph32[m] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    // per 32-point group bounds for the warp-level quick reject
+    const int G = (E + 31) / 32;
+    for (int gi = tid; gi < N * G; gi += blockDim.x) {
+        const int K = gi / G, g = gi - K * G;
+        float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
+        for (int j = g * 32; j < min(E, g * 32 + 32); ++j) {
+            const float4* t4 = sf->tool32 + 4 * (size_t)(K * E + j);
+            float wy = t4[1].z, ay = t4[2].y, wz = t4[2].x, az = t4[2].w;
+            ymin = fminf(ymin, wy - ay);
+            ymax = fmaxf(ymax, wy + ay);
+            zmin = fminf(zmin, wz - az);
+        }
+        sf->groups[gi] = make_float4(ymin, ymax, zmin, 0.f);
+    }
+    if (tid == 0) {
+        const double zr = sf->stock_z - sf->ap - zlo_exact;
+        sf->z_ref = zr;
+        sf->fs = (double)N * sf->fz / (double)S;
+        sf->dtheta = dth;
+        sf->reach_x = red_rx[0];
+        sf->reach_y = red_ry[0];
+        sf->zrel_lo = (float)(zr + zlo_exact - sf->stock_z);
+        // FP32 tile-local error bound (mm): inputs, products and sums each
+        // round by <= 2^-24 relative; a factor 2 on top of the sum of terms.
+        const double u24 = 5.9604644775390625e-8;
+        double rho = fmax((double)red_rx[0], (double)red_ry[0]);
+        double tile = fmax((double)sf->tile_x, (double)sf->tile_y) * sf->pitch;
+        double span = tile + 2.0 * rho + 2.0 * (double)N * sf->fz;
+        double err = u24 * (7.0 * rho + 2.0 * (rho + tile + span) + 2.0 * span + tile);
+        sf->guard_cells = (float)(2.0 * err / sf->pitch + 4.0 * u24 * (double)(sf->tile_x + sf->tile_y));
+    }
+}
+
+// ===========================================================================
+// Tile sweep
+// ===========================================================================
+struct Counters {
+    long long evaluated, cutting, rebinned, atomics;
+};
+
+__device__ __forceinline__ void warp_flush(Counters& c, long long* out) {
+    if (out == nullptr) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        c.evaluated += __shfl_xor_sync(0xffffffffu, c.evaluated, o);
+        c.cutting += __shfl_xor_sync(0xffffffffu, c.cutting, o);
+        c.rebinned += __shfl_xor_sync(0xffffffffu, c.rebinned, o);
+        c.atomics += __shfl_xor_sync(0xffffffffu, c.atomics, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd((unsigned long long*)out + 0, (unsigned long long)c.evaluated);
+        atomicAdd((unsigned long long*)out + 1, (unsigned long long)c.cutting);
+        atomicAdd((unsigned long long*)out + 2, (unsigned long long)c.rebinned);
+        atomicAdd((unsigned long long*)out + 3, (unsigned long long)c.atomics);
+    }
+}
+
+// One warp's scratch: runs of 32 edge points.
+struct WarpRuns {
+    Run run[32][kMaxArcs];
+    int32_t n[32];
+};
+
+template <typename Cell>
+struct TileCtx {
+    Cell* cells;          // [tile_y][tile_x] encodings
+    int tx, ty;           // tile index
+    int txc, tyc;         // valid cells in this tile
+    double X0, Y0;        // tile origin (world)
+};
+
+// FP64 pose of (point idx, step s) in world coordinates, for the FP64 path
+// and for FP32 near-boundary re-binning. Same association on both uses.
+struct Pose64 {
+    double x, y, z;
+};
+
+struct Vec9 {
+    double ux, uy, uz, vx, vy, vz, wx, wy, wz;
+};
+
+__device__ __forceinline__ Vec9 load_vec9(const double* t64, int NE, int idx) {
+    Vec9 v;
+    v.ux = t64[0 * NE + idx]; v.uy = t64[1 * NE + idx]; v.uz = t64[2 * NE + idx];
+    v.vx = t64[3 * NE + idx]; v.vy = t64[4 * NE + idx]; v.vz = t64[5 * NE + idx];
+    v.wx = t64[6 * NE + idx]; v.wy = t64[7 * NE + idx]; v.wz = t64[8 * NE + idx];
+    return v;
+}
+
+// Every FP64 pose of the library goes through this function, with each
+// rounding step spelled out, so the FP64 path and the FP32 path's re-binning
+// assign a point to the same cell.
+__device__ __forceinline__ double path_x(const Surface& sf, int32_t n) {
+    return __dadd_rn(sf.pass_x0, __dmul_rn((double)n, sf.fs));
+}
+__device__ __forceinline__ Pose64 pose64(const Vec9& v, double2 cs, double xc, double yc, double zr) {
+    Pose64 P;
+    P.x = __dadd_rn(xc, __fma_rn(cs.x, v.ux, __fma_rn(cs.y, v.vx, v.wx)));
+    P.y = __dadd_rn(yc, __fma_rn(cs.x, v.uy, __fma_rn(cs.y, v.vy, v.wy)));
+    P.z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
+    return P;
+}
+__device__ __forceinline__ long long bin64(double coord, double origin, double inv_pitch) {
+    return (long long)floor(__dmul_rn(__dsub_rn(coord, origin), inv_pitch));
+}
+
+// Item t of a run without an integer division per item (t < 2^24).
+__device__ __forceinline__ void run_item_fast(const Run& r, const RunIter& it, int32_t S, float inv_len,
+                                              int32_t t, int32_t* s, int32_t* m) {
+    int32_t k, off;
+    if (t < it.len0) {
+        k = 0;
+        off = it.first_off + t;
+    } else {
+        const int32_t tt = t - it.len0;
+        int32_t q = __float2int_rz((float)tt * inv_len);
+        if ((q + 1) * r.len <= tt) ++q;
+        else if (q * r.len > tt) --q;
+        k = 1 + q;
+        off = tt - q * r.len;
+    }
+    *s = it.occ0 + k * S + off;
+    const int32_t mm = r.m0 + off;
+    *m = mm >= S ? mm - S : mm;
+}
+
+// Enumerate runs for 32 points (lane = point) of tooth K, group g, pass p.
+template <typename Cell>
+__device__ __forceinline__ int warp_runs(const Surface& sf, const TileCtx<Cell>& tc, int K, int g,
+                                         int p, WarpRuns& wr) {
+    const int lane = threadIdx.x & 31;
+    const int E = sf.E;
+    const int j = g * 32 + lane;
+    int nr = 0;
+    if (j < E) {
+        const float4* t4 = sf.tool32 + 4 * (size_t)(K * E + j);
+        PointGeom geo = load_geom(t4);
+        TileFrame f;
+        const double yc = sf.pass_y0 + (double)p * sf.ae;
+        f.ylo = (float)(tc.Y0 - yc) - kMarginMm;
+        f.yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
+        f.zhi = (float)(sf.stock_z - sf.z_ref) + kMarginMm;
+        f.xlo = (float)(tc.X0 - sf.pass_x0) - kMarginMm;
+        f.xhi = (float)(tc.X0 + (double)tc.txc * sf.pitch - sf.pass_x0) + kMarginMm;
+        f.inv_fs = (float)(1.0 / sf.fs);
+        f.s0 = p * sf.steps_per_pass;
+        f.n_steps = sf.steps_per_pass;
+        f.dth = (float)sf.dtheta;
+        f.inv_dth = (float)(1.0 / sf.dtheta);
+        f.S = sf.S;
+        nr = point_runs(geo, f, wr.run[lane]);
+    }
+    wr.n[lane] = nr;
+    __syncwarp();
+    return __any_sync(0xffffffffu, nr > 0);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 path: tile-local FP32 poses, FP64 re-binning near cell boundaries.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void update32(uint32_t* cells, int idx, float zrel, Counters& c) {
+    const uint32_t e = enc32(__float_as_uint(zrel));
+    if (e < cells[idx]) {
+        atomicMin(cells + idx, e);
+        ++c.atomics;
+    }
+}
+
+__device__ void sweep_point32(const Surface& sf, const TileCtx<uint32_t>& tc, int K, int j, int p,
+                              const WarpRuns& wr, int o, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const int E = sf.E, NE = sf.n_teeth * E;
+    const int idx = K * E + j;
+    const float4* t4 = sf.tool32 + 4 * (size_t)idx;
+    const float4 a = t4[0], b = t4[1];
+    const float wz = t4[2].x;
+    const float ux = a.x, vx = a.y, wx = a.z, uz = a.w;
+    const float uy = b.x, vy = b.y, wy = b.z, vz = b.w;
+    const float zb = (float)(sf.z_ref - sf.stock_z) + wz;
+    const double yc = sf.pass_y0 + (double)p * sf.ae;
+    const float dy = (float)(yc - tc.Y0);
+    const float fs32 = (float)sf.fs;
+    const float inv_pitch = (float)(1.0 / sf.pitch);
+    const float g = sf.guard_cells;
+    const int S = sf.S;
+    const int s0 = p * sf.steps_per_pass;
+    const float2* __restrict__ ph32 = sf.ph32;
+    const int tile_x = sf.tile_x;
+    uint32_t* cells = tc.cells;
+    const int txc = tc.txc, tyc = tc.tyc;
+    for (int ai = 0; ai < wr.n[o]; ++ai) {
+        const Run r = wr.run[o][ai];
+        const RunIter it = run_iter(r, S);
+        if (it.total <= 0) continue;
+        const float inv_len = 1.0f / (float)r.len;
+        const int32_t sA = it.occ0 + it.first_off;
+        const float dxA = (float)((sf.pass_x0 - tc.X0) + (double)(sA - s0) * sf.fs);
+        for (int t = lane; t < it.total; t += 32) {
+            int32_t s, m;
+            run_item_fast(r, it, S, inv_len, t, &s, &m);
+            const float2 cs = __ldg(ph32 + m);
+            ++cnt.evaluated;
+            const float z = fmaf(cs.x, uz, fmaf(cs.y, vz, zb));
+            if (!(z < 0.f)) continue;
+            const float dx = fmaf((float)(s - sA), fs32, dxA);
+            const float xl = dx + fmaf(cs.x, ux, fmaf(cs.y, vx, wx));
+            const float yl = dy + fmaf(cs.x, uy, fmaf(cs.y, vy, wy));
+            const float fx = xl * inv_pitch, fy = yl * inv_pitch;
+            const float flx = floorf(fx), fly = floorf(fy);
+            const float rx = fx - flx, ry = fy - fly;
+            const int i = (int)flx, k = (int)fly;
+            const bool amb = rx < g || rx > 1.f - g || ry < g || ry > 1.f - g;
+            if (!amb) {
+                if ((unsigned)i < (unsigned)txc && (unsigned)k < (unsigned)tyc) {
+                    ++cnt.cutting;
+                    update32(cells, k * tile_x + i, z, cnt);
+                }
+                continue;
+            }
+            // ambiguous: could the point be in this tile at all?
+            const int i0 = rx < g ? i - 1 : i, i1 = rx > 1.f - g ? i + 1 : i;
+            const int k0 = ry < g ? k - 1 : k, k1 = ry > 1.f - g ? k + 1 : k;
+            if (i1 < 0 || i0 >= txc || k1 < 0 || k0 >= tyc) continue;
+            // re-bin in FP64 with the global sampling boundaries
+            ++cnt.rebinned;
+            const Vec9 v = load_vec9(sf.tool64, NE, idx);
+            const Pose64 P = pose64(v, __ldg(sf.ph64 + m), path_x(sf, s - s0), yc, sf.z_ref);
+            if (!(P.z < sf.stock_z)) continue;
+            const long long ig = bin64(P.x, sf.x0, 1.0 / sf.pitch) - (long long)tc.tx * tile_x;
+            const long long kg = bin64(P.y, sf.y0, 1.0 / sf.pitch) - (long long)tc.ty * sf.tile_y;
+            if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
+            ++cnt.cutting;
+            update32(cells, (int)kg * tile_x + (int)ig, (float)(P.z - sf.stock_z), cnt);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 path: all pose and binning arithmetic in FP64, global coordinates.
+// ---------------------------------------------------------------------------
+__device__ void sweep_point64(const Surface& sf, const TileCtx<unsigned long long>& tc, int K, int j,
+                              int p, const WarpRuns& wr, int o, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const int E = sf.E, NE = sf.n_teeth * E;
+    const int idx = K * E + j;
+    const Vec9 v = load_vec9(sf.tool64, NE, idx);
+    const double yc = sf.pass_y0 + (double)p * sf.ae;
+    const double inv_pitch = 1.0 / sf.pitch;
+    const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock_z;
+    const int S = sf.S;
+    const int s0 = p * sf.steps_per_pass;
+    const long long ib = (long long)tc.tx * sf.tile_x, kb = (long long)tc.ty * sf.tile_y;
+    const double2* __restrict__ ph64 = sf.ph64;
+    const int tile_x = sf.tile_x;
+    unsigned long long* cells = tc.cells;
+    const int txc = tc.txc, tyc = tc.tyc;
+    for (int ai = 0; ai < wr.n[o]; ++ai) {
+        const Run r = wr.run[o][ai];
+        const RunIter it = run_iter(r, S);
+        if (it.total <= 0) continue;
+        const float inv_len = 1.0f / (float)r.len;
+        for (int t = lane; t < it.total; t += 32) {
+            int32_t s, m;
+            run_item_fast(r, it, S, inv_len, t, &s, &m);
+            const double2 cs = __ldg(ph64 + m);
+            ++cnt.evaluated;
+            const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
+            if (!(z < stock)) continue;
+            const Pose64 P = pose64(v, cs, path_x(sf, s - s0), yc, zr);
+            const long long ig = bin64(P.x, x0, inv_pitch) - ib;
+            const long long kg = bin64(P.y, y0, inv_pitch) - kb;
+            if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
+            ++cnt.cutting;
+            const unsigned long long e = enc64((unsigned long long)__double_as_longlong(P.z));
+            unsigned long long* cell = cells + (int)kg * tile_x + (int)ig;
+            if (e < *cell) {
+                atomicMin(cell, e);
+                ++cnt.atomics;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent tile sweep. Tiles of all surfaces form one index space
+// (tile_base[s] = first tile of surface s); CTAs take tiles in a static
+// stride, or from *queue when it is not NULL. Inside a tile, warps take
+// (pass, tooth, 32-point group) tasks from a shared counter.
+template <bool FP64>
+__global__ void __launch_bounds__(256) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
+                                                    const int* __restrict__ tile_base,
+                                                    int total_tiles, int* queue,
+                                                    long long* counters) {
+    using Cell = typename std::conditional<FP64, unsigned long long, uint32_t>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_task, s_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    WarpRuns* wruns = reinterpret_cast<WarpRuns*>(smem);
+    Cell* cells = reinterpret_cast<Cell*>(smem + sizeof(WarpRuns) * nwarps);
+    WarpRuns& wr = wruns[warp];
+    Counters cnt = {0, 0, 0, 0};
+
+    int iter = 0;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_tile = queue ? atomicAdd(queue, 1) : (int)blockIdx.x + iter * (int)gridDim.x;
+            s_task = 0;
+        }
+        ++iter;
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= total_tiles) break;
+        const int sidx = (n_surf == 1 || tile_base == nullptr) ? 0 : find_surface(tile_base, n_surf, t);
+        const Surface& sf = surfs[sidx];
+        const int lt = t - (tile_base ? tile_base[sidx] : 0);
+        TileCtx<Cell> tc;
+        tc.cells = cells;
+        tc.tx = lt % sf.ntx;
+        tc.ty = lt / sf.ntx;
+        tc.txc = min(sf.tile_x, sf.nx - tc.tx * sf.tile_x);
+        tc.tyc = min(sf.tile_y, sf.ny - tc.ty * sf.tile_y);
+        tc.X0 = sf.x0 + (double)(tc.tx * sf.tile_x) * sf.pitch;
+        tc.Y0 = sf.y0 + (double)(tc.ty * sf.tile_y) * sf.pitch;
+        const int ncell = sf.tile_x * sf.tile_y;
+        Cell init;
+        if constexpr (FP64) init = (Cell)enc64((unsigned long long)__double_as_longlong(sf.stock_z));
+        else init = (Cell)enc32(__float_as_uint(0.0f));  // FP32 cells hold heights relative to the stock
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) cells[c] = init;
+        __syncthreads();
+
+        const int G = (sf.E + 31) / 32;
+        const int n_tasks = sf.n_passes * sf.n_teeth * G;
+        const double tile_y1 = tc.Y0 + (double)tc.tyc * sf.pitch;
+        const double tile_x1 = tc.X0 + (double)tc.txc * sf.pitch;
+        const double pass_x1 = sf.pass_x0 + (double)(sf.steps_per_pass - 1) * sf.fs;
+        const bool x_miss = (pass_x1 + sf.reach_x < tc.X0 - 1e-3) || (sf.pass_x0 - sf.reach_x > tile_x1 + 1e-3);
+        const float zhi = (float)(sf.stock_z - sf.z_ref) + kMarginMm;
+        while (!x_miss) {
+            int task = 0;
+            if (lane == 0) task = atomicAdd(&s_task, 1);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (task >= n_tasks) break;
+            const int p = task / (sf.n_teeth * G);
+            const int rem = task - p * sf.n_teeth * G;
+            const int K = rem / G, g = rem - K * G;
+            const double yc = sf.pass_y0 + (double)p * sf.ae;
+            const float4 gb = sf.groups[K * G + g];
+            const float ylo = (float)(tc.Y0 - yc) - kMarginMm, yhi = (float)(tile_y1 - yc) + kMarginMm;
+            if (gb.y < ylo || gb.x > yhi || gb.z >= zhi) continue;  // warp-uniform
+            if (!warp_runs(sf, tc, K, g, p, wr)) continue;
+            for (int o = 0; o < 32; ++o) {
+                if (wr.n[o] == 0) continue;
+                if constexpr (FP64) sweep_point64(sf, tc, K, g * 32 + o, p, wr, o, cnt);
+                else sweep_point32(sf, tc, K, g * 32 + o, p, wr, o, cnt);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // decode and store the tile
+        if constexpr (FP64) {
+            double* out = reinterpret_cast<double*>(sf.heights);
+            for (int c = threadIdx.x; c < tc.txc * tc.tyc; c += blockDim.x) {
+                const int k = c / tc.txc, i = c - k * tc.txc;
+                const unsigned long long e = cells[k * sf.tile_x + i];
+                out[(size_t)(tc.ty * sf.tile_y + k) * sf.nx + tc.tx * sf.tile_x + i] =
+                    __longlong_as_double((long long)dec64(e));
+            }
+        } else {
+            float* out = reinterpret_cast<float*>(sf.heights);
+            const float st = (float)sf.stock_z;
+            const bool vec = ((sf.nx & 3) == 0) && ((tc.txc & 3) == 0) && ((sf.tile_x & 3) == 0) &&
+                             ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+            if (vec) {
+                const int q = tc.txc >> 2;
+                for (int c = threadIdx.x; c < q * tc.tyc; c += blockDim.x) {
+                    const int k = c / q, i4 = (c - k * q) << 2;
+                    const uint4 e = *reinterpret_cast<const uint4*>(cells + k * sf.tile_x + i4);
+                    float4 v;
+                    v.x = st + __uint_as_float(dec32(e.x));
+                    v.y = st + __uint_as_float(dec32(e.y));
+                    v.z = st + __uint_as_float(dec32(e.z));
+                    v.w = st + __uint_as_float(dec32(e.w));
+                    *reinterpret_cast<float4*>(
+                        out + (size_t)(tc.ty * sf.tile_y + k) * sf.nx + tc.tx * sf.tile_x + i4) = v;
+                }
+            } else {
+                for (int c = threadIdx.x; c < tc.txc * tc.tyc; c += blockDim.x) {
+                    const int k = c / tc.txc, i = c - k * tc.txc;
+                    out[(size_t)(tc.ty * sf.tile_y + k) * sf.nx + tc.tx * sf.tile_x + i] =
+                        st + __uint_as_float(dec32(cells[k * sf.tile_x + i]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    warp_flush(cnt, counters);
+}
+
+// ===========================================================================
+// Roughness: FP64 moments with a fixed reduction tree. Maps are cut into
+// chunks of kChunk cells; block b reduces chunk b of the job that owns it
+// (chunk_base[j] = first chunk of job j), so one launch serves one map or a
+// batch of maps of any sizes. Every sum is taken in the same order whatever
+// the launch timing, so results are reproducible bit for bit.
+// ===========================================================================
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Sum (kind 0), min (1) or max (2) of v over the block, in a fixed order;
+// every thread gets the result.
+template <int KIND>
+__device__ __forceinline__ double block_reduce(double v, double* sh /*[32]*/) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    v = KIND == 0 ? warp_sum(v) : KIND == 1 ? warp_min(v) : warp_max(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double x = lane < nw ? sh[lane] : (KIND == 0 ? 0.0 : KIND == 1 ? 1e300 : -1e300);
+    x = KIND == 0 ? warp_sum(x) : KIND == 1 ? warp_min(x) : warp_max(x);
+    return x;
+}
+
+__device__ __forceinline__ int find_job(const int* base, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ void chunk_range(const RoughJob& jb, int c, size_t* lo, size_t* hi) {
+    *lo = (size_t)c * kChunk;
+    const size_t e = *lo + kChunk;
+    *hi = e < jb.n ? e : jb.n;
+}
+
+// Pass 1: per chunk sum, min, max -> part[b*3 + {0,1,2}]
+template <typename T>
+__global__ void __launch_bounds__(256) rough1_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                     const int* __restrict__ chunk_base, double* part) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    size_t lo, hi;
+    chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
+    const T* h = reinterpret_cast<const T*>(jb.h);
+    double s = 0.0, mn = 1e300, mx = -1e300;
+#pragma unroll 4
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double z = (double)h[i];
+        s += z;
+        mn = fmin(mn, z);
+        mx = fmax(mx, z);
+    }
+    s = block_reduce<0>(s, sh);
+    mn = block_reduce<1>(mn, sh);
+    mx = block_reduce<2>(mx, sh);
+    if (threadIdx.x == 0) {
+        part[3 * (size_t)b] = s;
+        part[3 * (size_t)b + 1] = mn;
+        part[3 * (size_t)b + 2] = mx;
+    }
+}
+
+// Mean of job j from its chunk sums, in chunk order (identical in every block).
+__device__ double job_mean(const double* part, int c0, int c1, size_t n, double* sh) {
+    double s = 0.0;
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) s += part[3 * (size_t)c];
+    s = block_reduce<0>(s, sh);
+    return s / (double)n;
+}
+
+// Pass 2: per chunk sums of |d|, d^2, d^3, d^4 about the job mean -> part2[b*4 + a]
+template <typename T>
+__global__ void __launch_bounds__(256) rough2_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                     const int* __restrict__ chunk_base, const double* part,
+                                                     double* part2) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    const double mu = job_mean(part, chunk_base[j], chunk_base[j + 1], jb.n, sh);
+    size_t lo, hi;
+    chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
+    const T* h = reinterpret_cast<const T*>(jb.h);
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+#pragma unroll 4
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double d = (double)h[i] - mu;
+        const double d2 = d * d;
+        v0 += fabs(d);
+        v1 += d2;
+        v2 += d2 * d;
+        v3 += d2 * d2;
+    }
+    v0 = block_reduce<0>(v0, sh);
+    v1 = block_reduce<0>(v1, sh);
+    v2 = block_reduce<0>(v2, sh);
+    v3 = block_reduce<0>(v3, sh);
+    if (threadIdx.x == 0) {
+        double* o = part2 + 4 * (size_t)b;
+        o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
+    }
+}
+
+// Final: one block per job combines its chunks and writes the areal values.
+__global__ void __launch_bounds__(256) rough3_kernel(const RoughJob* __restrict__ jobs,
+                                                     const int* __restrict__ chunk_base, const double* part,
+                                                     const double* part2) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    const RoughJob jb = jobs[j];
+    const int c0 = chunk_base[j], c1 = chunk_base[j + 1];
+    const double mu = job_mean(part, c0, c1, jb.n, sh);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    double mn = 1e300, mx = -1e300;
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
+        for (int a = 0; a < 4; ++a) v[a] += part2[4 * (size_t)c + a];
+        mn = fmin(mn, part[3 * (size_t)c + 1]);
+        mx = fmax(mx, part[3 * (size_t)c + 2]);
+    }
+    for (int a = 0; a < 4; ++a) v[a] = block_reduce<0>(v[a], sh);
+    mn = block_reduce<1>(mn, sh);
+    mx = block_reduce<2>(mx, sh);
+    if (threadIdx.x == 0) {
+        fsm_roughness_out* out = jb.out;
+        const double dn = (double)jb.n;
+        out->n = dn;
+        out->mean = mu;
+        out->zmin = mn;
+        out->zmax = mx;
+        out->Sa = v[0] / dn;
+        out->Sq = sqrt(v[1] / dn);
+        out->Sp = mx - mu;
+        out->Sv = mu - mn;
+        out->Sz = out->Sp + out->Sv;
+        if (out->Sq > 0.0) {
+            const double sq = out->Sq;
+            out->Ssk = (v[2] / dn) / (sq * sq * sq);
+            out->Sku = (v[3] / dn) / (sq * sq * sq * sq);
+        } else {
+            out->Ssk = __longlong_as_double(0x7ff8000000000000ll);
+            out->Sku = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        out->n_rows = jb.n_rows;
+        out->n_cols = jb.n_cols;
+    }
+}
+
+// Profiles: block (j, q) handles profile q of job j (rows first, then columns).
+template <typename T>
+__global__ void __launch_bounds__(256) profiles_kernel(const RoughJob* __restrict__ jobs, int per_job) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x / per_job, q = blockIdx.x - j * per_job;
+    const RoughJob jb = jobs[j];
+    if (q >= jb.n_rows + jb.n_cols) return;
+    const bool row = q < jb.n_rows;
+    const int r = row ? q : q - jb.n_rows;
+    const int nx = jb.nx, ny = jb.ny;
+    const int L = row ? nx : ny;
+    int fixed;
+    size_t stride, base;
+    if (row) {
+        fixed = (int)(((long long)(2 * r + 1) * ny) / (2 * jb.n_rows));
+        base = (size_t)fixed * nx;
+        stride = 1;
+    } else {
+        fixed = (int)(((long long)(2 * r + 1) * nx) / (2 * jb.n_cols));
+        base = (size_t)fixed;
+        stride = (size_t)nx;
+    }
+    const T* h = reinterpret_cast<const T*>(jb.h);
+    double s = 0.0;
+    for (int a = threadIdx.x; a < L; a += blockDim.x) s += (double)h[base + (size_t)a * stride];
+    const double mu = block_reduce<0>(s, sh) / (double)L;
+    double w = 0.0;
+    for (int a = threadIdx.x; a < L; a += blockDim.x) w += fabs((double)h[base + (size_t)a * stride] - mu);
+    const double ra = block_reduce<0>(w, sh) / (double)L;
+    double rz = 0.0;
+    for (int seg = 0; seg < 5; ++seg) {  // Rz: max - min over 5 segments [floor(qL/5), floor((q+1)L/5))
+        const int lo = (int)(((long long)seg * L) / 5), hi = (int)(((long long)(seg + 1) * L) / 5);
+        double mx = -1e300, mn = 1e300;
+        for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
+            const double z = (double)h[base + (size_t)a * stride];
+            mx = fmax(mx, z);
+            mn = fmin(mn, z);
+        }
+        mx = block_reduce<2>(mx, sh);
+        mn = block_reduce<1>(mn, sh);
+        rz += mx - mn;
+    }
+    if (threadIdx.x == 0) {
+        const double rzv = L >= 5 ? rz / 5.0 : __longlong_as_double(0x7ff8000000000000ll);
+        fsm_roughness_out* out = jb.out;
+        if (row) {
+            out->row_index[r] = fixed;
+            out->Ra_row[r] = ra;
+            out->Rz_row[r] = rzv;
+        } else {
+            out->col_index[r] = fixed;
+            out->Ra_col[r] = ra;
+            out->Rz_col[r] = rzv;
+        }
+    }
+}
+
+// ===========================================================================
+// Launchers (called by the C ABI layer)
+// ===========================================================================
+cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_t st) {
+    Surface dummy;
+    if (one) dummy = *one;
+    else memset(&dummy, 0, sizeof dummy);
+    plan_kernel<<<n, 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
+    return cudaGetLastError();
+}
+
+size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads) {
+    const size_t cell = precision == 0 ? 8 : 4;
+    return sizeof(WarpRuns) * (size_t)(threads / 32) + cell * (size_t)tile_x * (size_t)tile_y;
+}
+
+cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
+                                const int* d_tile_base, int total_tiles, int* d_queue,
+                                long long* d_counters, int grid, int threads, size_t smem,
+                                cudaStream_t st) {
+    if (precision == 0) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sweep_kernel<true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles, d_queue,
+                                                        d_counters);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sweep_kernel<false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles, d_queue,
+                                                         d_counters);
+    }
+    return cudaGetLastError();
+}
+
+int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
+    int nb = 0;
+    // dynamic shared memory above 48 KB needs the opt-in before any query
+    if (precision == 0) {
+        if (cudaFuncSetAttribute(sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<true>, threads, smem);
+    } else {
+        if (cudaFuncSetAttribute(sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false>, threads, smem);
+    }
+    return nb;
+}
+
+__global__ void rough_setup_one_kernel(RoughJob jb, int chunks, RoughJob* d_job, int* d_base) {
+    if (threadIdx.x == 0) {
+        *d_job = jb;
+        d_base[0] = 0;
+        d_base[1] = chunks;
+    }
+}
+
+cudaError_t launch_roughness_one(int precision, const RoughJob& jb, char* d_ws, cudaStream_t st) {
+    const int chunks = (int)((jb.n + kChunk - 1) / kChunk);
+    RoughJob* d_job = (RoughJob*)d_ws;
+    int* d_base = (int*)(d_ws + 256);
+    double* d_part = (double*)(d_ws + 512);
+    rough_setup_one_kernel<<<1, 32, 0, st>>>(jb, chunks, d_job, d_base);
+    return launch_roughness_jobs(precision, d_job, 1, d_base, chunks, jb.n_rows + jb.n_cols, d_part, st);
+}
+
+size_t roughness_one_ws_bytes(size_t n) {
+    const size_t chunks = (n + kChunk - 1) / kChunk;
+    return 512 + 7 * sizeof(double) * chunks;
+}
+
+cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_jobs, const int* d_chunk_base,
+                                  int total_chunks, int max_profiles, double* d_part, cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    double* part2 = d_part + 3 * (size_t)total_chunks;
+    if (precision == 0) {
+        rough1_kernel<double><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part);
+        rough2_kernel<double><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
+        if (max_profiles > 0) profiles_kernel<double><<<n_jobs * max_profiles, 256, 0, st>>>(d_jobs, max_profiles);
+    } else {
+        rough1_kernel<float><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part);
+        rough2_kernel<float><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
+        if (max_profiles > 0) profiles_kernel<float><<<n_jobs * max_profiles, 256, 0, st>>>(d_jobs, max_profiles);
+    }
+    rough3_kernel<<<n_jobs, 256, 0, st>>>(d_jobs, d_chunk_base, d_part, part2);
+    return cudaGetLastError();
+}
+
+}  // namespace fsm

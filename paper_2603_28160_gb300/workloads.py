@@ -225,8 +225,16 @@ def lhs_batch(n: int = 4096, seed: int = 4096, precision: str = "fp32",
                         n_edge=n_edge, n_end=n_end)
         x0, y0, nx, ny = _patch(side, side, pitch)
         n_passes = int(math.ceil(side / ae)) + 1
-        first_y = -0.5 * (n_passes - 1) * ae
-        px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, first_y, ap, pitch)
+        # a tilted flat end cuts with the low side of its rim, D/2 from the
+        # axis toward (+lead, +tilt): shift the tool path so that rim sweeps
+        # the patch
+        sx = sy = 0.0
+        if kind == "flat" and (lead > 0.0 or tilt > 0.0):
+            a, b = math.sin(math.radians(lead)), math.sin(math.radians(tilt))
+            nrm = math.hypot(a, b)
+            sx, sy = 0.5 * D * a / nrm, 0.5 * D * b / nrm
+        first_y = -0.5 * (n_passes - 1) * ae - sy
+        px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, -sx, first_y, ap, pitch)
         proc = ProcessSpec(fz=fz, rpm=6000, rot_step_deg=rot_step_deg, ap=ap, pass_x0=px,
                            pass_y0=py, steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch,
                            nx=nx, ny=ny, n_passes=n_passes, ae=ae, lead_deg=lead,
