@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the FSM surface generator on GB300.
+
+One step = one pass of the whole hot path over one surface: device planning
+(edge, phase and path tables), the persistent tile sweep with decode and
+store, the FP64 roughness moments and the profiles -- the 5x5 mm, 1 um
+ball-end raster (25 Mcells, 12 passes; the metric's configuration). Prints
+ONE JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank predicts its own
+surface (weak scaling, no collective on the data path); the time is the max
+over ranks. --impl reference times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge-point evals/s and surfaces/s at <=5 nm height error; p50/p99 latency"
+UNIT = "cutting edge-point evaluations/s"
+FP32_FLOPS_PER_EVAL = 16  # 6 FMA pose (12) + 2 tile offsets + 2 bin scalings
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--width", type=float, default=5.0,
+                    help="patch width in mm (5.0 = the measured configuration; smaller for profiling)")
+    args = ap.parse_args()
+    global WIDTH
+    WIDTH = args.width
+    return args
+
+
+WIDTH = 5.0
+
+
+def workload(precision):
+    from paper_2603_28160_gb300 import workloads as W
+    return W.raster_ball_d10(precision=precision, width=WIDTH)
+
+
+def config(w, extra=None):
+    p = w.process
+    c = {"workload": "raster_ball_d10 (ball D=10, 4 flutes, helix 30, runout 5um@30, lead 15, 12 passes "
+                     "fz=0.08 ae=0.3, 200 edge pts, 0.1 deg/step, %gx%g mm @ 1 um)" % (WIDTH, WIDTH),
+         "cells": p.nx * p.ny, "passes": p.n_passes, "time_steps": p.n_passes * p.steps_per_pass,
+         "trajectory_points": w.trajectory_points, "precision": p.precision,
+         "l2": "flushed between timed steps (256 MB write, outside the step events)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("fsm_kernels.cu", "fsm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2603_28160_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                mx.append(float(v[2]))
+            except ValueError:
+                continue
+            for n, flag in zip(names, v[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(n_threads=None):
+    """Bounded sample for the CPU oracle: the four middle passes of the
+    workload (same tool, grid and path; a third of the tool path)."""
+    from paper_2603_28160_gb300 import workloads as W
+    w = workload("fp64")
+    p = w.process
+    mid = p.n_passes // 2 - 2
+    p2 = p.replace(n_passes=4, pass_y0=p.pass_y0 + mid * p.ae)
+    return W.Workload(w.name + "_4passes", w.tool, p2)
+
+
+def run_oracle_step(sample, threads):
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    r = O.fsm(sample, n_threads=threads)
+    return time.perf_counter() - t0, r.stats
+
+
+def cpu_baseline():
+    sample = oracle_sample()
+    threads = min(os.cpu_count() or 1, sample.process.n_passes)
+    dt, st = run_oracle_step(sample, threads)
+    return {"value": st["cutting"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "4 of the 12 passes (middle ones) of the same workload, full grid; plain FP64 C oracle "
+                      "evaluating all %d trajectory points, one pass per thread; %.2f s wall"
+                      % (st["trajectory_points"], dt)}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle as the reference arm (bounded sample per step)."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1 and rank != 0:
+        return 0
+    sample = oracle_sample()
+    threads = min(os.cpu_count() or 1, sample.process.n_passes)
+    for _ in range(args.warmup):
+        run_oracle_step(sample, threads)
+    times, cut = [], 0
+    for _ in range(args.steps):
+        dt, st = run_oracle_step(sample, threads)
+        times.append(dt)
+        cut = st["cutting"]
+    ms = 1e3 * sum(times) / len(times)
+    value = cut / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config(workload("fp64"), {"sample": "4 middle passes of 12", "oracle_threads": threads}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "4 of the 12 passes of the workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def time_steps(ctx, F, tool, proc, out, rough, K, flush, precision, events_sweep=True):
+    import torch
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in sw:  # create the underlying CUDA events before handing them over
+        a.record(st)
+        b.record(st)
+    torch.cuda.synchronize()
+    prec_code = F.FSM_FP64 if precision == "fp64" else F.FSM_FP32
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(st)
+        ctx.predict_surface(tool, proc, out, events=sw[i] if events_sweep else None)
+        ctx.roughness_async(out, prec_code, rough)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    sweep_ms = [a.elapsed_time(b) for a, b in sw]
+    return step_ms, sweep_ms
+
+
+def gb300_arm(args):
+    import torch
+
+    from paper_2603_28160_gb300 import fsm as F
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    ctx = F.Context(local)
+    w = workload(args.precision)
+    tool, proc = ctx.tool(w.tool), ctx.process(w.process)
+    out = F.heights_tensor(w.process)
+    rough = torch.zeros(F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    prec_code = F.FSM_FP64 if args.precision == "fp64" else F.FSM_FP32
+
+    # work counts of one step (deterministic), outside the timed region
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ctx.predict_surface(tool, proc, out, counters=cnt)
+    torch.cuda.synchronize()
+    evaluated, cutting, rebinned, atomics = [int(x) for x in cnt.cpu()]
+
+    for _ in range(args.warmup):
+        ctx.predict_surface(tool, proc, out)
+        ctx.roughness_async(out, prec_code, rough)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    step_ms, sweep_ms = time_steps(ctx, F, tool, proc, out, rough, args.steps, flush, args.precision)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(ws)
+    clk = clocks.stop()
+    ms_local = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(ms_local, ws)
+    value = ws * cutting / (ms / 1e3)
+    p50 = statistics.median(step_ms)
+    p99 = sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]
+    sweep_mean = sum(sweep_ms) / len(sweep_ms)
+
+    # end to end through the C ABI with host buffers: descriptors in, the map
+    # and the roughness record copied back to pinned host memory every step
+    host_map = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    host_rough = torch.empty(F.ROUGH_BYTES, dtype=torch.uint8, pin_memory=True)
+    e2e_steps = max(3, args.steps // 3)
+    for _ in range(2):
+        ctx.predict_surface(tool, proc, out)
+        ctx.roughness_async(out, prec_code, rough)
+        host_map.copy_(out, non_blocking=True)
+        host_rough.copy_(rough, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        t_ = ctx.tool(w.tool)   # descriptors cross the ABI every step
+        p_ = ctx.process(w.process)
+        ctx.predict_surface(t_, p_, out)
+        ctx.roughness_async(out, prec_code, rough)
+        host_map.copy_(out, non_blocking=True)
+        host_rough.copy_(rough, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+    d2h = out.numel() * out.element_size() + F.ROUGH_BYTES
+    h2d = F.C.sizeof(F.ToolDesc) + F.C.sizeof(F.ProcessDesc)
+
+    # the plain FP64 single-surface form, for comparison
+    fp64 = None
+    if not args.skip_fp64 and args.precision != "fp64":
+        w64 = workload("fp64")
+        t64, p64 = ctx.tool(w64.tool), ctx.process(w64.process)
+        out64 = F.heights_tensor(w64.process)
+        cnt64 = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ctx.predict_surface(t64, p64, out64, counters=cnt64)
+        torch.cuda.synchronize()
+        cut64 = int(cnt64[1].item())
+        k64 = max(3, args.steps // 10)
+        s64, sw64 = time_steps(ctx, F, t64, p64, out64, rough, k64, flush, "fp64")
+        ms64 = max_over_ranks(sum(s64) / len(s64), ws)
+        fp64 = {"value": ws * cut64 / (ms64 / 1e3), "ms_per_step": ms64, "steps": k64,
+                "sweep_ms": sum(sw64) / len(sw64), "cutting": cut64,
+                "roofline": {"bound": "alu", "achieved": cut64 * FP32_FLOPS_PER_EVAL / (sum(sw64) / len(sw64)) / 1e9,
+                             "peak": 1.25, "unit": "TFLOP/s (FP64)"}}
+        fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / 1.25
+        del out64
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant kernel (the FP32 sweep): algorithmic FP32 flops
+    # per cutting evaluation / live event time of the sweep launch
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    if args.precision == "fp32":
+        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        peak_note = "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (props.multi_processor_count, sm_max)
+    else:
+        peak = 1.25
+        peak_note = "nominal FP64"
+    achieved = cutting * FP32_FLOPS_PER_EVAL / (sweep_mean / 1e3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "sweep_%s_raster_ball_d10.json" % args.precision)
+    if os.path.exists(prof):
+        try:
+            pj = json.load(open(prof))
+            if pj.get("src_hash") == src_hash():
+                traffic = pj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": config(w, {"parallelism": "replicas" if ws > 1 else "single GPU"}),
+        "surfaces_per_s": ws / (ms / 1e3),
+        "latency_ms": {"p50": p50, "p99": p99, "of": "single-surface steps (events, stream-ordered)"},
+        "work": {"cutting": cutting, "evaluated": evaluated, "rebinned_fp64": rebinned, "atomics": atomics,
+                 "trajectory_points": w.trajectory_points,
+                 "trajectory_points_per_s": ws * w.trajectory_points / (ms / 1e3)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "sweep_kernel<%s>" % args.precision.upper(),
+                     "sweep_ms": sweep_mean, "flops_per_cutting_eval": FP32_FLOPS_PER_EVAL,
+                     "peak_source": peak_note},
+        "e2e": {"value": ws * cutting / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3,
+                "note": "host descriptors by value through the C ABI; height map and roughness copied to "
+                        "pinned host memory every step"},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+        "fp64_single_surface": fp64,
+        "src_hash": src_hash(),
+    }
+    if ws == 1 and not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gb300_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -122,22 +122,28 @@ typedef struct {
     int32_t reserved;
 } fsm_process_desc;
 
-/* Optional launch overrides and counters for fsm_predict_surface.
- *   tile_x, tile_y    shared-memory tile in cells (0 = library default)
+/* Optional launch overrides, counters and timing for the prediction calls.
+ *   tile_x, tile_y    shared-memory tile in cells (0 = library default;
+ *                     tile_x a multiple of 4)
  *   block_threads     threads per CTA (0 = default)
+ *   ctas_per_sm       cap on resident CTAs per SM (0 = as many as fit)
  *   d_counters        NULL, or device int64_t[4] the sweep ADDS to:
  *                     [0] edge-point poses evaluated,
  *                     [1] cutting evaluations: inside the patch and below the
  *                         stock surface (the points the per-cell minimum runs
  *                         over),
  *                     [2] cutting points re-binned in FP64 (FP32 path),
- *                     [3] shared-memory atomic updates issued. */
+ *                     [3] shared-memory atomic updates issued.
+ *   sweep_events      NULL or two cudaEvent_t (as void*) recorded on the
+ *                     stream just before and just after the sweep launch(es),
+ *                     to time the sweep kernel alone. */
 typedef struct {
     int32_t tile_x;
     int32_t tile_y;
     int32_t block_threads;
     int32_t ctas_per_sm;
     int64_t* d_counters;
+    void* sweep_events[2];
 } fsm_predict_opts;
 
 /* Areal (ISO 25178-2) and line (ISO 4287) roughness of one height map,

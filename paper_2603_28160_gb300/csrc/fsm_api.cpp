@@ -274,9 +274,12 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
         return cuda_fail(e, "plan kernel");
     }
     const int tiles = s.ntx * s.nty;
+    if (opts && opts->ctas_per_sm > 0) bps = std::min(bps, (int)opts->ctas_per_sm);
     const int grid = std::min(tiles, ctx->sm_count * bps);
+    if (opts && opts->sweep_events[0]) cudaEventRecord((cudaEvent_t)opts->sweep_events[0], st);
     e = launch_sweep_shaped(p.precision, d_s, 1, nullptr, tiles, nullptr,
                             opts ? (long long*)opts->d_counters : nullptr, grid, sh.threads, smem, st);
+    if (opts && opts->sweep_events[1]) cudaEventRecord((cudaEvent_t)opts->sweep_events[1], st);
     cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

@@ -30,6 +30,7 @@ struct BatchLayout {
            off_cb32 = 0, off_part64 = 0, off_part32 = 0, off_tables = 0, total = 0;
     bool rough = false;
     long long* counters = nullptr;
+    void* events[2] = {nullptr, nullptr};
     std::vector<char> blob;  // host image of [off_surf, off_tables)
 };
 
@@ -58,6 +59,14 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     if (L->n32 && (rc = sweep_config(ctx, FSM_FP32, L->sh32, &L->smem32, &L->bps32)) != FSM_OK) return rc;
     L->rough = d_rough != nullptr;
     L->counters = opts ? (long long*)opts->d_counters : nullptr;
+    if (opts) {
+        L->events[0] = opts->sweep_events[0];
+        L->events[1] = opts->sweep_events[1];
+        if (opts->ctas_per_sm > 0) {
+            L->bps64 = std::min(L->bps64, (int)opts->ctas_per_sm);
+            L->bps32 = std::min(L->bps32, (int)opts->ctas_per_sm);
+        }
+    }
 
     // sizes
     std::vector<Surface> hs(n);
@@ -135,6 +144,7 @@ fsm_status run_batch(fsm_ctx* ctx, const BatchLayout& L, char* base, cudaStream_
     Surface* d_surf = (Surface*)(base + L.off_surf);
     if ((e = launch_plan(d_surf, L.n, nullptr, st)) != cudaSuccess) return cuda_fail(e, "plan kernel");
     int* q = (int*)(base + L.off_queue);
+    if (L.events[0]) cudaEventRecord((cudaEvent_t)L.events[0], st);
     if (L.n64) {
         const int grid = std::min(L.tiles64, ctx->sm_count * L.bps64);
         e = launch_sweep_shaped(FSM_FP64, d_surf, L.n64, (const int*)(base + L.off_tb64), L.tiles64, q, L.counters,
@@ -147,6 +157,7 @@ fsm_status run_batch(fsm_ctx* ctx, const BatchLayout& L, char* base, cudaStream_
                                 L.counters, grid, L.sh32.threads, L.smem32, st);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel (FP32)");
     }
+    if (L.events[1]) cudaEventRecord((cudaEvent_t)L.events[1], st);
     if (L.rough) {
         const RoughJob* jobs = (const RoughJob*)(base + L.off_jobs);
         if (L.n64 && (e = launch_roughness_jobs(FSM_FP64, jobs, L.n64, (const int*)(base + L.off_cb64), L.chunks64,

@@ -60,9 +60,12 @@ struct Surface {
     void* heights;    // output map
     // ---- derived (plan kernel) ----
     double z_ref, fs, dtheta;       // reference height, feed per step, step angle (rad)
+    double inv_pitch;               // 1 / pitch
     float reach_x, reach_y;         // max |P_x|, |P_y| over points and phases
-    float guard_cells;              // FP32 bin ambiguity band (cells)
-    float zrel_lo;                  // lowest P_z + z_ref - stock over all points
+    float zrel_f;                   // z_ref - stock_z
+    float fs_hi, fs_lo;             // fs as an unevaluated float pair (fs_hi + fs_lo)
+    float fs_f, inv_fs_f, dth_f, inv_dth_f, inv_pitch_f;
+    float guard_extra;              // FP32 rounding of the bin scaling, in cells
 };
 
 // ---------------------------------------------------------------------------
@@ -268,6 +271,27 @@ FSM_HD int point_runs(const PointGeom& g, const TileFrame& f, Run* runs) {
         ++nr;
     }
     return nr;
+}
+
+// a + b as an unevaluated pair (hi, lo) with hi = fl(a + b) (Knuth's two-sum).
+FSM_HD void two_sum(float a, float b, float* hi, float* lo) {
+    const float s = a + b;
+    const float bb = s - a;
+    *lo = (a - (s - bb)) + (b - bb);
+    *hi = s;
+}
+
+// (d_hi + d_lo) + n * (f_hi + f_lo) rounded to float, for an integer n that
+// is exact in float (|n| < 2^24): the product's rounding error is recovered
+// with an FMA, so the result is within about one rounding of the exact value.
+FSM_HD float df_affine(float d_hi, float d_lo, int32_t n, float f_hi, float f_lo) {
+    const float nf = (float)n;
+    const float p = nf * f_hi;
+    const float pe = fmaf(nf, f_hi, -p);
+    float s, e;
+    two_sum(d_hi, p, &s, &e);
+    e += d_lo + pe + nf * f_lo;
+    return s + e;
 }
 
 // Steps of a run: global steps s in [s_lo, s_hi] with (s - m0) mod S < len.

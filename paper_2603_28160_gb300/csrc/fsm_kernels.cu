@@ -162,20 +162,24 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
     }
     if (tid == 0) {
         const double zr = sf->stock_z - sf->ap - zlo_exact;
+        const double fs = (double)N * sf->fz / (double)S;
         sf->z_ref = zr;
-        sf->fs = (double)N * sf->fz / (double)S;
+        sf->fs = fs;
         sf->dtheta = dth;
+        sf->inv_pitch = 1.0 / sf->pitch;
         sf->reach_x = red_rx[0];
         sf->reach_y = red_ry[0];
-        sf->zrel_lo = (float)(zr + zlo_exact - sf->stock_z);
-        // FP32 tile-local error bound (mm): inputs, products and sums each
-        // round by <= 2^-24 relative; a factor 2 on top of the sum of terms.
+        sf->zrel_f = (float)(zr - sf->stock_z);
+        sf->fs_hi = (float)fs;
+        sf->fs_lo = (float)(fs - (double)sf->fs_hi);
+        sf->fs_f = (float)fs;
+        sf->inv_fs_f = (float)(1.0 / fs);
+        sf->dth_f = (float)dth;
+        sf->inv_dth_f = (float)(1.0 / dth);
+        sf->inv_pitch_f = (float)(1.0 / sf->pitch);
+        // the bin scaling x_l * (1/pitch) rounds twice, relative to |x_l / pitch|
         const double u24 = 5.9604644775390625e-8;
-        double rho = fmax((double)red_rx[0], (double)red_ry[0]);
-        double tile = fmax((double)sf->tile_x, (double)sf->tile_y) * sf->pitch;
-        double span = tile + 2.0 * rho + 2.0 * (double)N * sf->fz;
-        double err = u24 * (7.0 * rho + 2.0 * (rho + tile + span) + 2.0 * span + tile);
-        sf->guard_cells = (float)(2.0 * err / sf->pitch + 4.0 * u24 * (double)(sf->tile_x + sf->tile_y));
+        sf->guard_extra = (float)(3.0 * u24 * (double)max(sf->tile_x, sf->tile_y) + 1e-6);
     }
 }
 
@@ -202,10 +206,28 @@ __device__ __forceinline__ void warp_flush(Counters& c, long long* out) {
     }
 }
 
-// One warp's scratch: runs of 32 edge points.
-struct WarpRuns {
-    Run run[32][kMaxArcs];
+// A run of one edge point with its iteration bookkeeping (see run_iter).
+struct RunRec {
+    int32_t m0, len, occ0, first_off, len0, total, span;
+};
+
+constexpr int kRebinCap = 64;
+
+// One warp's scratch: runs of 32 edge points and the FP64 re-binning queue.
+struct WarpScratch {
+    RunRec run[32][kMaxArcs];
     int32_t n[32];
+    int32_t q_s[kRebinCap], q_m[kRebinCap], q_idx[kRebinCap];
+};
+
+constexpr int kPassCache = 64;
+
+// Per-tile values shared by all warps, computed once per tile in FP64.
+struct TileShared {
+    float ylo[kPassCache], yhi[kPassCache], dy[kPassCache];
+    float dx_hi, dx_lo;  // pass_x0 - tile origin x, as a float pair
+    float xlo, xhi;      // tile x extent relative to pass_x0, margins included
+    float zhi;           // stock - z_ref + margin
 };
 
 template <typename Cell>
@@ -216,8 +238,6 @@ struct TileCtx {
     double X0, Y0;        // tile origin (world)
 };
 
-// FP64 pose of (point idx, step s) in world coordinates, for the FP64 path
-// and for FP32 near-boundary re-binning. Same association on both uses.
 struct Pose64 {
     double x, y, z;
 };
@@ -234,11 +254,14 @@ __device__ __forceinline__ Vec9 load_vec9(const double* t64, int NE, int idx) {
     return v;
 }
 
-// Every FP64 pose of the library goes through this function, with each
+// Every FP64 pose of the library goes through these functions, with each
 // rounding step spelled out, so the FP64 path and the FP32 path's re-binning
 // assign a point to the same cell.
 __device__ __forceinline__ double path_x(const Surface& sf, int32_t n) {
     return __dadd_rn(sf.pass_x0, __dmul_rn((double)n, sf.fs));
+}
+__device__ __forceinline__ double path_y(const Surface& sf, int p) {
+    return __dadd_rn(sf.pass_y0, __dmul_rn((double)p, sf.ae));
 }
 __device__ __forceinline__ Pose64 pose64(const Vec9& v, double2 cs, double xc, double yc, double zr) {
     Pose64 P;
@@ -252,58 +275,134 @@ __device__ __forceinline__ long long bin64(double coord, double origin, double i
 }
 
 // Item t of a run without an integer division per item (t < 2^24).
-__device__ __forceinline__ void run_item_fast(const Run& r, const RunIter& it, int32_t S, float inv_len,
-                                              int32_t t, int32_t* s, int32_t* m) {
+__device__ __forceinline__ void rec_item(const RunRec& r, int32_t S, float inv_len, int32_t t, int32_t* s,
+                                         int32_t* m) {
     int32_t k, off;
-    if (t < it.len0) {
+    if (t < r.len0) {
         k = 0;
-        off = it.first_off + t;
+        off = r.first_off + t;
     } else {
-        const int32_t tt = t - it.len0;
+        const int32_t tt = t - r.len0;
         int32_t q = __float2int_rz((float)tt * inv_len);
         if ((q + 1) * r.len <= tt) ++q;
         else if (q * r.len > tt) --q;
         k = 1 + q;
         off = tt - q * r.len;
     }
-    *s = it.occ0 + k * S + off;
+    *s = r.occ0 + k * S + off;
     const int32_t mm = r.m0 + off;
     *m = mm >= S ? mm - S : mm;
 }
 
-// Enumerate runs for 32 points (lane = point) of tooth K, group g, pass p.
 template <typename Cell>
-__device__ __forceinline__ int warp_runs(const Surface& sf, const TileCtx<Cell>& tc, int K, int g,
-                                         int p, WarpRuns& wr) {
+__device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCtx<Cell>& tc, TileShared& ts) {
+    const int np = min(sf.n_passes, kPassCache);
+    const double y1 = tc.Y0 + (double)tc.tyc * sf.pitch;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const double yc = path_y(sf, p);
+        ts.ylo[p] = (float)(tc.Y0 - yc) - kMarginMm;
+        ts.yhi[p] = (float)(y1 - yc) + kMarginMm;
+        ts.dy[p] = (float)(yc - tc.Y0);
+    }
+    if (threadIdx.x == 0) {
+        const double d = sf.pass_x0 - tc.X0;
+        ts.dx_hi = (float)d;
+        ts.dx_lo = (float)(d - (double)ts.dx_hi);
+        ts.xlo = (float)(tc.X0 - sf.pass_x0) - kMarginMm;
+        ts.xhi = (float)(tc.X0 + (double)tc.txc * sf.pitch - sf.pass_x0) + kMarginMm;
+        ts.zhi = (float)(sf.stock_z - sf.z_ref) + kMarginMm;
+    }
+}
+
+// y band of pass p relative to the pass line, and the pass line relative to the tile
+__device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<uint32_t>& tc, const TileShared& ts,
+                                          int p, float* ylo, float* yhi, float* dy) {
+    if (p < kPassCache) {
+        *ylo = ts.ylo[p];
+        *yhi = ts.yhi[p];
+        *dy = ts.dy[p];
+    } else {
+        const double yc = path_y(sf, p);
+        *ylo = (float)(tc.Y0 - yc) - kMarginMm;
+        *yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
+        *dy = (float)(yc - tc.Y0);
+    }
+}
+
+template <typename Cell>
+__device__ __forceinline__ void pass_band_any(const Surface& sf, const TileCtx<Cell>& tc, const TileShared& ts,
+                                              int p, float* ylo, float* yhi) {
+    if (p < kPassCache) {
+        *ylo = ts.ylo[p];
+        *yhi = ts.yhi[p];
+    } else {
+        const double yc = path_y(sf, p);
+        *ylo = (float)(tc.Y0 - yc) - kMarginMm;
+        *yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
+    }
+}
+
+// Phase 1 of a warp task: lane = edge point j = 32 g + lane of tooth K. Each
+// lane enumerates its runs for pass p and stores them with their iteration
+// bookkeeping. Returns whether any lane has work.
+__device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& ts, float ylo, float yhi, int K,
+                                          int g, int p, WarpScratch& ws, float4 (&t4)[3]) {
     const int lane = threadIdx.x & 31;
     const int E = sf.E;
     const int j = g * 32 + lane;
     int nr = 0;
+    t4[0] = t4[1] = t4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j < E) {
-        const float4* t4 = sf.tool32 + 4 * (size_t)(K * E + j);
-        PointGeom geo = load_geom(t4);
+        const float4* tp = sf.tool32 + 4 * (size_t)(K * E + j);
+        t4[0] = tp[0];
+        t4[1] = tp[1];
+        t4[2] = tp[2];
+        const float4 t3 = tp[3];
+        PointGeom geo;
+        geo.wx = t4[0].z;
+        geo.wy = t4[1].z;
+        geo.wz = t4[2].x;
+        geo.amp_y = t4[2].y;
+        geo.mph_y = t4[2].z;
+        geo.amp_z = t4[2].w;
+        geo.mph_z = t3.x;
+        geo.amp_x = t3.y;
+        geo.mph_x = t3.z;
         TileFrame f;
-        const double yc = sf.pass_y0 + (double)p * sf.ae;
-        f.ylo = (float)(tc.Y0 - yc) - kMarginMm;
-        f.yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
-        f.zhi = (float)(sf.stock_z - sf.z_ref) + kMarginMm;
-        f.xlo = (float)(tc.X0 - sf.pass_x0) - kMarginMm;
-        f.xhi = (float)(tc.X0 + (double)tc.txc * sf.pitch - sf.pass_x0) + kMarginMm;
-        f.inv_fs = (float)(1.0 / sf.fs);
+        f.ylo = ylo;
+        f.yhi = yhi;
+        f.zhi = ts.zhi;
+        f.xlo = ts.xlo;
+        f.xhi = ts.xhi;
+        f.inv_fs = sf.inv_fs_f;
         f.s0 = p * sf.steps_per_pass;
         f.n_steps = sf.steps_per_pass;
-        f.dth = (float)sf.dtheta;
-        f.inv_dth = (float)(1.0 / sf.dtheta);
+        f.dth = sf.dth_f;
+        f.inv_dth = sf.inv_dth_f;
         f.S = sf.S;
-        nr = point_runs(geo, f, wr.run[lane]);
+        Run runs[kMaxArcs];
+        const int n = point_runs(geo, f, runs);
+        for (int a = 0; a < n; ++a) {
+            const RunIter it = run_iter(runs[a], sf.S);
+            if (it.total <= 0) continue;
+            RunRec& r = ws.run[lane][nr++];
+            r.m0 = runs[a].m0;
+            r.len = runs[a].len;
+            r.occ0 = it.occ0;
+            r.first_off = it.first_off;
+            r.len0 = it.len0;
+            r.total = it.total;
+            r.span = runs[a].s_hi - runs[a].s_lo;
+        }
     }
-    wr.n[lane] = nr;
+    ws.n[lane] = nr;
     __syncwarp();
     return __any_sync(0xffffffffu, nr > 0);
 }
 
 // ---------------------------------------------------------------------------
-// FP32 path: tile-local FP32 poses, FP64 re-binning near cell boundaries.
+// FP32 path: tile-local FP32 poses; points whose FP32 cell is ambiguous and
+// that could lower a cell are re-binned in FP64, 32 at a time.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void update32(uint32_t* cells, int idx, float zrel, Counters& c) {
     const uint32_t e = enc32(__float_as_uint(zrel));
@@ -313,86 +412,146 @@ __device__ __forceinline__ void update32(uint32_t* cells, int idx, float zrel, C
     }
 }
 
-__device__ void sweep_point32(const Surface& sf, const TileCtx<uint32_t>& tc, int K, int j, int p,
-                              const WarpRuns& wr, int o, Counters& cnt) {
+// Re-bin queued points in FP64 (lanes < count take one entry each).
+__device__ __noinline__ void rebin_flush(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws, int p,
+                                         int count, Counters& cnt) {
     const int lane = threadIdx.x & 31;
-    const int E = sf.E, NE = sf.n_teeth * E;
-    const int idx = K * E + j;
-    const float4* t4 = sf.tool32 + 4 * (size_t)idx;
-    const float4 a = t4[0], b = t4[1];
-    const float wz = t4[2].x;
-    const float ux = a.x, vx = a.y, wx = a.z, uz = a.w;
-    const float uy = b.x, vy = b.y, wy = b.z, vz = b.w;
-    const float zb = (float)(sf.z_ref - sf.stock_z) + wz;
-    const double yc = sf.pass_y0 + (double)p * sf.ae;
-    const float dy = (float)(yc - tc.Y0);
-    const float fs32 = (float)sf.fs;
-    const float inv_pitch = (float)(1.0 / sf.pitch);
-    const float g = sf.guard_cells;
+    if (lane < count) {
+        const int NE = sf.n_teeth * sf.E;
+        const int s = ws.q_s[lane], m = ws.q_m[lane], idx = ws.q_idx[lane];
+        const Vec9 v = load_vec9(sf.tool64, NE, idx);
+        const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, s - p * sf.steps_per_pass), path_y(sf, p), sf.z_ref);
+        ++cnt.rebinned;
+        if (P.z < sf.stock_z) {
+            const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tc.tx * sf.tile_x;
+            const long long kg = bin64(P.y, sf.y0, sf.inv_pitch) - (long long)tc.ty * sf.tile_y;
+            if (ig >= 0 && ig < tc.txc && kg >= 0 && kg < tc.tyc)
+                update32(tc.cells, (int)kg * sf.tile_x + (int)ig, (float)(P.z - sf.stock_z), cnt);
+        }
+    }
+    __syncwarp();
+    // move the tail down
+    const int rest = count > 32 ? count - 32 : 0;
+    int s = 0, m = 0, idx = 0;
+    if (lane < rest) {
+        s = ws.q_s[32 + lane];
+        m = ws.q_m[32 + lane];
+        idx = ws.q_idx[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        ws.q_s[lane] = s;
+        ws.q_m[lane] = m;
+        ws.q_idx[lane] = idx;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<uint32_t>& tc, const TileShared& ts,
+                                             float dyp, int K, int g, int p, WarpScratch& ws,
+                                             const float4 (&t4)[3], Counters& cnt) {
+    const int lane = threadIdx.x & 31;
     const int S = sf.S;
     const int s0 = p * sf.steps_per_pass;
+    const float fs32 = sf.fs_f, fs_hi = sf.fs_hi, fs_lo = sf.fs_lo;
+    const float inv_pitch = sf.inv_pitch_f;
     const float2* __restrict__ ph32 = sf.ph32;
     const int tile_x = sf.tile_x;
     uint32_t* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
-    for (int ai = 0; ai < wr.n[o]; ++ai) {
-        const Run r = wr.run[o][ai];
-        const RunIter it = run_iter(r, S);
-        if (it.total <= 0) continue;
-        const float inv_len = 1.0f / (float)r.len;
-        const int32_t sA = it.occ0 + it.first_off;
-        const float dxA = (float)((sf.pass_x0 - tc.X0) + (double)(sA - s0) * sf.fs);
-        for (int t = lane; t < it.total; t += 32) {
-            int32_t s, m;
-            run_item_fast(r, it, S, inv_len, t, &s, &m);
-            const float2 cs = __ldg(ph32 + m);
-            ++cnt.evaluated;
-            const float z = fmaf(cs.x, uz, fmaf(cs.y, vz, zb));
-            if (!(z < 0.f)) continue;
-            const float dx = fmaf((float)(s - sA), fs32, dxA);
-            const float xl = dx + fmaf(cs.x, ux, fmaf(cs.y, vx, wx));
-            const float yl = dy + fmaf(cs.x, uy, fmaf(cs.y, vy, wy));
-            const float fx = xl * inv_pitch, fy = yl * inv_pitch;
-            const float flx = floorf(fx), fly = floorf(fy);
-            const float rx = fx - flx, ry = fy - fly;
-            const int i = (int)flx, k = (int)fly;
-            const bool amb = rx < g || rx > 1.f - g || ry < g || ry > 1.f - g;
-            if (!amb) {
-                if ((unsigned)i < (unsigned)txc && (unsigned)k < (unsigned)tyc) {
-                    ++cnt.cutting;
-                    update32(cells, k * tile_x + i, z, cnt);
+    const float u24 = 5.9604644775390625e-8f;
+    const float pitch_f = (float)sf.pitch;
+    int qn = 0;  // queued re-bins (warp-uniform)
+    for (int o = 0; o < 32; ++o) {
+        const int nr = ws.n[o];
+        if (nr == 0) continue;
+        // the point's pose vectors, from the lane that loaded them
+        const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
+        const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
+        const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
+        const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
+        const float wz = __shfl_sync(0xffffffffu, t4[2].x, o);
+        const float amp_xy = fmaxf(sqrtf(ux * ux + vx * vx), sqrtf(uy * uy + vy * vy));
+        const float amp_z = sqrtf(uz * uz + vz * vz);
+        const float zb = sf.zrel_f + wz;
+        // FP32 error bounds of z and of the tile-local x, y (see the error
+        // model in the documentation of the precision scheme), 1.5x margin
+        const float eps_z = 1.5f * u24 * (5.f * amp_z + 4.f * (fabsf(sf.zrel_f) + fabsf(wz)));
+        const float pt_err = 6.f * amp_xy + 3.f * (fabsf(wx) + fabsf(wy) + fabsf(wz)) +
+                             3.f * (float)max(tile_x, sf.tile_y) * pitch_f;
+        const int idx = K * sf.E + g * 32 + o;
+        for (int a = 0; a < nr; ++a) {
+            const RunRec r = ws.run[o][a];
+            const int32_t sA = r.occ0 + r.first_off;
+            const float dxA = df_affine(ts.dx_hi, ts.dx_lo, sA - s0, fs_hi, fs_lo);
+            const float span_mm = (float)r.span * fs32;
+            const float g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * inv_pitch + sf.guard_extra;
+            const float inv_len = 1.0f / (float)r.len;
+            for (int base = 0; base < r.total; base += 32) {
+                const int t = base + lane;
+                bool want_rebin = false;
+                int32_t s = 0, m = 0;
+                if (t < r.total) {
+                    rec_item(r, S, inv_len, t, &s, &m);
+                    const float2 cs = __ldg(ph32 + m);
+                    ++cnt.evaluated;
+                    const float z = fmaf(cs.x, uz, fmaf(cs.y, vz, zb));
+                    if (z < 0.f) {
+                        const float dx = fmaf((float)(s - sA), fs32, dxA);
+                        const float xl = dx + fmaf(cs.x, ux, fmaf(cs.y, vx, wx));
+                        const float yl = dyp + fmaf(cs.x, uy, fmaf(cs.y, vy, wy));
+                        const float fx = xl * inv_pitch, fy = yl * inv_pitch;
+                        const float flx = floorf(fx), fly = floorf(fy);
+                        const float rx = fx - flx, ry = fy - fly;
+                        const int i = (int)flx, k = (int)fly;
+                        const bool in = (unsigned)i < (unsigned)txc && (unsigned)k < (unsigned)tyc;
+                        if (in) ++cnt.cutting;
+                        const bool amb = rx < g_cells || rx > 1.f - g_cells || ry < g_cells || ry > 1.f - g_cells;
+                        if (!amb) {
+                            if (in) update32(cells, k * tile_x + i, z, cnt);
+                        } else {
+                            // candidate cells of the ambiguous point inside this tile: re-bin only if
+                            // the point could lower one of them
+                            const int i0 = max(rx < g_cells ? i - 1 : i, 0), i1 = min(rx > 1.f - g_cells ? i + 1 : i, txc - 1);
+                            const int k0 = max(ry < g_cells ? k - 1 : k, 0), k1 = min(ry > 1.f - g_cells ? k + 1 : k, tyc - 1);
+                            const uint32_t elo = enc32(__float_as_uint(z - eps_z));
+                            for (int kk = k0; kk <= k1 && !want_rebin; ++kk)
+                                for (int ii = i0; ii <= i1; ++ii)
+                                    if (elo < cells[kk * tile_x + ii]) { want_rebin = true; break; }
+                        }
+                    }
                 }
-                continue;
+                // queue the re-bins of this iteration (warp-cooperative)
+                const unsigned bal = __ballot_sync(0xffffffffu, want_rebin);
+                if (bal) {
+                    const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                    if (want_rebin) {
+                        ws.q_s[pos] = s;
+                        ws.q_m[pos] = m;
+                        ws.q_idx[pos] = idx;
+                    }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        rebin_flush(sf, tc, ws, p, qn, cnt);
+                        qn -= 32;
+                    }
+                }
             }
-            // ambiguous: could the point be in this tile at all?
-            const int i0 = rx < g ? i - 1 : i, i1 = rx > 1.f - g ? i + 1 : i;
-            const int k0 = ry < g ? k - 1 : k, k1 = ry > 1.f - g ? k + 1 : k;
-            if (i1 < 0 || i0 >= txc || k1 < 0 || k0 >= tyc) continue;
-            // re-bin in FP64 with the global sampling boundaries
-            ++cnt.rebinned;
-            const Vec9 v = load_vec9(sf.tool64, NE, idx);
-            const Pose64 P = pose64(v, __ldg(sf.ph64 + m), path_x(sf, s - s0), yc, sf.z_ref);
-            if (!(P.z < sf.stock_z)) continue;
-            const long long ig = bin64(P.x, sf.x0, 1.0 / sf.pitch) - (long long)tc.tx * tile_x;
-            const long long kg = bin64(P.y, sf.y0, 1.0 / sf.pitch) - (long long)tc.ty * sf.tile_y;
-            if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
-            ++cnt.cutting;
-            update32(cells, (int)kg * tile_x + (int)ig, (float)(P.z - sf.stock_z), cnt);
         }
     }
+    if (qn > 0) rebin_flush(sf, tc, ws, p, qn, cnt);
 }
 
 // ---------------------------------------------------------------------------
 // FP64 path: all pose and binning arithmetic in FP64, global coordinates.
 // ---------------------------------------------------------------------------
-__device__ void sweep_point64(const Surface& sf, const TileCtx<unsigned long long>& tc, int K, int j,
-                              int p, const WarpRuns& wr, int o, Counters& cnt) {
+__device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<unsigned long long>& tc, int K, int g,
+                                             int p, WarpScratch& ws, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const int E = sf.E, NE = sf.n_teeth * E;
-    const int idx = K * E + j;
-    const Vec9 v = load_vec9(sf.tool64, NE, idx);
-    const double yc = sf.pass_y0 + (double)p * sf.ae;
-    const double inv_pitch = 1.0 / sf.pitch;
+    const double yc = path_y(sf, p);
+    const double inv_pitch = sf.inv_pitch;
     const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock_z;
     const int S = sf.S;
     const int s0 = p * sf.steps_per_pass;
@@ -401,28 +560,32 @@ __device__ void sweep_point64(const Surface& sf, const TileCtx<unsigned long lon
     const int tile_x = sf.tile_x;
     unsigned long long* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
-    for (int ai = 0; ai < wr.n[o]; ++ai) {
-        const Run r = wr.run[o][ai];
-        const RunIter it = run_iter(r, S);
-        if (it.total <= 0) continue;
-        const float inv_len = 1.0f / (float)r.len;
-        for (int t = lane; t < it.total; t += 32) {
-            int32_t s, m;
-            run_item_fast(r, it, S, inv_len, t, &s, &m);
-            const double2 cs = __ldg(ph64 + m);
-            ++cnt.evaluated;
-            const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
-            if (!(z < stock)) continue;
-            const Pose64 P = pose64(v, cs, path_x(sf, s - s0), yc, zr);
-            const long long ig = bin64(P.x, x0, inv_pitch) - ib;
-            const long long kg = bin64(P.y, y0, inv_pitch) - kb;
-            if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
-            ++cnt.cutting;
-            const unsigned long long e = enc64((unsigned long long)__double_as_longlong(P.z));
-            unsigned long long* cell = cells + (int)kg * tile_x + (int)ig;
-            if (e < *cell) {
-                atomicMin(cell, e);
-                ++cnt.atomics;
+    for (int o = 0; o < 32; ++o) {
+        const int nr = ws.n[o];
+        if (nr == 0) continue;
+        const int idx = K * E + g * 32 + o;
+        const Vec9 v = load_vec9(sf.tool64, NE, idx);
+        for (int a = 0; a < nr; ++a) {
+            const RunRec r = ws.run[o][a];
+            const float inv_len = 1.0f / (float)r.len;
+            for (int t = lane; t < r.total; t += 32) {
+                int32_t s, m;
+                rec_item(r, S, inv_len, t, &s, &m);
+                const double2 cs = __ldg(ph64 + m);
+                ++cnt.evaluated;
+                const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
+                if (!(z < stock)) continue;
+                const Pose64 P = pose64(v, cs, path_x(sf, s - s0), yc, zr);
+                const long long ig = bin64(P.x, x0, inv_pitch) - ib;
+                const long long kg = bin64(P.y, y0, inv_pitch) - kb;
+                if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
+                ++cnt.cutting;
+                const unsigned long long e = enc64((unsigned long long)__double_as_longlong(P.z));
+                unsigned long long* cell = cells + (int)kg * tile_x + (int)ig;
+                if (e < *cell) {
+                    atomicMin(cell, e);
+                    ++cnt.atomics;
+                }
             }
         }
     }
@@ -442,18 +605,18 @@ __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) 
 // stride, or from *queue when it is not NULL. Inside a tile, warps take
 // (pass, tooth, 32-point group) tasks from a shared counter.
 template <bool FP64>
-__global__ void __launch_bounds__(256) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
-                                                    const int* __restrict__ tile_base,
-                                                    int total_tiles, int* queue,
-                                                    long long* counters) {
+__global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
+                                                       const int* __restrict__ tile_base, int total_tiles,
+                                                       int* queue, long long* counters) {
     using Cell = typename std::conditional<FP64, unsigned long long, uint32_t>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_task, s_tile;
+    __shared__ TileShared ts;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    WarpRuns* wruns = reinterpret_cast<WarpRuns*>(smem);
-    Cell* cells = reinterpret_cast<Cell*>(smem + sizeof(WarpRuns) * nwarps);
-    WarpRuns& wr = wruns[warp];
+    WarpScratch* wscr = reinterpret_cast<WarpScratch*>(smem);
+    Cell* cells = reinterpret_cast<Cell*>(smem + sizeof(WarpScratch) * nwarps);
+    WarpScratch& ws = wscr[warp];
     Counters cnt = {0, 0, 0, 0};
 
     int iter = 0;
@@ -482,15 +645,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const Surface* __restrict__ 
         if constexpr (FP64) init = (Cell)enc64((unsigned long long)__double_as_longlong(sf.stock_z));
         else init = (Cell)enc32(__float_as_uint(0.0f));  // FP32 cells hold heights relative to the stock
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cells[c] = init;
+        fill_tile_shared(sf, tc, ts);
         __syncthreads();
 
         const int G = (sf.E + 31) / 32;
         const int n_tasks = sf.n_passes * sf.n_teeth * G;
-        const double tile_y1 = tc.Y0 + (double)tc.tyc * sf.pitch;
         const double tile_x1 = tc.X0 + (double)tc.txc * sf.pitch;
         const double pass_x1 = sf.pass_x0 + (double)(sf.steps_per_pass - 1) * sf.fs;
         const bool x_miss = (pass_x1 + sf.reach_x < tc.X0 - 1e-3) || (sf.pass_x0 - sf.reach_x > tile_x1 + 1e-3);
-        const float zhi = (float)(sf.stock_z - sf.z_ref) + kMarginMm;
         while (!x_miss) {
             int task = 0;
             if (lane == 0) task = atomicAdd(&s_task, 1);
@@ -499,15 +661,18 @@ __global__ void __launch_bounds__(256) sweep_kernel(const Surface* __restrict__ 
             const int p = task / (sf.n_teeth * G);
             const int rem = task - p * sf.n_teeth * G;
             const int K = rem / G, g = rem - K * G;
-            const double yc = sf.pass_y0 + (double)p * sf.ae;
+            float ylo, yhi;
+            pass_band_any(sf, tc, ts, p, &ylo, &yhi);
             const float4 gb = sf.groups[K * G + g];
-            const float ylo = (float)(tc.Y0 - yc) - kMarginMm, yhi = (float)(tile_y1 - yc) + kMarginMm;
-            if (gb.y < ylo || gb.x > yhi || gb.z >= zhi) continue;  // warp-uniform
-            if (!warp_runs(sf, tc, K, g, p, wr)) continue;
-            for (int o = 0; o < 32; ++o) {
-                if (wr.n[o] == 0) continue;
-                if constexpr (FP64) sweep_point64(sf, tc, K, g * 32 + o, p, wr, o, cnt);
-                else sweep_point32(sf, tc, K, g * 32 + o, p, wr, o, cnt);
+            if (gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi) continue;  // warp-uniform
+            float4 t4[3];
+            if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4)) continue;
+            if constexpr (FP64) {
+                sweep_task64(sf, tc, K, g, p, ws, cnt);
+            } else {
+                float yl2, yh2, dyp;
+                pass_band(sf, tc, ts, p, &yl2, &yh2, &dyp);
+                sweep_task32(sf, tc, ts, dyp, K, g, p, ws, t4, cnt);
             }
             __syncwarp();
         }
@@ -787,7 +952,7 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
 
 size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads) {
     const size_t cell = precision == 0 ? 8 : 4;
-    return sizeof(WarpRuns) * (size_t)(threads / 32) + cell * (size_t)tile_x * (size_t)tile_y;
+    return sizeof(WarpScratch) * (size_t)(threads / 32) + cell * (size_t)tile_x * (size_t)tile_y;
 }
 
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,

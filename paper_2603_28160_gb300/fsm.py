@@ -44,7 +44,7 @@ class ProcessDesc(C.Structure):
 
 class PredictOpts(C.Structure):
     _fields_ = [("tile_x", C.c_int32), ("tile_y", C.c_int32), ("block_threads", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("d_counters", C.c_void_p)]
+                ("ctas_per_sm", C.c_int32), ("d_counters", C.c_void_p), ("sweep_events", C.c_void_p * 2)]
 
 
 class RoughnessOut(C.Structure):
@@ -218,22 +218,28 @@ class Context:
 
     # -- single surface ---------------------------------------------------
     @staticmethod
-    def _opts(tile=None, threads=None, counters=None) -> Optional[PredictOpts]:
-        if tile is None and threads is None and counters is None:
+    def _opts(tile=None, threads=None, counters=None, events=None, ctas_per_sm=None) -> Optional[PredictOpts]:
+        if tile is None and threads is None and counters is None and events is None and ctas_per_sm is None:
             return None
         o = PredictOpts()
         if tile is not None:
             o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
         if threads is not None:
             o.block_threads = int(threads)
+        if ctas_per_sm is not None:
+            o.ctas_per_sm = int(ctas_per_sm)
         if counters is not None:
             o.d_counters = counters.data_ptr()
+        if events is not None:  # two torch.cuda.Event objects, already recorded once
+            o.sweep_events[0] = events[0].cuda_event
+            o.sweep_events[1] = events[1].cuda_event
         return o
 
     def predict_surface(self, tool: _Handle, proc: _Handle, out, tile=None, threads=None, counters=None,
-                        stream=None) -> None:
-        """Enqueue fsm_predict_surface writing into the CUDA tensor `out`."""
-        o = self._opts(tile, threads, counters)
+                        stream=None, events=None, ctas_per_sm=None) -> None:
+        """Enqueue fsm_predict_surface writing into the CUDA tensor `out`.
+        events: optional pair of torch.cuda.Event recorded around the sweep."""
+        o = self._opts(tile, threads, counters, events, ctas_per_sm)
         self._call("fsm_predict_surface", self.ptr, tool.ptr, proc.ptr, out.data_ptr(),
                    C.byref(o) if o is not None else None, _stream_ptr(stream))
 
@@ -260,16 +266,17 @@ class Context:
         return n, ta, pa, ha
 
     def predict_batch(self, tools, procs, outs, rough_buf=None, tile=None, threads=None, counters=None,
-                      stream=None) -> None:
+                      stream=None, events=None) -> None:
         n, ta, pa, ha = self._arrays(tools, procs, outs)
-        o = self._opts(tile, threads, counters)
+        o = self._opts(tile, threads, counters, events)
         self._call("fsm_predict_batch", self.ptr, n, ta, pa, ha,
                    rough_buf.data_ptr() if rough_buf is not None else None,
                    C.byref(o) if o is not None else None, _stream_ptr(stream))
 
-    def batch(self, tools, procs, outs, rough_buf=None, tile=None, threads=None, counters=None) -> "Batch":
+    def batch(self, tools, procs, outs, rough_buf=None, tile=None, threads=None, counters=None,
+              events=None) -> "Batch":
         n, ta, pa, ha = self._arrays(tools, procs, outs)
-        o = self._opts(tile, threads, counters)
+        o = self._opts(tile, threads, counters, events)
         p = _P()
         self._call("fsm_batch_create", self.ptr, n, ta, pa, ha,
                    rough_buf.data_ptr() if rough_buf is not None else None,
