@@ -211,6 +211,29 @@ fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision,
                          int32_t ny, int32_t n_rows, int32_t n_cols, fsm_roughness_out* d_out,
                          void* stream);
 
+/* Roughness without any device allocation (the paper has no counterpart:
+ * this exists for callers of the library that must not allocate device
+ * memory once they are running -- a host that has already handed all device
+ * memory to its own pool, a control loop with a fixed memory footprint, or
+ * code that may not call cudaMalloc/cudaMallocAsync at all). Same result as
+ * fsm_roughness, computed by the same kernels, but the per-chunk partial
+ * sums live in a fixed array of about 0.9 MiB that the library reserves in
+ * device memory on every GPU that loads it, until the process exits.
+ *   Limit: nx * ny <= 536870912 (2^29) cells; larger maps fail with
+ *          FSM_E_INVALID and a message saying so.
+ *   The first call on a device looks the array up on that device (with it
+ *   made current); make that first call before any stream capture.
+ *   All calls on a device share the one array: calls whose kernels overlap on
+ *   the GPU (e.g. on two streams) race and give wrong results; order them on
+ *   one stream or synchronise between them. The array keeps the last call's
+ *   contents; no part of it needs to start at zero (every word a call reads
+ *   is written earlier in the same call).
+ * Arguments as for fsm_roughness; no cudaMalloc, cudaFree or allocating
+ * library call is made. */
+fsm_status fsm_roughness_noalloc(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx,
+                                 int32_t ny, int32_t n_rows, int32_t n_cols,
+                                 fsm_roughness_out* d_out, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Batched prediction                                                      */
 /* ---------------------------------------------------------------------- */

@@ -18,7 +18,10 @@
 
 #include <type_traits>
 
+#include <mutex>
+
 #include "fsm_device.cuh"
+#include "fsm_host.h"
 #include "fsm_internal.h"
 
 namespace fsm {
@@ -1032,3 +1035,71 @@ cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_j
 }
 
 }  // namespace fsm
+
+// ===========================================================================
+// Allocation-free roughness: the same launches as fsm_roughness with the
+// scratch (job record, chunk prefix, per-chunk partials) in a fixed device
+// array, for callers that may not allocate device memory while running.
+// ===========================================================================
+namespace fsm {
+
+constexpr size_t kNoAllocMaxCells = (size_t)1 << 29;
+constexpr size_t kNoAllocChunks = (kNoAllocMaxCells + kChunk - 1) / kChunk;
+constexpr size_t kNoAllocBytes = 512 + 7 * sizeof(double) * kNoAllocChunks;  // about 0.9 MiB
+
+// One per device that loads the library, kept until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the array, looked up once per device with that device
+// current (in host code the symbol names a host-side stand-in, not memory
+// the GPU can use).
+static char* noalloc_scratch(int device, cudaError_t* err) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static char* addr[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[device]) {
+        void* p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        addr[device] = (char*)p;
+    }
+    *err = cudaSuccess;
+    return addr[device];
+}
+
+}  // namespace fsm
+
+extern "C" fsm_status fsm_roughness_noalloc(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx,
+                                            int32_t ny, int32_t n_rows, int32_t n_cols,
+                                            fsm_roughness_out* d_out, void* stream) {
+    using namespace fsm;
+    if (!ctx || !d_heights || !d_out) return fail(FSM_E_INVALID, "ctx/d_heights/d_out is NULL");
+    if (precision != FSM_FP64 && precision != FSM_FP32) return fail(FSM_E_INVALID, "unknown precision");
+    if (nx < 1 || ny < 1) return fail(FSM_E_INVALID, "nx, ny must be >= 1");
+    if (n_rows < 0 || n_cols < 0 || n_rows > FSM_MAX_PROFILES || n_cols > FSM_MAX_PROFILES)
+        return fail(FSM_E_INVALID, "0 <= n_rows, n_cols <= 16");
+    const size_t n = (size_t)nx * (size_t)ny;
+    if (n > kNoAllocMaxCells)
+        return fail(FSM_E_INVALID, "fsm_roughness_noalloc handles at most 2^29 cells (" +
+                                       std::to_string(kNoAllocMaxCells) + "); this map has " + std::to_string(n));
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    char* ws = noalloc_scratch(ctx->device, &e);
+    if (!ws) return cuda_fail(e, "cudaGetSymbolAddress (no-alloc scratch)");
+    RoughJob jb;
+    jb.h = d_heights;
+    jb.n = n;
+    jb.nx = nx;
+    jb.ny = ny;
+    jb.n_rows = n_rows;
+    jb.n_cols = n_cols;
+    jb.out = d_out;
+    if ((e = launch_roughness_one(precision, jb, ws, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(e, "roughness kernels (no-alloc)");
+    return FSM_OK;
+}

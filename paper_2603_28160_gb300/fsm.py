@@ -76,6 +76,7 @@ SIGNATURES = {
     "fsm_destroy_process": [_P, _P],
     "fsm_predict_surface": [_P, _P, _P, _P, C.POINTER(PredictOpts), _P],
     "fsm_roughness": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P],
+    "fsm_roughness_noalloc": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P],
     "fsm_predict_batch": [_P, C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), _P,
                           C.POINTER(PredictOpts), _P],
     "fsm_batch_create": [_P, C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), _P,
