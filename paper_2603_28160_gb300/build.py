@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-            "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-lpthread"]
+            "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-Xlinker", "-z,defs", "-lpthread"]
         subprocess.check_call(cmd)
         os.replace(tmp, LIB)
     return LIB

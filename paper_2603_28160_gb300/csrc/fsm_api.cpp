@@ -153,6 +153,8 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     off += align256((size_t)s->S * sizeof(double2));
     s->groups = (float4*)(base + off);
     off += align256(G * sizeof(float4));
+    s->plan_part = (double*)(base + off);
+    off += align256(sizeof(double) * 4 * kPlanParts);
     return off;
 }
 
@@ -182,7 +184,12 @@ fsm_status fsm_create_context(int device, fsm_ctx** out) {
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
     if (prop.major * 10 + prop.minor < 100)
         return fail(FSM_E_CUDA, "the library is built for sm_103a (Blackwell Ultra)");
-    // make sure our kernels are loadable on this device
+    // make sure our kernels are loadable on this device and may use all of
+    // its opt-in shared memory
+    if ((e = fsm::sweep_allow_smem(prop.sharedMemPerBlockOptin)) != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "kernel image not loadable on this device");
+    }
     size_t smem = fsm::sweep_smem_bytes(FSM_FP32, 8, 8, 256);
     if (fsm::sweep_blocks_per_sm(FSM_FP32, 256, smem) <= 0) {
         cudaGetLastError();

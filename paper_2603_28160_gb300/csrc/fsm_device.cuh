@@ -33,6 +33,7 @@ namespace fsm {
 constexpr int kMaxTeeth = 16;
 constexpr int kMaxArcs = 4;        // per edge point and pass after merging
 constexpr float kMarginMm = 2e-5f; // enumeration slack in x, y, z (20 nm)
+constexpr int kPlanParts = 64;     // max planning blocks per surface
 
 // Per-surface plan. The host fills the inputs and table pointers; the plan
 // kernel fills the derived block and the tables.
@@ -57,6 +58,7 @@ struct Surface {
     float2* ph32;     // [S] (cos, sin) of Theta_m
     double2* ph64;    // [S]
     float4* groups;   // [N * ceil(E/32)]: (min P_y, max P_y, min P_z, 0) over 32 points
+    double* plan_part;  // [kPlanParts][4]: per planning block, lowest z, x and y reach
     void* heights;    // output map
     // ---- derived (plan kernel) ----
     double z_ref, fs, dtheta;       // reference height, feed per step, step angle (rad)

@@ -15,6 +15,7 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
 
 size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads);
 int sweep_blocks_per_sm(int precision, int threads, size_t smem);
+cudaError_t sweep_allow_smem(size_t max_bytes);
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,

@@ -31,59 +31,81 @@ namespace fsm {
 // ===========================================================================
 __device__ __forceinline__ double deg2rad(double d) { return d * (3.14159265358979323846 / 180.0); }
 
+__device__ __forceinline__ double block_min_d(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmin(r, sh[w]);
+    return r;
+}
+__device__ __forceinline__ float block_max_f(float v, float* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
+    return r;
+}
+
+// Tables of surface blockIdx.x; gridDim.y blocks share its edge points and
+// phase entries. A single surface may arrive by value (`one`, graph-capture
+// friendly); block (0,0) then stores it for the kernels that follow.
 __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surface one, int use_one) {
     const int sidx = blockIdx.x;
     if (sidx >= n) return;
-    Surface* sf = surfs + sidx;
-    if (use_one) {  // a single surface arrives by value (graph-capture friendly)
-        if (threadIdx.x == 0) *sf = one;
-        __syncthreads();
-    }
+    const Surface& sf = use_one ? one : surfs[sidx];
+    if (use_one && blockIdx.y == 0 && threadIdx.x == 0) surfs[sidx] = one;
     __shared__ double A[9];
     __shared__ double kap[2];
-    __shared__ float red_lo[256], red_rx[256], red_ry[256];
+    __shared__ double shd[32];
+    __shared__ float shf[32];
     const int tid = threadIdx.x;
-    const int N = sf->n_teeth, E = sf->E, S = sf->S;
-    const double R = 0.5 * sf->diameter;
-    const double sigma = (double)sf->rot_sense;
-    const double dth = deg2rad(sf->rot_step_deg);
+    const int N = sf.n_teeth, E = sf.E, S = sf.S;
+    const double R = 0.5 * sf.diameter;
+    const double sigma = (double)sf.rot_sense;
+    const double dth = deg2rad(sf.rot_step_deg);
     if (tid == 0) {
-        double L = deg2rad(sf->lead_deg), T = deg2rad(sf->tilt_deg);
+        double L = deg2rad(sf.lead_deg), T = deg2rad(sf.tilt_deg);
         double cL = cos(L), sL = sin(L), cT = cos(T), sT = sin(T);
         // A = Rx(-tilt) Ry(lead): the tool axis leans toward +X by lead, +Y by tilt
         A[0] = cL;        A[1] = 0.0; A[2] = sL;
         A[3] = -sT * sL;  A[4] = cT;  A[5] = sT * cL;
         A[6] = -cT * sL;  A[7] = -sT; A[8] = cT * cL;
         double tau = acos(fmin(1.0, A[8]));
-        double c = fmin(1.0, fmax(-1.0, (R - sf->ap) / R));
+        double c = fmin(1.0, fmax(-1.0, (R - sf.ap) / R));
         double half = acos(c);
         kap[0] = fmax(0.0, tau - half);
         kap[1] = fmin(0.5 * 3.14159265358979323846, tau + half);
     }
     __syncthreads();
     const int NE = N * E;
-    float lo_min = 3.0e38f, rx = 0.f, ry = 0.f;
-    for (int idx = tid; idx < NE; idx += blockDim.x) {
+    const int first = blockIdx.y * blockDim.x + tid, stride = gridDim.y * blockDim.x;
+    double zlo = 1e300;
+    float rx = 0.f, ry = 0.f;
+    for (int idx = first; idx < NE; idx += stride) {
         const int K = idx / E, j = idx - K * E;
         double r, h;
-        if (sf->kind == 0) {  // flat: bottom edge then flank
-            if (j < sf->n_end) {
-                r = R * ((double)j / (double)(sf->n_end - 1));
+        if (sf.kind == 0) {  // flat: bottom edge then flank
+            if (j < sf.n_end) {
+                r = R * ((double)j / (double)(sf.n_end - 1));
                 h = 0.0;
             } else {
                 r = R;
-                h = sf->ap * ((double)(j - sf->n_end) / (double)(sf->n_edge - 1));
+                h = sf.ap * ((double)(j - sf.n_end) / (double)(sf.n_edge - 1));
             }
         } else {              // ball: uniform in polar angle over the engaged cap
             double kappa = kap[0] + (kap[1] - kap[0]) * ((double)j / (double)(E - 1));
             r = R * sin(kappa);
             h = R * (1.0 - cos(kappa));
         }
-        double psi = h * tan(deg2rad(sf->helix_deg[K])) / R;   // helix lag
-        double alpha = -deg2rad(sf->tooth_deg[K]) - sigma * psi;
-        double lam = deg2rad(sf->runout_phase_deg);
-        double qx = r * cos(alpha) + sf->runout_mm * cos(lam);
-        double qy = r * sin(alpha) + sf->runout_mm * sin(lam);
+        double psi = h * tan(deg2rad(sf.helix_deg[K])) / R;   // helix lag
+        double alpha = -deg2rad(sf.tooth_deg[K]) - sigma * psi;
+        double lam = deg2rad(sf.runout_phase_deg);
+        double qx = r * cos(alpha) + sf.runout_mm * cos(lam);
+        double qy = r * sin(alpha) + sf.runout_mm * sin(lam);
         double qz = h;
         double u[3], v[3], w[3];
         for (int d = 0; d < 3; ++d) {
@@ -91,7 +113,7 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
             v[d] = A[3 * d + 1] * qx - A[3 * d] * qy;
             w[d] = A[3 * d + 2] * qz;
         }
-        double* t64 = sf->tool64;
+        double* t64 = sf.tool64;
         t64[0 * NE + idx] = u[0]; t64[1 * NE + idx] = u[1]; t64[2 * NE + idx] = u[2];
         t64[3 * NE + idx] = v[0]; t64[4 * NE + idx] = v[1]; t64[5 * NE + idx] = v[2];
         t64[6 * NE + idx] = w[0]; t64[7 * NE + idx] = w[1]; t64[8 * NE + idx] = w[2];
@@ -100,78 +122,84 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
             double a = sqrt(u[d] * u[d] + v[d] * v[d]);
             double delta = atan2(v[d], u[d]);
             // Theta_m - delta = sense*dth*(m - mph)
-            double m = sigma * (delta - deg2rad(sf->phase0_deg)) / dth;
+            double m = sigma * (delta - deg2rad(sf.phase0_deg)) / dth;
             m = fmod(m, (double)S);
             if (m < 0.0) m += (double)S;
             amp[d] = (float)a;
             mph[d] = (float)m;
         }
-        float4* t32 = sf->tool32 + 4 * (size_t)idx;
+        float4* t32 = sf.tool32 + 4 * (size_t)idx;
         t32[0] = make_float4((float)u[0], (float)v[0], (float)w[0], (float)u[2]);
         t32[1] = make_float4((float)u[1], (float)v[1], (float)w[1], (float)v[2]);
         t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
         t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
-        double zlow = w[2] - sqrt(u[2] * u[2] + v[2] * v[2]);
-        lo_min = fminf(lo_min, (float)zlow);
+        // lowest z of the point over a turn (exact FP64; min is order-free)
+        zlo = fmin(zlo, w[2] - sqrt(u[2] * u[2] + v[2] * v[2]));
         rx = fmaxf(rx, (float)(fabs(w[0]) + sqrt(u[0] * u[0] + v[0] * v[0])));
         ry = fmaxf(ry, (float)(fabs(w[1]) + sqrt(u[1] * u[1] + v[1] * v[1])));
     }
-    red_lo[tid] = lo_min;
-    red_rx[tid] = rx;
-    red_ry[tid] = ry;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (tid < o) {
-            red_lo[tid] = fminf(red_lo[tid], red_lo[tid + o]);
-            red_rx[tid] = fmaxf(red_rx[tid], red_rx[tid + o]);
-            red_ry[tid] = fmaxf(red_ry[tid], red_ry[tid + o]);
-        }
-        __syncthreads();
-    }
-    // z_ref needs the exact FP64 lowest point: recompute it deterministically
-    __shared__ double zlo_exact;
-    if (tid == 0) {
-        double best = 1e300;
-        for (int idx = 0; idx < NE; ++idx) {
-            double uz = sf->tool64[2 * NE + idx], vz = sf->tool64[5 * NE + idx],
-                   wz = sf->tool64[8 * NE + idx];
-            double zl = wz - sqrt(uz * uz + vz * vz);
-            if (zl < best) best = zl;
-        }
-        zlo_exact = best;
-    }
     // phase table
-    for (int m = tid; m < S; m += blockDim.x) {
-        double th = deg2rad(sf->phase0_deg + sigma * ((double)m * sf->rot_step_deg));
+    for (int m = first; m < S; m += stride) {
+        double th = deg2rad(sf.phase0_deg + sigma * ((double)m * sf.rot_step_deg));
         double sn, cs;
         sincos(th, &sn, &cs);
-        sf->ph64[m] = make_double2(cs, sn);
-        sf->ph32[m] = make_float2((float)cs, (float)sn);
+        sf.ph64[m] = make_double2(cs, sn);
+        sf.ph32[m] = make_float2((float)cs, (float)sn);
     }
-    __syncthreads();
-    // per 32-point group bounds for the warp-level quick reject
+    zlo = block_min_d(zlo, shd);
+    rx = block_max_f(rx, shf);
+    ry = block_max_f(ry, shf);
+    if (tid == 0) {
+        double* part = sf.plan_part + 4 * blockIdx.y;
+        part[0] = zlo;
+        part[1] = (double)rx;
+        part[2] = (double)ry;
+    }
+}
+
+// Reductions over the planning blocks, per-group bounds, derived scalars.
+__global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n, int parts) {
+    const int sidx = blockIdx.x;
+    if (sidx >= n) return;
+    Surface* sf = surfs + sidx;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int N = sf->n_teeth, E = sf->E, S = sf->S;
+    // per 32-point group bounds for the warp-level quick reject (warp per group)
     const int G = (E + 31) / 32;
-    for (int gi = tid; gi < N * G; gi += blockDim.x) {
+    for (int gi = warp; gi < N * G; gi += nw) {
         const int K = gi / G, g = gi - K * G;
+        const int j = g * 32 + lane;
         float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
-        for (int j = g * 32; j < min(E, g * 32 + 32); ++j) {
+        if (j < E) {
             const float4* t4 = sf->tool32 + 4 * (size_t)(K * E + j);
-            float wy = t4[1].z, ay = t4[2].y, wz = t4[2].x, az = t4[2].w;
-            ymin = fminf(ymin, wy - ay);
-            ymax = fmaxf(ymax, wy + ay);
-            zmin = fminf(zmin, wz - az);
+            const float wy = t4[1].z, ay = t4[2].y, wz = t4[2].x, az = t4[2].w;
+            ymin = wy - ay;
+            ymax = wy + ay;
+            zmin = wz - az;
         }
-        sf->groups[gi] = make_float4(ymin, ymax, zmin, 0.f);
+        for (int o = 16; o > 0; o >>= 1) {
+            ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+            ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+            zmin = fminf(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+        }
+        if (lane == 0) sf->groups[gi] = make_float4(ymin, ymax, zmin, 0.f);
     }
     if (tid == 0) {
-        const double zr = sf->stock_z - sf->ap - zlo_exact;
+        double zlo = 1e300, rx = 0.0, ry = 0.0;
+        for (int q = 0; q < parts; ++q) {
+            zlo = fmin(zlo, sf->plan_part[4 * q]);
+            rx = fmax(rx, sf->plan_part[4 * q + 1]);
+            ry = fmax(ry, sf->plan_part[4 * q + 2]);
+        }
+        const double dth = deg2rad(sf->rot_step_deg);
+        const double zr = sf->stock_z - sf->ap - zlo;
         const double fs = (double)N * sf->fz / (double)S;
         sf->z_ref = zr;
         sf->fs = fs;
         sf->dtheta = dth;
         sf->inv_pitch = 1.0 / sf->pitch;
-        sf->reach_x = red_rx[0];
-        sf->reach_y = red_ry[0];
+        sf->reach_x = (float)rx;
+        sf->reach_y = (float)ry;
         sf->zrel_f = (float)(zr - sf->stock_z);
         sf->fs_hi = (float)fs;
         sf->fs_lo = (float)(fs - (double)sf->fs_hi);
@@ -841,6 +869,124 @@ __global__ void __launch_bounds__(256) rough2_kernel(const RoughJob* __restrict_
     }
 }
 
+// FP32 maps: the same two passes with 16-byte loads; per-cell terms in FP32,
+// summed in FP32 over 32 cells and then folded into the FP64 sums (relative
+// error of a leaf <= 32 u ~ 2e-6, far inside the FP32 path's 1e-4 target;
+// FP64 maps keep FP64 throughout). The mean is used as a float pair so the
+// deviations keep full FP32 precision.
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+__global__ void __launch_bounds__(256) rough1_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                         const int* __restrict__ chunk_base, double* part) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    size_t lo, hi;
+    chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
+    const float* h = reinterpret_cast<const float*>(jb.h);
+    double s = 0.0;
+    float mn = 3.0e38f, mx = -3.0e38f;
+    if (aligned16(h)) {
+        const size_t v0 = lo >> 2, v1 = hi >> 2;  // lo is a multiple of 4
+        const float4* h4 = reinterpret_cast<const float4*>(h);
+        size_t v = v0 + threadIdx.x;
+        while (v < v1) {
+            float leaf = 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r, v += blockDim.x) {
+                if (v < v1) {
+                    const float4 q = __ldg(h4 + v);
+                    leaf += (q.x + q.y) + (q.z + q.w);
+                    mn = fminf(mn, fminf(fminf(q.x, q.y), fminf(q.z, q.w)));
+                    mx = fmaxf(mx, fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)));
+                }
+            }
+            s += (double)leaf;
+        }
+        for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
+            const float z = h[i];
+            s += (double)z;
+            mn = fminf(mn, z);
+            mx = fmaxf(mx, z);
+        }
+    } else {
+        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const float z = h[i];
+            s += (double)z;
+            mn = fminf(mn, z);
+            mx = fmaxf(mx, z);
+        }
+    }
+    s = block_reduce<0>(s, sh);
+    const double dmn = block_reduce<1>((double)mn, sh);
+    const double dmx = block_reduce<2>((double)mx, sh);
+    if (threadIdx.x == 0) {
+        part[3 * (size_t)b] = s;
+        part[3 * (size_t)b + 1] = dmn;
+        part[3 * (size_t)b + 2] = dmx;
+    }
+}
+
+__device__ __forceinline__ void dev_terms(float z, float mu_hi, float mu_lo, float* a) {
+    const float d = (z - mu_hi) - mu_lo;
+    const float d2 = d * d;
+    a[0] += fabsf(d);
+    a[1] += d2;
+    a[2] = fmaf(d2, d, a[2]);
+    a[3] = fmaf(d2, d2, a[3]);
+}
+
+__global__ void __launch_bounds__(256) rough2_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                         const int* __restrict__ chunk_base, const double* part,
+                                                         double* part2) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    const double mu = job_mean(part, chunk_base[j], chunk_base[j + 1], jb.n, sh);
+    const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
+    size_t lo, hi;
+    chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
+    const float* h = reinterpret_cast<const float*>(jb.h);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (aligned16(h)) {
+        const size_t v0 = lo >> 2, v1 = hi >> 2;
+        const float4* h4 = reinterpret_cast<const float4*>(h);
+        size_t q = v0 + threadIdx.x;
+        while (q < v1) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int r = 0; r < 8; ++r, q += blockDim.x) {
+                if (q < v1) {
+                    const float4 z = __ldg(h4 + q);
+                    dev_terms(z.x, mu_hi, mu_lo, a);
+                    dev_terms(z.y, mu_hi, mu_lo, a);
+                    dev_terms(z.z, mu_hi, mu_lo, a);
+                    dev_terms(z.w, mu_hi, mu_lo, a);
+                }
+            }
+            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+        }
+        for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            dev_terms(h[i], mu_hi, mu_lo, a);
+            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+        }
+    } else {
+        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            dev_terms(h[i], mu_hi, mu_lo, a);
+            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+        }
+    }
+    for (int k = 0; k < 4; ++k) v[k] = block_reduce<0>(v[k], sh);
+    if (threadIdx.x == 0) {
+        double* o = part2 + 4 * (size_t)b;
+        o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
+    }
+}
+
 // Final: one block per job combines its chunks and writes the areal values.
 __global__ void __launch_bounds__(256) rough3_kernel(const RoughJob* __restrict__ jobs,
                                                      const int* __restrict__ chunk_base, const double* part,
@@ -949,7 +1095,14 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
     Surface dummy;
     if (one) dummy = *one;
     else memset(&dummy, 0, sizeof dummy);
-    plan_kernel<<<n, 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
+    // a lone surface spreads its FP64 table work over many blocks
+    int parts = 1;
+    if (one) {
+        const int work = one->n_teeth * one->E + one->S;
+        parts = max(1, min(kPlanParts, (work + 255) / 256));
+    }
+    plan_kernel<<<dim3(n, parts), 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
+    plan_finish_kernel<<<n, 256, 0, st>>>(d_surfs, n, parts);
     return cudaGetLastError();
 }
 
@@ -962,37 +1115,40 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,
                                 cudaStream_t st) {
-    if (precision == 0) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    if (precision == 0)
         sweep_kernel<true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles, d_queue,
                                                         d_counters);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    else
         sweep_kernel<false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles, d_queue,
                                                          d_counters);
-    }
     return cudaGetLastError();
+}
+
+// Allow the sweep kernels the device's whole opt-in shared memory; called once
+// per context with its device current (not a stream operation).
+template <typename K>
+static cudaError_t allow_dynamic_smem(K kernel, size_t max_bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    const size_t dyn = max_bytes > a.sharedSizeBytes ? max_bytes - a.sharedSizeBytes : 0;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+cudaError_t sweep_allow_smem(size_t max_bytes) {
+    cudaError_t e = allow_dynamic_smem(sweep_kernel<true>, max_bytes);
+    if (e != cudaSuccess) return e;
+    return allow_dynamic_smem(sweep_kernel<false>, max_bytes);
 }
 
 int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
     int nb = 0;
-    // dynamic shared memory above 48 KB needs the opt-in before any query
-    if (precision == 0) {
-        if (cudaFuncSetAttribute(sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<true>, threads, smem);
-    } else {
-        if (cudaFuncSetAttribute(sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false>, threads, smem);
-    }
-    return nb;
+    cudaError_t e;
+    if (precision == 0)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<true>, threads, smem);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false>, threads, smem);
+    return e == cudaSuccess ? nb : 0;
 }
 
 __global__ void rough_setup_one_kernel(RoughJob jb, int chunks, RoughJob* d_job, int* d_base) {
@@ -1026,8 +1182,8 @@ cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_j
         rough2_kernel<double><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
         if (max_profiles > 0) profiles_kernel<double><<<n_jobs * max_profiles, 256, 0, st>>>(d_jobs, max_profiles);
     } else {
-        rough1_kernel<float><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part);
-        rough2_kernel<float><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
+        rough1_f32_kernel<<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part);
+        rough2_f32_kernel<<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
         if (max_profiles > 0) profiles_kernel<float><<<n_jobs * max_profiles, 256, 0, st>>>(d_jobs, max_profiles);
     }
     rough3_kernel<<<n_jobs, 256, 0, st>>>(d_jobs, d_chunk_base, d_part, part2);

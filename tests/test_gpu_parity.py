@@ -79,16 +79,22 @@ def test_roughness_against_oracle_random_maps(ctx, oracle_mod):
     rng = np.random.default_rng(3)
     for shape in [(1, 1), (3, 7), (257, 131), (1000, 333)]:
         Hn = rng.normal(0.0, 0.002, size=shape) - 0.1
-        for dt in (torch.float64, torch.float32):
+        # FP64 maps: FP64 throughout; FP32 maps: FP32 per-cell terms summed in
+        # FP64 over 32-cell FP32 leaves (relative error ~1e-6)
+        for dt, rel in ((torch.float64, 1e-12), (torch.float32, 2e-5)):
             H = torch.from_numpy(Hn).to(dt).cuda()
             n_rows, n_cols = min(10, shape[0]), min(10, shape[1])
             r = ctx.roughness(H, n_rows, n_cols)
             ro = oracle_mod.roughness(H.double().cpu().numpy(), n_rows, n_cols)
-            for k in ("mean", "Sa", "Sq", "Sp", "Sv", "Sz", "zmin", "zmax"):
-                assert abs(r[k] - ro[k]) <= 1e-12 * max(abs(ro[k]), 1e-300), (shape, k)
+            for k in ("zmin", "zmax"):
+                assert r[k] == ro[k], (shape, k)
+            for k in ("mean", "Sa", "Sq"):
+                assert abs(r[k] - ro[k]) <= rel * max(abs(ro[k]), 1e-300), (shape, k, r[k], ro[k])
+            for k in ("Sp", "Sv", "Sz"):
+                assert abs(r[k] - ro[k]) <= rel * max(abs(ro[k]), abs(ro["mean"])), (shape, k)
             if ro["Sq"] > 0:
                 for k in ("Ssk", "Sku"):
-                    assert abs(r[k] - ro[k]) <= 1e-10 * max(abs(ro[k]), 1.0), (shape, k)
+                    assert abs(r[k] - ro[k]) <= 100 * rel * max(abs(ro[k]), 1.0), (shape, k)
             assert r["row_index"] == ro["row_index"] and r["col_index"] == ro["col_index"]
             for k in ("Ra_row", "Ra_col", "Rz_row", "Rz_col"):
                 a, b = np.asarray(r[k]), np.asarray(ro[k])
