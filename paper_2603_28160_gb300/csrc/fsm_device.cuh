@@ -59,6 +59,7 @@ struct Surface {
     double2* ph64;    // [S]
     float4* groups;   // [N * ceil(E/32)]: (min P_y, max P_y, min P_z, 0) over 32 points
     double* plan_part;  // [kPlanParts][4]: per planning block, lowest z, x and y reach
+    int* tile_queue;    // next-tile counter of a single-surface sweep (zeroed by planning)
     void* heights;    // output map
     // ---- derived (plan kernel) ----
     double z_ref, fs, dtheta;       // reference height, feed per step, step angle (rad)

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         if (lane == 0) sf->groups[gi] = make_float4(ymin, ymax, zmin, 0.f);
     }
     if (tid == 0) {
+        if (sf->tile_queue) *sf->tile_queue = 0;
         double zlo = 1e300, rx = 0.0, ry = 0.0;
         for (int q = 0; q < parts; ++q) {
             zlo = fmin(zlo, sf->plan_part[4 * q]);
@@ -217,29 +218,27 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
 // ===========================================================================
 // Tile sweep
 // ===========================================================================
+// Per-thread work counters. 32-bit per thread is enough (a thread handles
+// well under 2^32 items of one launch); they are widened when flushed.
 struct Counters {
-    long long evaluated, cutting, rebinned, atomics;
+    unsigned evaluated, cutting, rebinned, atomics;
 };
 
 __device__ __forceinline__ void warp_flush(Counters& c, long long* out) {
     if (out == nullptr) return;
-    for (int o = 16; o > 0; o >>= 1) {
-        c.evaluated += __shfl_xor_sync(0xffffffffu, c.evaluated, o);
-        c.cutting += __shfl_xor_sync(0xffffffffu, c.cutting, o);
-        c.rebinned += __shfl_xor_sync(0xffffffffu, c.rebinned, o);
-        c.atomics += __shfl_xor_sync(0xffffffffu, c.atomics, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd((unsigned long long*)out + 0, (unsigned long long)c.evaluated);
-        atomicAdd((unsigned long long*)out + 1, (unsigned long long)c.cutting);
-        atomicAdd((unsigned long long*)out + 2, (unsigned long long)c.rebinned);
-        atomicAdd((unsigned long long*)out + 3, (unsigned long long)c.atomics);
-    }
+    unsigned long long v[4] = {c.evaluated, c.cutting, c.rebinned, c.atomics};
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 4; ++k) atomicAdd((unsigned long long*)out + k, v[k]);
 }
 
 // A run of one edge point with its iteration bookkeeping (see run_iter).
 struct RunRec {
-    int32_t m0, len, occ0, first_off, len0, total, span;
+    int32_t m0, len, occ0, first_off, len0, total;
+    float dxA;      // FP32 path: tile-local x of the pass at the run's first step
+    float g_cells;  // FP32 path: bin ambiguity band of this run (cells)
+    float inv_len;  // 1 / len
 };
 
 constexpr int kRebinCap = 64;
@@ -249,6 +248,7 @@ struct WarpScratch {
     RunRec run[32][kMaxArcs];
     int32_t n[32];
     int32_t q_s[kRebinCap], q_m[kRebinCap], q_idx[kRebinCap];
+    uint8_t flat[32 * kMaxArcs];  // run list of the task: (point << 2) | arc
 };
 
 constexpr int kPassCache = 64;
@@ -309,6 +309,12 @@ __device__ __forceinline__ long long bin64(double coord, double origin, double i
 __device__ __forceinline__ void rec_item(const RunRec& r, int32_t S, float inv_len, int32_t t, int32_t* s,
                                          int32_t* m) {
     int32_t k, off;
+    if (r.total == r.len0) {  // a single occurrence: consecutive steps
+        *s = r.occ0 + r.first_off + t;
+        const int32_t mm = r.m0 + r.first_off + t;
+        *m = mm >= S ? mm - S : mm;
+        return;
+    }
     if (t < r.len0) {
         k = 0;
         off = r.first_off + t;
@@ -375,14 +381,16 @@ __device__ __forceinline__ void pass_band_any(const Surface& sf, const TileCtx<C
 
 // Phase 1 of a warp task: lane = edge point j = 32 g + lane of tooth K. Each
 // lane enumerates its runs for pass p and stores them with their iteration
-// bookkeeping. Returns whether any lane has work.
+// bookkeeping, its FP32 anchor and guard band. t4 and pt (zb, eps_z) stay
+// in the lane's registers for phase 2. Returns whether any lane has work.
 __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& ts, float ylo, float yhi, int K,
-                                          int g, int p, WarpScratch& ws, float4 (&t4)[3]) {
+                                          int g, int p, WarpScratch& ws, float4 (&t4)[3], float2& pt) {
     const int lane = threadIdx.x & 31;
     const int E = sf.E;
     const int j = g * 32 + lane;
     int nr = 0;
     t4[0] = t4[1] = t4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    pt = make_float2(0.f, 0.f);
     if (j < E) {
         const float4* tp = sf.tool32 + 4 * (size_t)(K * E + j);
         t4[0] = tp[0];
@@ -413,6 +421,14 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         f.S = sf.S;
         Run runs[kMaxArcs];
         const int n = point_runs(geo, f, runs);
+        // FP32 error bounds of z and of the tile-local x, y for this point
+        // (error model in the precision-scheme documentation), 1.5x margin
+        const float u24 = 5.9604644775390625e-8f;
+        const float amp_xy = fmaxf(geo.amp_x, geo.amp_y);
+        const float pt_err = 6.f * amp_xy + 3.f * (fabsf(geo.wx) + fabsf(geo.wy) + fabsf(geo.wz)) +
+                             3.f * (float)max(sf.tile_x, sf.tile_y) * (float)sf.pitch;
+        pt.x = sf.zrel_f + geo.wz;                                                          // zb
+        pt.y = 1.5f * u24 * (5.f * geo.amp_z + 4.f * (fabsf(sf.zrel_f) + fabsf(geo.wz)));  // eps_z
         for (int a = 0; a < n; ++a) {
             const RunIter it = run_iter(runs[a], sf.S);
             if (it.total <= 0) continue;
@@ -423,10 +439,21 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
             r.first_off = it.first_off;
             r.len0 = it.len0;
             r.total = it.total;
-            r.span = runs[a].s_hi - runs[a].s_lo;
+            const int32_t sA = it.occ0 + it.first_off;
+            r.dxA = df_affine(ts.dx_hi, ts.dx_lo, sA - f.s0, sf.fs_hi, sf.fs_lo);
+            const float span_mm = (float)(runs[a].s_hi - runs[a].s_lo) * sf.fs_f;
+            r.g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * sf.inv_pitch_f + sf.guard_extra;
+            r.inv_len = 1.0f / (float)r.len;
         }
     }
     ws.n[lane] = nr;
+    // flat run list in point order
+    int pre = nr;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    for (int a = 0; a < nr; ++a) ws.flat[pre - nr + a] = (uint8_t)((lane << 2) | a);
     __syncwarp();
     return __any_sync(0xffffffffu, nr > 0);
 }
@@ -478,97 +505,113 @@ __device__ __noinline__ void rebin_flush(const Surface& sf, const TileCtx<uint32
     __syncwarp();
 }
 
-__device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<uint32_t>& tc, const TileShared& ts,
-                                             float dyp, int K, int g, int p, WarpScratch& ws,
-                                             const float4 (&t4)[3], Counters& cnt) {
+// Evaluate one FP32 item; returns whether it must be re-binned in FP64.
+__device__ __forceinline__ bool eval32(const RunRec& r, int t, int S, const float2* __restrict__ ph32, float ux,
+                                       float vx, float wx, float uy, float vy, float wy, float uz, float vz, float zb,
+                                       float eps_z, float dyp, float fs32, float inv_pitch, uint32_t* cells,
+                                       int tile_x, int txc, int tyc, int32_t* s_out, int32_t* m_out, Counters& cnt) {
+    int32_t s, m;
+    rec_item(r, S, r.inv_len, t, &s, &m);
+    *s_out = s;
+    *m_out = m;
+    const float2 cs = __ldg(ph32 + m);
+    ++cnt.evaluated;
+    const float z = fmaf(cs.x, uz, fmaf(cs.y, vz, zb));
+    if (!(z < 0.f)) return false;
+    const int32_t sA = r.occ0 + r.first_off;
+    const float dx = fmaf((float)(s - sA), fs32, r.dxA);
+    const float xl = dx + fmaf(cs.x, ux, fmaf(cs.y, vx, wx));
+    const float yl = dyp + fmaf(cs.x, uy, fmaf(cs.y, vy, wy));
+    const float fx = xl * inv_pitch, fy = yl * inv_pitch;
+    const float flx = floorf(fx), fly = floorf(fy);
+    const float rx = fx - flx, ry = fy - fly;
+    const int i = (int)flx, k = (int)fly;
+    const bool in = (unsigned)i < (unsigned)txc && (unsigned)k < (unsigned)tyc;
+    if (in) ++cnt.cutting;
+    const float g = r.g_cells;
+    const bool amb = rx < g || rx > 1.f - g || ry < g || ry > 1.f - g;
+    if (!amb) {
+        if (in) update32(cells, k * tile_x + i, z, cnt);
+        return false;
+    }
+    // candidate cells of the ambiguous point inside this tile: re-bin only if
+    // the point could lower one of them
+    const int i0 = max(rx < g ? i - 1 : i, 0), i1 = min(rx > 1.f - g ? i + 1 : i, txc - 1);
+    const int k0 = max(ry < g ? k - 1 : k, 0), k1 = min(ry > 1.f - g ? k + 1 : k, tyc - 1);
+    const uint32_t elo = enc32(__float_as_uint(z - eps_z));
+    for (int kk = k0; kk <= k1; ++kk)
+        for (int ii = i0; ii <= i1; ++ii)
+            if (elo < cells[kk * tile_x + ii]) return true;
+    return false;
+}
+
+// Queue this iteration's re-bins (warp-cooperative) and flush full batches.
+__device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws, int p,
+                                           bool want, int32_t s, int32_t m, int idx, int& qn, Counters& cnt) {
     const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (!bal) return;
+    const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+    if (want) {
+        ws.q_s[pos] = s;
+        ws.q_m[pos] = m;
+        ws.q_idx[pos] = idx;
+    }
+    qn += __popc(bal);
+    __syncwarp();
+    if (qn >= 32) {
+        rebin_flush(sf, tc, ws, p, qn, cnt);
+        qn -= 32;
+    }
+}
+
+// Phase 2 (FP32): the task's runs are taken two at a time, one per half-warp;
+// each lane evaluates two items of its half's run per iteration, so every lane
+// carries two independent dependency chains.
+__device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
+                                             int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
+                                             Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const int hl = lane & 15, half = lane >> 4;
     const int S = sf.S;
-    const int s0 = p * sf.steps_per_pass;
-    const float fs32 = sf.fs_f, fs_hi = sf.fs_hi, fs_lo = sf.fs_lo;
+    const float fs32 = sf.fs_f;
     const float inv_pitch = sf.inv_pitch_f;
     const float2* __restrict__ ph32 = sf.ph32;
     const int tile_x = sf.tile_x;
     uint32_t* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
-    const float u24 = 5.9604644775390625e-8f;
-    const float pitch_f = (float)sf.pitch;
+    // number of runs in the task (n[] summed)
+    int R = ws.n[lane];
+    for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
-    for (int o = 0; o < 32; ++o) {
-        const int nr = ws.n[o];
-        if (nr == 0) continue;
-        // the point's pose vectors, from the lane that loaded them
+    for (int q = 0; q < R; q += 2) {
+        const int ri = q + half;
+        const bool has = ri < R;
+        const int code = has ? (int)ws.flat[ri] : 0;
+        const int o = code >> 2, a = code & 3;
+        RunRec r = ws.run[o][a];
+        if (!has) r.total = 0;
+        // pose vectors and scalars of this half's point, from the lane that loaded them
         const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
         const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
         const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
-        const float wz = __shfl_sync(0xffffffffu, t4[2].x, o);
-        const float amp_xy = fmaxf(sqrtf(ux * ux + vx * vx), sqrtf(uy * uy + vy * vy));
-        const float amp_z = sqrtf(uz * uz + vz * vz);
-        const float zb = sf.zrel_f + wz;
-        // FP32 error bounds of z and of the tile-local x, y (see the error
-        // model in the documentation of the precision scheme), 1.5x margin
-        const float eps_z = 1.5f * u24 * (5.f * amp_z + 4.f * (fabsf(sf.zrel_f) + fabsf(wz)));
-        const float pt_err = 6.f * amp_xy + 3.f * (fabsf(wx) + fabsf(wy) + fabsf(wz)) +
-                             3.f * (float)max(tile_x, sf.tile_y) * pitch_f;
+        const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
         const int idx = K * sf.E + g * 32 + o;
-        for (int a = 0; a < nr; ++a) {
-            const RunRec r = ws.run[o][a];
-            const int32_t sA = r.occ0 + r.first_off;
-            const float dxA = df_affine(ts.dx_hi, ts.dx_lo, sA - s0, fs_hi, fs_lo);
-            const float span_mm = (float)r.span * fs32;
-            const float g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * inv_pitch + sf.guard_extra;
-            const float inv_len = 1.0f / (float)r.len;
-            for (int base = 0; base < r.total; base += 32) {
-                const int t = base + lane;
-                bool want_rebin = false;
-                int32_t s = 0, m = 0;
-                if (t < r.total) {
-                    rec_item(r, S, inv_len, t, &s, &m);
-                    const float2 cs = __ldg(ph32 + m);
-                    ++cnt.evaluated;
-                    const float z = fmaf(cs.x, uz, fmaf(cs.y, vz, zb));
-                    if (z < 0.f) {
-                        const float dx = fmaf((float)(s - sA), fs32, dxA);
-                        const float xl = dx + fmaf(cs.x, ux, fmaf(cs.y, vx, wx));
-                        const float yl = dyp + fmaf(cs.x, uy, fmaf(cs.y, vy, wy));
-                        const float fx = xl * inv_pitch, fy = yl * inv_pitch;
-                        const float flx = floorf(fx), fly = floorf(fy);
-                        const float rx = fx - flx, ry = fy - fly;
-                        const int i = (int)flx, k = (int)fly;
-                        const bool in = (unsigned)i < (unsigned)txc && (unsigned)k < (unsigned)tyc;
-                        if (in) ++cnt.cutting;
-                        const bool amb = rx < g_cells || rx > 1.f - g_cells || ry < g_cells || ry > 1.f - g_cells;
-                        if (!amb) {
-                            if (in) update32(cells, k * tile_x + i, z, cnt);
-                        } else {
-                            // candidate cells of the ambiguous point inside this tile: re-bin only if
-                            // the point could lower one of them
-                            const int i0 = max(rx < g_cells ? i - 1 : i, 0), i1 = min(rx > 1.f - g_cells ? i + 1 : i, txc - 1);
-                            const int k0 = max(ry < g_cells ? k - 1 : k, 0), k1 = min(ry > 1.f - g_cells ? k + 1 : k, tyc - 1);
-                            const uint32_t elo = enc32(__float_as_uint(z - eps_z));
-                            for (int kk = k0; kk <= k1 && !want_rebin; ++kk)
-                                for (int ii = i0; ii <= i1; ++ii)
-                                    if (elo < cells[kk * tile_x + ii]) { want_rebin = true; break; }
-                        }
-                    }
-                }
-                // queue the re-bins of this iteration (warp-cooperative)
-                const unsigned bal = __ballot_sync(0xffffffffu, want_rebin);
-                if (bal) {
-                    const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                    if (want_rebin) {
-                        ws.q_s[pos] = s;
-                        ws.q_m[pos] = m;
-                        ws.q_idx[pos] = idx;
-                    }
-                    qn += __popc(bal);
-                    __syncwarp();
-                    if (qn >= 32) {
-                        rebin_flush(sf, tc, ws, p, qn, cnt);
-                        qn -= 32;
-                    }
-                }
-            }
+        const int tot = r.total;
+        const int tmax = max(tot, __shfl_xor_sync(0xffffffffu, tot, 16));
+        for (int base = 0; base < tmax; base += 32) {
+            const int t0 = base + hl, t1 = base + 16 + hl;
+            int32_t s0 = 0, m0 = 0, s1 = 0, m1 = 0;
+            bool w0 = false, w1 = false;
+            if (t0 < tot)
+                w0 = eval32(r, t0, S, ph32, ux, vx, wx, uy, vy, wy, uz, vz, zb, eps_z, dyp, fs32, inv_pitch, cells,
+                            tile_x, txc, tyc, &s0, &m0, cnt);
+            if (t1 < tot)
+                w1 = eval32(r, t1, S, ph32, ux, vx, wx, uy, vy, wy, uz, vz, zb, eps_z, dyp, fs32, inv_pitch, cells,
+                            tile_x, txc, tyc, &s1, &m1, cnt);
+            rebin_push(sf, tc, ws, p, w0, s0, m0, idx, qn, cnt);
+            rebin_push(sf, tc, ws, p, w1, s1, m1, idx, qn, cnt);
         }
     }
     if (qn > 0) rebin_flush(sf, tc, ws, p, qn, cnt);
@@ -598,10 +641,9 @@ __device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<un
         const Vec9 v = load_vec9(sf.tool64, NE, idx);
         for (int a = 0; a < nr; ++a) {
             const RunRec r = ws.run[o][a];
-            const float inv_len = 1.0f / (float)r.len;
             for (int t = lane; t < r.total; t += 32) {
                 int32_t s, m;
-                rec_item(r, S, inv_len, t, &s, &m);
+                rec_item(r, S, r.inv_len, t, &s, &m);
                 const double2 cs = __ldg(ph64 + m);
                 ++cnt.evaluated;
                 const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
@@ -697,13 +739,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict
             const float4 gb = sf.groups[K * G + g];
             if (gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi) continue;  // warp-uniform
             float4 t4[3];
-            if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4)) continue;
+            float2 pt;
+            if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4, pt)) continue;
             if constexpr (FP64) {
                 sweep_task64(sf, tc, K, g, p, ws, cnt);
             } else {
                 float yl2, yh2, dyp;
                 pass_band(sf, tc, ts, p, &yl2, &yh2, &dyp);
-                sweep_task32(sf, tc, ts, dyp, K, g, p, ws, t4, cnt);
+                sweep_task32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
             }
             __syncwarp();
         }
