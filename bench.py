@@ -41,6 +41,12 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--batch-size", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-rate", type=float, default=30.0, help="Poisson arrivals per second")
     ap.add_argument("--width", type=float, default=5.0,
                     help="patch width in mm (5.0 = the measured configuration; smaller for profiling)")
     args = ap.parse_args()
@@ -228,6 +234,130 @@ def time_steps(ctx, F, tool, proc, out, rough, K, flush, precision, events_sweep
     return step_ms, sweep_ms
 
 
+def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
+    """The Latin-hypercube batch (FP32) in one persistent launch per precision,
+    prepared once and replayed as a CUDA graph. With several ranks each rank
+    takes a disjoint share of the surfaces (see paper_2603_28160_gb300.shard)."""
+    import torch
+    from paper_2603_28160_gb300 import shard
+    from paper_2603_28160_gb300 import workloads as W
+    allw = W.lhs_batch(n=n)
+    mine = shard.split_by_cost([w.process.cells for w in allw], ws_count)[rank]
+    ws = [allw[i] for i in mine]
+    tools = [ctx.tool(w.tool) for w in ws]
+    procs = [ctx.process(w.process) for w in ws]
+    outs = [F.heights_tensor(w.process) for w in ws]
+    rough = torch.zeros(len(ws) * F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    counted = ctx.batch(tools, procs, outs, rough_buf=rough, counters=cnt)
+    counted.run()
+    torch.cuda.synchronize()
+    cutting = int(cnt[1].item())
+    counted.close()
+    b = ctx.batch(tools, procs, outs, rough_buf=rough)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(s)
+    g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, e in ev:
+        with torch.cuda.stream(s):
+            a.record(s)
+            g.replay()
+            e.record(s)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(e) for a, e in ev]
+    mean = sum(ms) / len(ms)
+    cells = sum(w.process.cells for w in ws)
+    # the stated comparison: the same first surfaces predicted one at a time
+    # by the plain FP64 single-surface path, against the FP32 batch of them
+    k = min(256, len(ws))
+    sub = [W.Workload(w.name, w.tool, w.process.replace(precision="fp64")) for w in ws[:k]]
+    t_sub = [ctx.tool(w.tool) for w in sub]
+    p_sub = [ctx.process(w.process) for w in sub]
+    o_sub = [F.heights_tensor(w.process) for w in sub]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t_, p_, o_ in zip(t_sub, p_sub, o_sub):
+        ctx.predict_surface(t_, p_, o_)
+        ctx.roughness_async(o_, F.FSM_FP64, rough)
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    del o_sub
+    b32 = ctx.batch(tools[:k], procs[:k], outs[:k], rough_buf=rough)
+    b32.run()
+    torch.cuda.synchronize()
+    e0.record()
+    b32.run()
+    e1.record()
+    torch.cuda.synchronize()
+    fp32_ms = e0.elapsed_time(e1)
+    b32.close()
+    del outs
+    b.close()
+    torch.cuda.empty_cache()
+    return {"workload": "lhs_batch: %d seeded Latin-hypercube surfaces (ball/flat, D 4-16, 2-6 flutes, helix "
+                        "20-45, runout 0-15 um, lead/tilt 0-20, fz 0.03-0.2, ae 0.1-1.0, patches 0.5-4 mm "
+                        "at 1-5 um), FP32, 200 edge pts, 0.1 deg/step" % n,
+            "surfaces": len(ws), "cells": cells, "cutting": cutting, "steps": steps, "ms_per_step": mean,
+            "surfaces_per_s": len(ws) / (mean / 1e3), "value": cutting / (mean / 1e3), "unit": UNIT,
+            "launch": "prepared batch replayed as one CUDA graph (planning, persistent sweep, roughness)",
+            "vs_plain_fp64": {"surfaces": k, "fp32_batch_surfaces_per_s": k / (fp32_ms / 1e3),
+                              "fp64_single_surface_surfaces_per_s": k / (fp64_ms / 1e3),
+                              "speedup": fp64_ms / fp32_ms}}
+
+
+def served_leg(ctx, F, seconds, rate, seed=5):
+    """Poisson request stream through fsm_submit/fsm_poll (continuous batching,
+    120 GB admission budget, 70 % FP32 / 30 % FP64, 0.25-25 Mcells)."""
+    import threading
+    from paper_2603_28160_gb300 import workloads as W
+    n = max(1, int(seconds * rate))
+    reqs = W.serve_stream(n, seed=seed)
+    arrivals = W.poisson_arrivals(n, rate, seed=seed)
+    handles = [(ctx.tool(w.tool), ctx.process(w.process)) for w in reqs]
+    ctx.server_start(budget_bytes=120 << 30, n_streams=4, max_batch=64)
+    tickets = [None] * n
+    lat, queue = [0.0] * n, [0.0] * n
+    done = threading.Event()
+
+    def collect():
+        for i in range(n):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            r = ctx.poll(tickets[i], timeout_ms=-1)
+            lat[i], queue[i] = r["latency_s"], r["queue_s"]
+            ctx.release(tickets[i])
+        done.set()
+
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(n):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets[i] = ctx.submit(*handles[i])
+    done.wait()
+    elapsed = time.perf_counter() - t0
+    th.join()
+    ctx.server_stop()
+    srt = sorted(lat)
+    return {"workload": "serve_stream: Poisson arrivals at %.0f/s for %.0f s, batch-distribution tools, "
+                        "0.25-25 Mcells, 30%% FP64" % (rate, seconds),
+            "requests": n, "fp64_requests": sum(w.process.precision == "fp64" for w in reqs),
+            "elapsed_s": elapsed, "surfaces_per_s": n / elapsed,
+            "p50_ms": 1e3 * srt[len(srt) // 2], "p99_ms": 1e3 * srt[min(n - 1, int(0.99 * n))],
+            "queue_p50_ms": 1e3 * sorted(queue)[n // 2], "budget_gb": 120, "streams": 4}
+
+
 def gb300_arm(args):
     import torch
 
@@ -316,6 +446,18 @@ def gb300_arm(args):
         fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / 1.25
         del out64
 
+    batched = None
+    if not args.skip_batch:
+        batched = batched_leg(ctx, F, args.batch_size, args.batch_steps, rank, ws)
+        if ws > 1:
+            bms = max_over_ranks(batched["ms_per_step"], ws)
+            batched["ms_per_step_max_over_ranks"] = bms
+            batched["surfaces_per_s"] = args.batch_size / (bms / 1e3)
+    served = None
+    if not args.skip_serve and rank == 0:
+        served = served_leg(ctx, F, args.serve_seconds, args.serve_rate)
+    barrier(ws)
+
     if rank != 0:
         return 0
 
@@ -361,6 +503,8 @@ def gb300_arm(args):
         "clocks": clk,
         "wall_s": wall,
         "fp64_single_surface": fp64,
+        "batched": batched,
+        "served": served,
         "src_hash": src_hash(),
     }
     if ws == 1 and not args.skip_cpu_baseline:

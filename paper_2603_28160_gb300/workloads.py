@@ -243,6 +243,38 @@ def lhs_batch(n: int = 4096, seed: int = 4096, precision: str = "fp32",
     return out
 
 
+def serve_stream(n: int, seed: int = 5, fp64_fraction: float = 0.3, rot_step_deg: float = 0.1,
+                 n_edge: int = 200, cells_range=(0.25e6, 25e6)) -> List[Workload]:
+    """Requests of a served stream: tools and cutting conditions drawn from
+    the batch distribution (seeded Latin hypercube), square patches whose
+    cell count is log-uniform in [0.25, 25] Mcells at 1-5 um pitch, and a
+    seeded 30 % of the requests in FP64 (the rest FP32)."""
+    rng = np.random.default_rng(seed + 1000)
+    base = lhs_batch(n=n, seed=seed, rot_step_deg=rot_step_deg, n_edge=n_edge)
+    out = []
+    for w in base:
+        t, p = w.tool, w.process
+        cells = float(np.exp(rng.uniform(np.log(cells_range[0]), np.log(cells_range[1]))))
+        side_cells = int(round(np.sqrt(cells)))
+        side = side_cells * p.pitch
+        if t.kind == "flat":
+            t = dataclasses.replace(t, n_end=int(math.ceil((t.diameter / 2) / (p.pitch / 2))))
+        x0, y0, nx, ny = _patch(side, side, p.pitch)
+        n_passes = int(math.ceil(side / p.ae)) + 1
+        sx = sy = 0.0
+        if t.kind == "flat" and (p.lead_deg > 0.0 or p.tilt_deg > 0.0):
+            a, b = math.sin(math.radians(p.lead_deg)), math.sin(math.radians(p.tilt_deg))
+            nrm = math.hypot(a, b)
+            sx, sy = 0.5 * t.diameter * a / nrm, 0.5 * t.diameter * b / nrm
+        first_y = -0.5 * (n_passes - 1) * p.ae - sy
+        px, py, spp = plan_passes(t, p.fz, p.rot_step_deg, nx * p.pitch, -sx, first_y, p.ap, p.pitch)
+        prec = "fp64" if rng.random() < fp64_fraction else "fp32"
+        p2 = p.replace(x0=x0, y0=y0, nx=nx, ny=ny, n_passes=n_passes, pass_x0=px, pass_y0=py,
+                       steps_per_pass=spp, precision=prec)
+        out.append(Workload("serve_%d" % len(out), t, p2))
+    return out
+
+
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 5) -> np.ndarray:
     """Seeded Poisson process: arrival times (s) of n requests."""
     rng = np.random.default_rng(seed)
