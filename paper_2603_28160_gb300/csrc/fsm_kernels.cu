@@ -505,46 +505,6 @@ __device__ __noinline__ void rebin_flush(const Surface& sf, const TileCtx<uint32
     __syncwarp();
 }
 
-// Evaluate one FP32 item; returns whether it must be re-binned in FP64.
-__device__ __forceinline__ bool eval32(const RunRec& r, int t, int S, const float2* __restrict__ ph32, float ux,
-                                       float vx, float wx, float uy, float vy, float wy, float uz, float vz, float zb,
-                                       float eps_z, float dyp, float fs32, float inv_pitch, uint32_t* cells,
-                                       int tile_x, int txc, int tyc, int32_t* s_out, int32_t* m_out, Counters& cnt) {
-    int32_t s, m;
-    rec_item(r, S, r.inv_len, t, &s, &m);
-    *s_out = s;
-    *m_out = m;
-    const float2 cs = __ldg(ph32 + m);
-    ++cnt.evaluated;
-    const float z = fmaf(cs.x, uz, fmaf(cs.y, vz, zb));
-    if (!(z < 0.f)) return false;
-    const int32_t sA = r.occ0 + r.first_off;
-    const float dx = fmaf((float)(s - sA), fs32, r.dxA);
-    const float xl = dx + fmaf(cs.x, ux, fmaf(cs.y, vx, wx));
-    const float yl = dyp + fmaf(cs.x, uy, fmaf(cs.y, vy, wy));
-    const float fx = xl * inv_pitch, fy = yl * inv_pitch;
-    const float flx = floorf(fx), fly = floorf(fy);
-    const float rx = fx - flx, ry = fy - fly;
-    const int i = (int)flx, k = (int)fly;
-    const bool in = (unsigned)i < (unsigned)txc && (unsigned)k < (unsigned)tyc;
-    if (in) ++cnt.cutting;
-    const float g = r.g_cells;
-    const bool amb = rx < g || rx > 1.f - g || ry < g || ry > 1.f - g;
-    if (!amb) {
-        if (in) update32(cells, k * tile_x + i, z, cnt);
-        return false;
-    }
-    // candidate cells of the ambiguous point inside this tile: re-bin only if
-    // the point could lower one of them
-    const int i0 = max(rx < g ? i - 1 : i, 0), i1 = min(rx > 1.f - g ? i + 1 : i, txc - 1);
-    const int k0 = max(ry < g ? k - 1 : k, 0), k1 = min(ry > 1.f - g ? k + 1 : k, tyc - 1);
-    const uint32_t elo = enc32(__float_as_uint(z - eps_z));
-    for (int kk = k0; kk <= k1; ++kk)
-        for (int ii = i0; ii <= i1; ++ii)
-            if (elo < cells[kk * tile_x + ii]) return true;
-    return false;
-}
-
 // Queue this iteration's re-bins (warp-cooperative) and flush full batches.
 __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws, int p,
                                            bool want, int32_t s, int32_t m, int idx, int& qn, Counters& cnt) {
@@ -565,9 +525,37 @@ __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint
     }
 }
 
+// Item t of a run, without branches (both halves of a warp may be on runs of
+// different shapes): first occurrence if t < len0, later ones otherwise.
+__device__ __forceinline__ void rec_item_sel(const RunRec& r, int32_t S, int32_t t, int32_t* s, int32_t* m) {
+    const int32_t tt = t - r.len0;
+    int32_t q = __float2int_rz((float)max(tt, 0) * r.inv_len);
+    q += ((q + 1) * r.len <= tt) ? 1 : 0;
+    q -= (q * r.len > tt) ? 1 : 0;
+    const bool first = tt < 0;
+    const int32_t k = first ? 0 : 1 + q;
+    const int32_t off = first ? r.first_off + t : tt - q * r.len;
+    *s = r.occ0 + k * S + off;
+    const int32_t mm = r.m0 + off;
+    *m = mm >= S ? mm - S : mm;
+}
+
+// The rare tail of an evaluation: an FP32 cell index near a boundary. True
+// if the point could lower one of its candidate cells in this tile.
+__device__ __noinline__ bool ambiguous_may_lower(const uint32_t* cells, int tile_x, int txc, int tyc, int i, int k,
+                                                 float rx, float ry, float g, float z, float eps_z) {
+    const int i0 = max(rx < g ? i - 1 : i, 0), i1 = min(rx > 1.f - g ? i + 1 : i, txc - 1);
+    const int k0 = max(ry < g ? k - 1 : k, 0), k1 = min(ry > 1.f - g ? k + 1 : k, tyc - 1);
+    const uint32_t elo = enc32(__float_as_uint(z - eps_z));
+    for (int kk = k0; kk <= k1; ++kk)
+        for (int ii = i0; ii <= i1; ++ii)
+            if (elo < cells[kk * tile_x + ii]) return true;
+    return false;
+}
+
 // Phase 2 (FP32): the task's runs are taken two at a time, one per half-warp;
-// each lane evaluates two items of its half's run per iteration, so every lane
-// carries two independent dependency chains.
+// each lane evaluates two items of its half's run per iteration, written as
+// two interleaved, mostly predicated chains.
 __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
                                              int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
                                              Counters& cnt) {
@@ -580,7 +568,6 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
     const int tile_x = sf.tile_x;
     uint32_t* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
-    // number of runs in the task (n[] summed)
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
@@ -590,8 +577,10 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
         const int code = has ? (int)ws.flat[ri] : 0;
         const int o = code >> 2, a = code & 3;
         RunRec r = ws.run[o][a];
-        if (!has) r.total = 0;
-        // pose vectors and scalars of this half's point, from the lane that loaded them
+        if (!has) {  // a well-formed empty run: its (unused) item indices stay at phase 0
+            r.m0 = 0; r.len = 1; r.occ0 = 0; r.first_off = 0; r.len0 = 1; r.total = 0;
+            r.dxA = 0.f; r.g_cells = 0.f; r.inv_len = 1.f;
+        }
         const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
         const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
         const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
@@ -600,18 +589,53 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
         const int idx = K * sf.E + g * 32 + o;
         const int tot = r.total;
         const int tmax = max(tot, __shfl_xor_sync(0xffffffffu, tot, 16));
+        const int32_t sA = r.occ0 + r.first_off;
+        const float gc = r.g_cells;
         for (int base = 0; base < tmax; base += 32) {
-            const int t0 = base + hl, t1 = base + 16 + hl;
-            int32_t s0 = 0, m0 = 0, s1 = 0, m1 = 0;
-            bool w0 = false, w1 = false;
-            if (t0 < tot)
-                w0 = eval32(r, t0, S, ph32, ux, vx, wx, uy, vy, wy, uz, vz, zb, eps_z, dyp, fs32, inv_pitch, cells,
-                            tile_x, txc, tyc, &s0, &m0, cnt);
-            if (t1 < tot)
-                w1 = eval32(r, t1, S, ph32, ux, vx, wx, uy, vy, wy, uz, vz, zb, eps_z, dyp, fs32, inv_pitch, cells,
-                            tile_x, txc, tyc, &s1, &m1, cnt);
-            rebin_push(sf, tc, ws, p, w0, s0, m0, idx, qn, cnt);
-            rebin_push(sf, tc, ws, p, w1, s1, m1, idx, qn, cnt);
+            const int ta = base + hl, tb = base + 16 + hl;
+            const bool va = ta < tot, vb = tb < tot;
+            int32_t sa, ma, sb, mb;
+            rec_item_sel(r, S, va ? ta : 0, &sa, &ma);
+            rec_item_sel(r, S, vb ? tb : 0, &sb, &mb);
+            const float2 ca = __ldg(ph32 + ma);
+            const float2 cb = __ldg(ph32 + mb);
+            cnt.evaluated += (unsigned)va + (unsigned)vb;
+            const float za = fmaf(ca.x, uz, fmaf(ca.y, vz, zb));
+            const float zb2 = fmaf(cb.x, uz, fmaf(cb.y, vz, zb));
+            const float xa = fmaf((float)(sa - sA), fs32, r.dxA) + fmaf(ca.x, ux, fmaf(ca.y, vx, wx));
+            const float xb = fmaf((float)(sb - sA), fs32, r.dxA) + fmaf(cb.x, ux, fmaf(cb.y, vx, wx));
+            const float ya = dyp + fmaf(ca.x, uy, fmaf(ca.y, vy, wy));
+            const float yb = dyp + fmaf(cb.x, uy, fmaf(cb.y, vy, wy));
+            const float fxa = xa * inv_pitch, fya = ya * inv_pitch, fxb = xb * inv_pitch, fyb = yb * inv_pitch;
+            const float lxa = floorf(fxa), lya = floorf(fya), lxb = floorf(fxb), lyb = floorf(fyb);
+            const float rxa = fxa - lxa, rya = fya - lya, rxb = fxb - lxb, ryb = fyb - lyb;
+            const int ia = (int)lxa, ka = (int)lya, ib = (int)lxb, kb = (int)lyb;
+            const bool cut_a = va && za < 0.f, cut_b = vb && zb2 < 0.f;
+            const bool in_a = cut_a && (unsigned)ia < (unsigned)txc && (unsigned)ka < (unsigned)tyc;
+            const bool in_b = cut_b && (unsigned)ib < (unsigned)txc && (unsigned)kb < (unsigned)tyc;
+            cnt.cutting += (unsigned)in_a + (unsigned)in_b;
+            const bool amb_a = rxa < gc || rxa > 1.f - gc || rya < gc || rya > 1.f - gc;
+            const bool amb_b = rxb < gc || rxb > 1.f - gc || ryb < gc || ryb > 1.f - gc;
+            const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
+            const int cia = ka * tile_x + ia, cib = kb * tile_x + ib;
+            const uint32_t ea = enc32(__float_as_uint(za)), eb = enc32(__float_as_uint(zb2));
+            const uint32_t cva = upd_a ? cells[cia] : 0u;
+            const uint32_t cvb = upd_b ? cells[cib] : 0u;
+            if (upd_a && ea < cva) {
+                atomicMin(cells + cia, ea);
+                ++cnt.atomics;
+            }
+            if (upd_b && eb < cvb) {
+                atomicMin(cells + cib, eb);
+                ++cnt.atomics;
+            }
+            bool wa = false, wb = false;
+            if (cut_a && amb_a)
+                wa = ambiguous_may_lower(cells, tile_x, txc, tyc, ia, ka, rxa, rya, gc, za, eps_z);
+            if (cut_b && amb_b)
+                wb = ambiguous_may_lower(cells, tile_x, txc, tyc, ib, kb, rxb, ryb, gc, zb2, eps_z);
+            rebin_push(sf, tc, ws, p, wa, sa, ma, idx, qn, cnt);
+            rebin_push(sf, tc, ws, p, wb, sb, mb, idx, qn, cnt);
         }
     }
     if (qn > 0) rebin_flush(sf, tc, ws, p, qn, cnt);
