@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -232,6 +233,30 @@ def time_steps(ctx, F, tool, proc, out, rough, K, flush, precision, events_sweep
     step_ms = [a.elapsed_time(b) for a, b in ev]
     sweep_ms = [a.elapsed_time(b) for a, b in sw]
     return step_ms, sweep_ms
+
+
+def large_grid_leg(ctx, F, flush, steps=2):
+    """The 20x20 mm, 2 um flat-end floor finish (100 Mcells) in FP32: one
+    surface per step (planning, sweep, roughness)."""
+    import torch
+    from paper_2603_28160_gb300 import workloads as W
+    w = W.floor_flat_d12(precision="fp32")
+    t, p = ctx.tool(w.tool), ctx.process(w.process)
+    out = F.heights_tensor(w.process)
+    rough = torch.zeros(F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ctx.predict_surface(t, p, out, counters=cnt)
+    torch.cuda.synchronize()
+    cutting = int(cnt[1].item())
+    step_ms, sweep_ms = time_steps(ctx, F, t, p, out, rough, steps, flush, "fp32")
+    ms = sum(step_ms) / len(step_ms)
+    del out
+    torch.cuda.empty_cache()
+    return {"workload": "floor_flat_d12: flat D=12, 3 flutes 35/38/41 deg helix, runout 8 um, fz=%.4f (seeded), "
+                        "7 passes ae=4.8, 300 flank + 6000 bottom pts, 0.05 deg/step, 20x20 mm @ 2 um" % w.process.fz,
+            "cells": w.process.cells, "trajectory_points": w.trajectory_points, "cutting": cutting,
+            "steps": steps, "ms_per_step": ms, "sweep_ms": sum(sweep_ms) / len(sweep_ms),
+            "value": cutting / (ms / 1e3), "unit": UNIT, "surfaces_per_s": 1e3 / ms}
 
 
 def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
@@ -446,6 +471,9 @@ def gb300_arm(args):
         fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / 1.25
         del out64
 
+    large = None
+    if not args.skip_large and rank == 0:
+        large = large_grid_leg(ctx, F, flush)
     batched = None
     if not args.skip_batch:
         batched = batched_leg(ctx, F, args.batch_size, args.batch_steps, rank, ws)
@@ -503,6 +531,7 @@ def gb300_arm(args):
         "clocks": clk,
         "wall_s": wall,
         "fp64_single_surface": fp64,
+        "large_grid": large,
         "batched": batched,
         "served": served,
         "src_hash": src_hash(),

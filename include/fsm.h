@@ -131,7 +131,9 @@ typedef struct {
  *                     [0] edge-point poses evaluated,
  *                     [1] cutting evaluations: inside the patch and below the
  *                         stock surface (the points the per-cell minimum runs
- *                         over),
+ *                         over); exact in FP64, within ~1e-5 relative in FP32
+ *                         (a point within FP32 error of a tile edge is counted
+ *                         by its FP32 cell),
  *                     [2] cutting points re-binned in FP64 (FP32 path),
  *                     [3] shared-memory atomic updates issued.
  *   sweep_events      NULL or two cudaEvent_t (as void*) recorded on the

@@ -92,14 +92,41 @@ struct ArcF { float start, len; };           // real-valued, len in [0, S]
 struct ArcI { int32_t m0, len; };             // integer phases m0 .. m0+len-1 (mod S)
 struct Run { int32_t m0, len, s_lo, s_hi; };  // an ArcI restricted to steps [s_lo, s_hi]
 
+// a mod S in [0, S) for the phase circle (exact enough for arc bookkeeping,
+// which carries a step of slack).
 FSM_HD float fmod_pos(float a, float S) {
-    float r = fmodf(a, S);
-    return r < 0.f ? r + S : r;
+    float r = a - S * floorf(a * (1.0f / S));
+    if (r < 0.f) r += S;
+    if (r >= S) r -= S;
+    return r;
 }
 
+// a mod S in [0, S) for integers, through a float quotient corrected to exact.
 FSM_HD int32_t imod_pos(int32_t a, int32_t S) {
-    int32_t r = a % S;
-    return r < 0 ? r + S : r;
+    int32_t q = (int32_t)floorf((float)a * (1.0f / (float)S));
+    int32_t r = a - q * S;
+    while (r < 0) r += S;
+    while (r >= S) r -= S;
+    return r;
+}
+
+// floor(a / S) for a >= 0, through a float quotient corrected to exact.
+FSM_HD int32_t idiv_floor(int32_t a, int32_t S) {
+    int32_t q = (int32_t)((float)a * (1.0f / (float)S));
+    while (q * S > a) --q;
+    while ((q + 1) * S <= a) ++q;
+    return q;
+}
+
+// cos of dth * d for a phase offset d (steps): reduced to [-pi, pi] first.
+FSM_HD float phase_cos(float dth, float d, float S) {
+    float r = fmod_pos(d, S);
+    if (r > 0.5f * S) r -= S;
+#if defined(__CUDA_ARCH__)
+    return __cosf(dth * r);  // |error| < 4e-7 on [-pi, pi]; callers widen by 1e-5 relative
+#else
+    return cosf(dth * r);
+#endif
 }
 
 // Phases where lo <= w + amp cos(dth (m - mph)) <= hi. Up to two arcs.
@@ -200,8 +227,8 @@ FSM_HD void sinus_range(float w, float amp, float mph, ArcI a, float dth, int32_
         return;
     }
     float fS = (float)S;
-    float e0 = cosf(dth * ((float)a.m0 - mph));
-    float e1 = cosf(dth * ((float)(a.m0 + a.len - 1) - mph));
+    float e0 = phase_cos(dth, (float)a.m0 - mph, fS);
+    float e1 = phase_cos(dth, (float)(a.m0 + a.len - 1) - mph, fS);
     float cmin = fminf(e0, e1), cmax = fmaxf(e0, e1);
     float span = (float)(a.len - 1);
     if (fmod_pos(mph - (float)a.m0, fS) <= span + 0.5f) cmax = 1.f;
@@ -314,7 +341,7 @@ FSM_HD RunIter run_iter(const Run& r, int32_t S) {
     int32_t e0 = base + r.len - 1 < r.s_hi ? base + r.len - 1 : r.s_hi;
     it.first_off = f0 - base;
     it.len0 = e0 - f0 + 1;
-    it.k_last = (r.s_hi - base) / S;
+    it.k_last = idiv_floor(r.s_hi - base, S);
     if (it.k_last == 0) {
         it.len_last = 0;
         it.total = it.len0;

@@ -32,7 +32,7 @@ def test_fullsize_raster_ball(reference, oracle_mod, prec):
     if prec == "fp64":
         assert c[1] == reference.stats["cutting"]
     else:
-        assert abs(int(c[1]) - reference.stats["cutting"]) <= 1e-6 * reference.stats["cutting"] + 2
+        assert abs(int(c[1]) - reference.stats["cutting"]) <= 1e-5 * reference.stats["cutting"] + 2
     r = ctx.roughness(H)
     ro = oracle_mod.roughness(reference.H)
     compare_roughness(r, ro, SA_REL[prec], keys=("Sa", "Sq"))

@@ -34,6 +34,7 @@ SMALL = {
                                                    rot_step_deg=0.25),
     "ball_raster_ragged": lambda: W.raster_ball_d10(width=0.403, pitch=0.0013, n_passes=4, n_edge=50,
                                                     rot_step_deg=0.5),
+    "floor_flat_d12_reduced": lambda: W.floor_flat_d12(width=0.5, pitch=0.002, rot_step_deg=2.0),
     "flat_tilt_runout": lambda: Workload("flat_tilt", ToolSpec("flat", 3.0, 3, [35.0, 38.0, 41.0], n_edge=20,
                                                                n_end=80, runout_mm=0.008),
                                          ProcessSpec(fz=0.05, rpm=6000, rot_step_deg=1.0, ap=0.2, tilt_deg=4.0,
@@ -57,7 +58,7 @@ def test_small_parity(ctx, F, oracle_mod, name, prec):
     if prec == "fp64":
         assert c[1] == ref.stats["cutting"], (c, ref.stats)
     else:
-        assert abs(int(c[1]) - ref.stats["cutting"]) <= 1e-6 * ref.stats["cutting"] + 2
+        assert abs(int(c[1]) - ref.stats["cutting"]) <= 1e-5 * ref.stats["cutting"] + 2
     assert c[0] >= c[1]
     r = ctx.roughness(H)
     ro = oracle_mod.roughness(ref.H)
