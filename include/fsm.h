@@ -205,6 +205,20 @@ fsm_status fsm_destroy_process(fsm_ctx* ctx, fsm_process* proc);
 fsm_status fsm_predict_surface(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc,
                                void* d_heights, const fsm_predict_opts* opts, void* stream);
 
+/* Autotuner (no counterpart in the paper, whose CPU loops have no launch
+ * shape): times up to max_candidates (0 = all) sweep configurations -- tile
+ * shape and resident CTAs per SM -- on this tool and process, writing into
+ * d_heights, and returns the fastest in *best (d_counters and sweep_events
+ * cleared) with its sweep time in *best_ms (host). The choice is recorded in
+ * the context: later fsm_predict_surface calls with the same tool/process
+ * shape (precision, tool kind, teeth, edge points, steps per revolution,
+ * grid size and pitch) and no tile override use it. Synchronises the stream.
+ * The map contents afterwards are those of the last candidate run (all
+ * candidates compute the same map; FP32 maps may differ in the last
+ * rounding between tile shapes). */
+fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc, void* d_heights,
+                        int32_t max_candidates, fsm_predict_opts* best, float* best_ms, void* stream);
+
 /* Roughness of a device height map (FSM_FP64 doubles or FSM_FP32 floats),
  * computed on the device in FP64 with a fixed reduction order (results do not
  * depend on launch timing). Writes one fsm_roughness_out to DEVICE memory

@@ -264,9 +264,30 @@ fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* sm
     return FSM_OK;
 }
 
+std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%.6g/%d/%d/%.6g", p.precision, t.kind, t.n_teeth,
+             t.n_edge + (t.kind == FSM_TOOL_FLAT ? t.n_end : 0), (int)steps_per_rev(p.rot_step_deg), t.diameter,
+             p.nx, p.ny, p.pitch);
+    return buf;
+}
+
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st) {
-    const Shape sh = pick_shape(p, opts);
+    Shape sh = pick_shape(p, opts);
+    fsm_predict_opts tuned_opts;
+    if (!opts || opts->tile_x <= 0) {  // an autotuned shape for this workload, if any
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->tuned.find(tune_key(t, p));
+        if (it != ctx->tuned.end()) {
+            sh.tile_x = it->second[0];
+            sh.tile_y = it->second[1];
+            if (opts) tuned_opts = *opts;
+            else memset(&tuned_opts, 0, sizeof tuned_opts);
+            tuned_opts.ctas_per_sm = it->second[2];
+            opts = &tuned_opts;
+        }
+    }
     size_t smem = 0;
     int bps = 0;
     fsm_status rc = sweep_config(ctx, p.precision, sh, &smem, &bps);
@@ -344,3 +365,68 @@ fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision,
 }
 
 }  // extern "C"
+
+extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc, void* d_heights,
+                                   int32_t max_candidates, fsm_predict_opts* best, float* best_ms, void* stream) {
+    if (!ctx || !tool || !proc || !d_heights || !best) return fail(FSM_E_INVALID, "NULL argument");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    // candidates: wide, short tiles first (they keep per-arc x ranges tight)
+    static const int c32[][2] = {{256, 48}, {512, 32}, {256, 64}, {384, 32}, {128, 64}, {512, 24}, {192, 64}, {128, 128}};
+    static const int c64[][2] = {{128, 64}, {256, 32}, {128, 32}, {64, 64}, {256, 24}, {192, 32}};
+    const bool f64 = proc->d.precision == FSM_FP64;
+    const int nshape = f64 ? 6 : 8;
+    cudaEvent_t ev[2];
+    if ((e = cudaEventCreate(&ev[0])) != cudaSuccess || (e = cudaEventCreate(&ev[1])) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    float best_t = 1e30f;
+    fsm_predict_opts bo;
+    memset(&bo, 0, sizeof bo);
+    int tried = 0;
+    fsm_status rc = FSM_OK;
+    for (int si = 0; si < nshape && rc == FSM_OK; ++si) {
+        for (int cps = 2; cps >= 1 && rc == FSM_OK; --cps) {
+            if (max_candidates > 0 && tried >= max_candidates) break;
+            fsm_predict_opts o;
+            memset(&o, 0, sizeof o);
+            o.tile_x = f64 ? c64[si][0] : c32[si][0];
+            o.tile_y = f64 ? c64[si][1] : c32[si][1];
+            o.block_threads = 256;
+            o.ctas_per_sm = cps;
+            size_t smem;
+            int bps;
+            Shape sh{o.tile_x, o.tile_y, o.block_threads};
+            if (sweep_config(ctx, proc->d.precision, sh, &smem, &bps) != FSM_OK) continue;
+            if (bps < cps) continue;
+            ++tried;
+            // one warm run, then one timed run
+            rc = predict_one(ctx, tool->d, proc->d, d_heights, &o, st);
+            if (rc != FSM_OK) break;
+            o.sweep_events[0] = ev[0];
+            o.sweep_events[1] = ev[1];
+            rc = predict_one(ctx, tool->d, proc->d, d_heights, &o, st);
+            if (rc != FSM_OK) break;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                rc = cuda_fail(e, "autotune synchronise");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (ms < best_t) {
+                best_t = ms;
+                bo = o;
+                bo.sweep_events[0] = bo.sweep_events[1] = nullptr;
+            }
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != FSM_OK) return rc;
+    if (tried == 0) return fail(FSM_E_INVALID, "no sweep configuration fits this device");
+    *best = bo;
+    if (best_ms) *best_ms = best_t;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tuned[tune_key(tool->d, proc->d)] = {bo.tile_x, bo.tile_y, bo.ctas_per_sm};
+    return FSM_OK;
+}

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -26,6 +28,8 @@ struct fsm_ctx {
     size_t smem_optin = 0;
     std::mutex mu;
     fsm::Server* server = nullptr;
+    // autotuned sweep shapes: workload signature -> (tile_x, tile_y, ctas_per_sm)
+    std::map<std::string, std::array<int, 3>> tuned;
 };
 
 namespace fsm {
@@ -69,6 +73,8 @@ struct Shape {
 };
 
 size_t align256(size_t v);
+// Key of the autotuner's table for a tool/process pair.
+std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p);
 Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o);
 // Fill a device plan from the descriptors. Table pointers are laid out from
 // `base`; returns the table bytes (call with base = NULL to size).

@@ -79,6 +79,7 @@ SIGNATURES = {
     "fsm_roughness_noalloc": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P],
     "fsm_predict_batch": [_P, C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), _P,
                           C.POINTER(PredictOpts), _P],
+    "fsm_autotune": [_P, _P, _P, _P, C.c_int32, C.POINTER(PredictOpts), C.POINTER(C.c_float), _P],
     "fsm_batch_create": [_P, C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), _P,
                          C.POINTER(PredictOpts), C.POINTER(_P)],
     "fsm_batch_run": [_P, _P, _P],
@@ -243,6 +244,16 @@ class Context:
         o = self._opts(tile, threads, counters, events, ctas_per_sm)
         self._call("fsm_predict_surface", self.ptr, tool.ptr, proc.ptr, out.data_ptr(),
                    C.byref(o) if o is not None else None, _stream_ptr(stream))
+
+    def autotune(self, tool: _Handle, proc: _Handle, out, max_candidates: int = 0, stream=None) -> dict:
+        """fsm_autotune: time sweep configurations on this workload; the
+        choice is also recorded in the context for later predictions."""
+        best = PredictOpts()
+        ms = C.c_float()
+        self._call("fsm_autotune", self.ptr, tool.ptr, proc.ptr, out.data_ptr(), int(max_candidates),
+                   C.byref(best), C.byref(ms), _stream_ptr(stream))
+        return {"tile": (best.tile_x, best.tile_y), "threads": best.block_threads,
+                "ctas_per_sm": best.ctas_per_sm, "sweep_ms": ms.value}
 
     def roughness_async(self, heights, precision: int, out_buf, n_rows=10, n_cols=10, stream=None) -> None:
         ny, nx = heights.shape
