@@ -103,11 +103,12 @@ static int64_t steps_per_rev(const orc_process* p) {
 
 static int valid(const orc_tool* t, const orc_process* p) {
     if (!t || !p) return 0;
-    if (t->kind != ORC_FLAT && t->kind != ORC_BALL) return 0;
+    if (t->kind != ORC_FLAT && t->kind != ORC_BALL && t->kind != ORC_INSERT) return 0;
+    if (t->kind == ORC_INSERT && !(t->insert_radius > 0.0)) return 0;
     if (t->n_teeth < 1 || t->n_teeth > ORC_MAX_TEETH) return 0;
     if (t->n_edge < 2) return 0;
     if (t->kind == ORC_FLAT && (t->n_end == 1 || t->n_end < 0)) return 0;
-    if (t->kind == ORC_BALL && t->n_end != 0) return 0;
+    if (t->kind != ORC_FLAT && t->n_end != 0) return 0;
     if (!(t->diameter > 0.0)) return 0;
     if (steps_per_rev(p) < 0) return 0;
     if (!(p->fz > 0.0) || !(p->ap > 0.0) || !(p->pitch > 0.0)) return 0;
@@ -122,6 +123,22 @@ int orc_points_per_tooth(const orc_tool* t, int refine) {
     int edge = (t->n_edge - 1) * refine + 1;
     int end = (t->kind == ORC_FLAT && t->n_end >= 2) ? (t->n_end - 1) * refine + 1 : 0;
     return edge + end;
+}
+
+/* Round insert (Section 2.2, Eq. eq_tool_point_p_equation): N points with
+ * l uniform in [-dL, dL], dL = max(sqrt(R^2 - (R - ap)^2), fz / (2 cos g_f)),
+ * on the lower semicircle z = R - sqrt(R^2 - l^2) (cutting-edge frame, origin
+ * at the insert's lowest point). dL is capped at R (the semicircle's end). */
+static void insert_point(const orc_tool* t, const orc_process* p, int refine, int j, double* l, double* z) {
+    double R = t->insert_radius;
+    int edge = (t->n_edge - 1) * refine + 1;
+    double imm = R - p->ap;
+    double dl_ap = p->ap >= R ? R : sqrt(R * R - imm * imm);
+    double dl_fz = p->fz / (2.0 * cos(t->rake_f_deg * DEG));
+    double dL = dl_ap > dl_fz ? dl_ap : dl_fz;
+    if (dL > R) dL = R;
+    *l = -dL + 2.0 * dL * ((double)j / (double)(edge - 1));
+    *z = R - sqrt(R * R - (*l) * (*l));
 }
 
 /* Radius and height (in the tool frame, origin at the tool tip on the axis)
@@ -162,8 +179,36 @@ static void profile_point(const orc_tool* t, const orc_process* p, int refine,
 /* T_CT for an end mill: place the profile point at the tooth's angular
  * position, lagged by the helix (psi = h tan(beta) / (D/2)), and offset by
  * the axis runout that rotates with the spindle. */
+/* T_CT of Eq. eq_cutting_edge_to_tool for insert K (0-based, so the
+ * paper's K-1 is K here): rake rotation and the translation
+ * (D/2 + K eps_r, 0, K eps_a). */
+static mat4 m_insert_to_tool(const orc_tool* t, int K) {
+    double gf = t->rake_f_deg * DEG, gp = t->rake_p_deg * DEG;
+    mat4 m = m_identity();
+    m.a[0][0] = cos(gf);  m.a[0][1] = sin(gf) * cos(gp); m.a[0][2] = sin(gf) * sin(gp);
+    m.a[1][0] = -sin(gf); m.a[1][1] = cos(gf) * cos(gp); m.a[1][2] = cos(gf) * sin(gp);
+    m.a[2][0] = 0.0;      m.a[2][1] = -sin(gp);          m.a[2][2] = cos(gp);
+    m.a[0][3] = 0.5 * t->diameter + (double)K * t->eps_r_mm;
+    m.a[1][3] = 0.0;
+    m.a[2][3] = (double)K * t->eps_a_mm;
+    return m;
+}
+
 static void tool_point(const orc_tool* t, const orc_process* p, int refine,
                        int K, int j, double out[3]) {
+    if (t->kind == ORC_INSERT) {
+        /* insert K sits at -tooth_deg[K] about the axis (the 2 pi (K-1)/z_n
+         * of Eq. eq_tool_to_spindle), then the spindle-axis runout */
+        double l, z;
+        insert_point(t, p, refine, j, &l, &z);
+        double lam = t->runout_phase_deg * DEG;
+        mat4 m = m_mul(m_mul(m_translate(t->runout_mm * cos(lam), t->runout_mm * sin(lam), 0.0),
+                             m_rot_z(-t->tooth_deg[K] * DEG)),
+                       m_insert_to_tool(t, K));
+        double pc[3] = {l, 0.0, z};
+        m_apply(&m, pc, out);
+        return;
+    }
     double r, h;
     profile_point(t, p, refine, j, &r, &h);
     double psi = h * tan(t->helix_deg[K] * DEG) / (0.5 * t->diameter);

@@ -37,7 +37,7 @@ extern "C" {
 
 #define ORC_MAX_TEETH 16
 
-enum { ORC_FLAT = 0, ORC_BALL = 1 };
+enum { ORC_FLAT = 0, ORC_BALL = 1, ORC_INSERT = 2 };
 
 /* Cutting tool. Angles in degrees, lengths in mm. */
 typedef struct {
@@ -50,6 +50,12 @@ typedef struct {
     double tooth_deg[ORC_MAX_TEETH];  /* angular position of each tooth */
     double runout_mm;      /* axis offset rho, rotates with the spindle */
     double runout_phase_deg; /* its phase lambda in the rotating frame */
+    /* round indexable inserts (ORC_INSERT, Eq. eq_point_p_equation and
+     * eq_cutting_edge_to_tool): insert radius R, radial and axial rake, and
+     * the per-insert radial/axial runout steps (insert K is offset K*eps) */
+    double insert_radius;
+    double rake_f_deg, rake_p_deg;
+    double eps_r_mm, eps_a_mm;
 } orc_tool;
 
 /* Process and workpiece grid. */

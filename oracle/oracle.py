@@ -25,6 +25,8 @@ class OrcTool(C.Structure):
         ("diameter", C.c_double),
         ("helix_deg", C.c_double * MAX_TEETH), ("tooth_deg", C.c_double * MAX_TEETH),
         ("runout_mm", C.c_double), ("runout_phase_deg", C.c_double),
+        ("insert_radius", C.c_double), ("rake_f_deg", C.c_double), ("rake_p_deg", C.c_double),
+        ("eps_r_mm", C.c_double), ("eps_a_mm", C.c_double),
     ]
 
 
@@ -84,7 +86,7 @@ def lib():
 
 def make_tool(tool) -> OrcTool:
     t = OrcTool()
-    t.kind = {"flat": 0, "ball": 1}[tool.kind]
+    t.kind = {"flat": 0, "ball": 1, "insert": 2}[tool.kind]
     t.n_teeth = tool.n_teeth
     t.n_edge = tool.n_edge
     t.n_end = tool.n_end if tool.kind == "flat" else 0
@@ -94,6 +96,11 @@ def make_tool(tool) -> OrcTool:
         t.tooth_deg[k] = a
     t.runout_mm = tool.runout_mm
     t.runout_phase_deg = tool.runout_phase_deg
+    t.insert_radius = tool.insert_radius
+    t.rake_f_deg = tool.rake_f_deg
+    t.rake_p_deg = tool.rake_p_deg
+    t.eps_r_mm = tool.eps_r_mm
+    t.eps_a_mm = tool.eps_a_mm
     return t
 
 

@@ -38,8 +38,8 @@ CELL_OFFSET = (0.318309886183791, 0.367879441171442)
 
 @dataclass
 class ToolSpec:
-    kind: str                     # "flat" or "ball"
-    diameter: float               # mm
+    kind: str                     # "flat", "ball" or "insert" (round inserts)
+    diameter: float               # mm (inserts: radius of the inserts' lowest points x 2)
     n_teeth: int
     helix_deg: List[float]        # one per tooth
     tooth_deg: Optional[List[float]] = None  # angular positions; None = even pitch
@@ -47,6 +47,11 @@ class ToolSpec:
     runout_phase_deg: float = 0.0
     n_edge: int = 50              # flank (flat) / meridian (ball) points
     n_end: int = 0                # flat bottom-edge points (0 or >= 2)
+    insert_radius: float = 0.0    # round insert radius R
+    rake_f_deg: float = 0.0       # radial rake (gamma_f)
+    rake_p_deg: float = 0.0       # axial rake (gamma_p)
+    eps_r_mm: float = 0.0         # insert K sits K * eps_r further out ...
+    eps_a_mm: float = 0.0         # ... and K * eps_a higher
 
     def teeth_angles(self) -> List[float]:
         if self.tooth_deg is not None:
@@ -116,7 +121,7 @@ def plan_passes(tool: ToolSpec, fz: float, rot_step_deg: float, width: float,
     both ends. Returns (pass_x0, pass_y0, steps_per_pass)."""
     steps_per_rev = int(round(360.0 / rot_step_deg))
     feed_per_step = tool.n_teeth * fz / steps_per_rev
-    overtravel = 0.5 * tool.diameter + tool.runout_mm + ap + 2.0 * pitch
+    overtravel = 0.5 * tool.diameter + tool.runout_mm + ap + 2.0 * pitch + tool.insert_radius
     half_steps = int(math.ceil((0.5 * width + overtravel) / feed_per_step))
     pass_x0 = centre_x - half_steps * feed_per_step
     return pass_x0, first_y, 2 * half_steps + 1
@@ -183,6 +188,46 @@ def floor_flat_d12(seed: int = 2603, precision: str = "fp32", width: float = 20.
                        pass_y0=py, steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx,
                        ny=ny, n_passes=n_passes, ae=ae, precision=precision)
     return Workload("floor_flat_d12", tool, proc)
+
+
+# Case 2 of the paper (Section 4.2.1): face mill R217.29-2520.3-05.2.070,
+# cutting diameter 10 mm, two round inserts of radius 5 mm, radial rake 0.6,
+# axial rake 0; (vc m/min, fz mm, ap mm, eps_r mm, eps_a mm) per case
+PAPER_CASES = [(170, 0.6, 0.5, 0.011, 0.003), (200, 0.4, 0.4, -0.026, 0.009), (230, 0.5, 0.3, -0.013, 0.007)]
+# the nine conditions of the computational-performance study (Section 4.3),
+# 10 x 5 mm, zero run-out: (vc, fz, ap)
+PAPER_GRID = [(170, 0.4, 0.3), (170, 0.5, 0.4), (170, 0.6, 0.5), (200, 0.4, 0.3), (200, 0.5, 0.4),
+              (200, 0.6, 0.5), (230, 0.4, 0.3), (230, 0.5, 0.4), (230, 0.6, 0.5)]
+
+
+def paper_insert_tool(eps_r: float = 0.0, eps_a: float = 0.0, n_edge: int = 100) -> ToolSpec:
+    return ToolSpec("insert", 10.0, 2, [0.0], n_edge=n_edge, insert_radius=5.0, rake_f_deg=0.6, rake_p_deg=0.0,
+                    eps_r_mm=eps_r, eps_a_mm=eps_a)
+
+
+def face_mill_insert(vc: float, fz: float, ap: float, eps_r: float = 0.0, eps_a: float = 0.0,
+                     precision: str = "fp32", pitch: float = 0.005, length: float = 10.0, width: float = 5.0,
+                     rot_step_deg: float = 0.1, n_edge: int = 100) -> Workload:
+    """One face-milling pass of the paper's insert cutter over a length x
+    width patch (feed along +X through the patch centre). The grid pitch,
+    angle step and edge-point count are not stated by the paper (chosen);
+    rpm follows from vc and the 10 mm cutting diameter (it labels time only)."""
+    tool = paper_insert_tool(eps_r, eps_a, n_edge)
+    rpm = 1000.0 * vc / (math.pi * tool.diameter)
+    x0, y0, nx, ny = _patch(length, width, pitch)
+    px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, 0.0, ap, pitch)
+    proc = ProcessSpec(fz=fz, rpm=rpm, rot_step_deg=rot_step_deg, ap=ap, pass_x0=px, pass_y0=py,
+                       steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx, ny=ny, precision=precision)
+    return Workload("face_mill_vc%g_fz%g_ap%g" % (vc, fz, ap), tool, proc)
+
+
+def paper_case(i: int, **kw) -> Workload:
+    vc, fz, ap, er, ea = PAPER_CASES[i]
+    return face_mill_insert(vc, fz, ap, er, ea, **kw)
+
+
+def paper_grid(**kw) -> List[Workload]:
+    return [face_mill_insert(vc, fz, ap, **kw) for vc, fz, ap in PAPER_GRID]
 
 
 def _lhs(rng: np.random.Generator, n: int, dims: int) -> np.ndarray:
