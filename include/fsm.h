@@ -47,7 +47,7 @@ typedef enum {
     FSM_E_STATE = -6          /* wrong call order (e.g. unknown ticket) */
 } fsm_status;
 
-enum { FSM_TOOL_FLAT = 0, FSM_TOOL_BALL = 1 };
+enum { FSM_TOOL_FLAT = 0, FSM_TOOL_BALL = 1, FSM_TOOL_INSERT = 2 };
 enum { FSM_FP64 = 0, FSM_FP32 = 1 };
 
 typedef struct fsm_ctx fsm_ctx;
@@ -65,10 +65,19 @@ typedef struct fsm_process fsm_process;
  *             h tan(helix) / (D/2) radians against the rotation.
  *   tooth_deg angular position of each tooth (tooth K sits -tooth_deg[K]
  *             from the spindle reference, the sign of Eq. eq_tool_to_spindle).
+ *             FSM_TOOL_INSERT: the paper's face mill with round indexable
+ *             inserts of radius insert_radius (Eq. eq_point_p_equation):
+ *             n_edge points on the insert's lower semicircle with
+ *             l uniform in [-dL, dL], dL = max(sqrt(R^2 - (R-ap)^2),
+ *             fz / (2 cos rake_f)) capped at R (Eq. eq_tool_point_p_equation);
+ *             placed by Eq. eq_cutting_edge_to_tool: radial/axial rake
+ *             rotation, lowest point at radius D/2 + K eps_r and height
+ *             K eps_a for insert K = 0..n_teeth-1 (the paper's K-1).
  *   runout    spindle-axis offset of radius runout_mm at runout_phase_deg in
  *             the rotating frame.
  * Validation: 1 <= n_teeth <= 16, n_edge >= 2, n_end == 0 or >= 2 (flat),
- * n_end == 0 (ball), D > 0, runout >= 0, all values finite. */
+ * n_end == 0 (ball, insert), D > 0, runout >= 0, insert_radius > 0 (insert),
+ * all values finite. helix_deg is ignored for inserts. */
 typedef struct {
     int32_t kind;
     int32_t n_teeth;
@@ -79,6 +88,11 @@ typedef struct {
     double tooth_deg[FSM_MAX_TEETH];
     double runout_mm;
     double runout_phase_deg;
+    double insert_radius;
+    double rake_f_deg;
+    double rake_p_deg;
+    double eps_r_mm;
+    double eps_a_mm;
 } fsm_tool_desc;
 
 /* Cutting conditions, tool path and sampling grid (Sections 2.1-2.2).

@@ -45,12 +45,20 @@ static int64_t steps_per_rev(double step_deg) {
 
 static fsm_status check_tool(const fsm_tool_desc* t) {
     if (!t) return fail(FSM_E_INVALID, "tool descriptor is NULL");
-    if (t->kind != FSM_TOOL_FLAT && t->kind != FSM_TOOL_BALL) return fail(FSM_E_INVALID, "unknown tool kind");
+    if (t->kind != FSM_TOOL_FLAT && t->kind != FSM_TOOL_BALL && t->kind != FSM_TOOL_INSERT)
+        return fail(FSM_E_INVALID, "unknown tool kind");
+    if (t->kind == FSM_TOOL_INSERT) {
+        if (!(t->insert_radius > 0.0) || !finite(t->insert_radius)) return fail(FSM_E_INVALID, "insert_radius must be > 0");
+        const double v[] = {t->rake_f_deg, t->rake_p_deg, t->eps_r_mm, t->eps_a_mm};
+        for (double x : v)
+            if (!finite(x)) return fail(FSM_E_INVALID, "non-finite insert parameter");
+        if (fabs(t->rake_f_deg) >= 80.0 || fabs(t->rake_p_deg) >= 80.0) return fail(FSM_E_INVALID, "|rake| < 80");
+    }
     if (t->n_teeth < 1 || t->n_teeth > FSM_MAX_TEETH) return fail(FSM_E_INVALID, "n_teeth must be 1..16");
     if (t->n_edge < 2) return fail(FSM_E_INVALID, "n_edge must be >= 2");
     if (t->kind == FSM_TOOL_FLAT && (t->n_end < 0 || t->n_end == 1))
         return fail(FSM_E_INVALID, "n_end must be 0 or >= 2");
-    if (t->kind == FSM_TOOL_BALL && t->n_end != 0) return fail(FSM_E_INVALID, "a ball end has n_end == 0");
+    if (t->kind != FSM_TOOL_FLAT && t->n_end != 0) return fail(FSM_E_INVALID, "only a flat end has n_end > 0");
     if ((int64_t)t->n_teeth * (t->n_edge + t->n_end) > (1 << 22))
         return fail(FSM_E_INVALID, "too many edge points");
     if (!(t->diameter > 0.0) || !finite(t->diameter)) return fail(FSM_E_INVALID, "diameter must be > 0");
@@ -114,9 +122,14 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     s->runout_mm = t.runout_mm;
     s->runout_phase_deg = t.runout_phase_deg;
     for (int k = 0; k < FSM_MAX_TEETH; ++k) {
-        s->helix_deg[k] = t.helix_deg[k];
+        s->helix_deg[k] = t.kind == FSM_TOOL_INSERT ? 0.0 : t.helix_deg[k];
         s->tooth_deg[k] = t.tooth_deg[k];
     }
+    s->insert_radius = t.insert_radius;
+    s->rake_f_deg = t.rake_f_deg;
+    s->rake_p_deg = t.rake_p_deg;
+    s->eps_r_mm = t.eps_r_mm;
+    s->eps_a_mm = t.eps_a_mm;
     s->fz = p.fz;
     s->rot_step_deg = p.rot_step_deg;
     s->phase0_deg = p.phase0_deg;

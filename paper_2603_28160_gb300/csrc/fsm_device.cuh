@@ -43,6 +43,7 @@ struct Surface {
     double diameter, runout_mm, runout_phase_deg;
     double helix_deg[kMaxTeeth];
     double tooth_deg[kMaxTeeth];
+    double insert_radius, rake_f_deg, rake_p_deg, eps_r_mm, eps_a_mm;
     // ---- process (inputs) ----
     double fz, rot_step_deg, phase0_deg;
     int32_t rot_sense, n_passes;

@@ -87,26 +87,46 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
     float rx = 0.f, ry = 0.f;
     for (int idx = first; idx < NE; idx += stride) {
         const int K = idx / E, j = idx - K * E;
-        double r, h;
-        if (sf.kind == 0) {  // flat: bottom edge then flank
-            if (j < sf.n_end) {
-                r = R * ((double)j / (double)(sf.n_end - 1));
-                h = 0.0;
-            } else {
-                r = R;
-                h = sf.ap * ((double)(j - sf.n_end) / (double)(sf.n_edge - 1));
+        double qx, qy, qz;
+        if (sf.kind == 2) {  // round insert: lower semicircle, rake, per-insert runout, tooth angle
+            const double Ri = sf.insert_radius;
+            const double gf = deg2rad(sf.rake_f_deg), gp = deg2rad(sf.rake_p_deg);
+            const double dl_ap = sf.ap >= Ri ? Ri : sqrt(Ri * Ri - (Ri - sf.ap) * (Ri - sf.ap));
+            const double dl_fz = sf.fz / (2.0 * cos(gf));
+            const double dL = fmin(fmax(dl_ap, dl_fz), Ri);
+            const double l = -dL + 2.0 * dL * ((double)j / (double)(E - 1));
+            const double zc = Ri - sqrt(Ri * Ri - l * l);
+            // insert frame -> tool frame (x along the radius at the tooth's reference)
+            const double xt = cos(gf) * l + sin(gf) * sin(gp) * zc + R + (double)K * sf.eps_r_mm;
+            const double yt = -sin(gf) * l + cos(gf) * sin(gp) * zc;
+            const double zt = cos(gp) * zc + (double)K * sf.eps_a_mm;
+            const double ta = -deg2rad(sf.tooth_deg[K]);
+            const double lam = deg2rad(sf.runout_phase_deg);
+            qx = cos(ta) * xt - sin(ta) * yt + sf.runout_mm * cos(lam);
+            qy = sin(ta) * xt + cos(ta) * yt + sf.runout_mm * sin(lam);
+            qz = zt;
+        } else {
+            double r, h;
+            if (sf.kind == 0) {  // flat: bottom edge then flank
+                if (j < sf.n_end) {
+                    r = R * ((double)j / (double)(sf.n_end - 1));
+                    h = 0.0;
+                } else {
+                    r = R;
+                    h = sf.ap * ((double)(j - sf.n_end) / (double)(sf.n_edge - 1));
+                }
+            } else {              // ball: uniform in polar angle over the engaged cap
+                double kappa = kap[0] + (kap[1] - kap[0]) * ((double)j / (double)(E - 1));
+                r = R * sin(kappa);
+                h = R * (1.0 - cos(kappa));
             }
-        } else {              // ball: uniform in polar angle over the engaged cap
-            double kappa = kap[0] + (kap[1] - kap[0]) * ((double)j / (double)(E - 1));
-            r = R * sin(kappa);
-            h = R * (1.0 - cos(kappa));
+            double psi = h * tan(deg2rad(sf.helix_deg[K])) / R;   // helix lag
+            double alpha = -deg2rad(sf.tooth_deg[K]) - sigma * psi;
+            double lam = deg2rad(sf.runout_phase_deg);
+            qx = r * cos(alpha) + sf.runout_mm * cos(lam);
+            qy = r * sin(alpha) + sf.runout_mm * sin(lam);
+            qz = h;
         }
-        double psi = h * tan(deg2rad(sf.helix_deg[K])) / R;   // helix lag
-        double alpha = -deg2rad(sf.tooth_deg[K]) - sigma * psi;
-        double lam = deg2rad(sf.runout_phase_deg);
-        double qx = r * cos(alpha) + sf.runout_mm * cos(lam);
-        double qy = r * sin(alpha) + sf.runout_mm * sin(lam);
-        double qz = h;
         double u[3], v[3], w[3];
         for (int d = 0; d < 3; ++d) {
             u[d] = A[3 * d] * qx + A[3 * d + 1] * qy;

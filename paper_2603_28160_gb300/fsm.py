@@ -30,7 +30,8 @@ class ToolDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_teeth", C.c_int32), ("n_edge", C.c_int32), ("n_end", C.c_int32),
                 ("diameter", C.c_double), ("helix_deg", C.c_double * MAX_TEETH),
                 ("tooth_deg", C.c_double * MAX_TEETH), ("runout_mm", C.c_double),
-                ("runout_phase_deg", C.c_double)]
+                ("runout_phase_deg", C.c_double), ("insert_radius", C.c_double), ("rake_f_deg", C.c_double),
+                ("rake_p_deg", C.c_double), ("eps_r_mm", C.c_double), ("eps_a_mm", C.c_double)]
 
 
 class ProcessDesc(C.Structure):
@@ -119,7 +120,7 @@ def lib() -> C.CDLL:
 
 def tool_desc(t: ToolSpec) -> ToolDesc:
     d = ToolDesc()
-    d.kind = {"flat": 0, "ball": 1}[t.kind]
+    d.kind = {"flat": 0, "ball": 1, "insert": 2}[t.kind]
     d.n_teeth = t.n_teeth
     d.n_edge = t.n_edge
     d.n_end = t.n_end if t.kind == "flat" else 0
@@ -129,6 +130,11 @@ def tool_desc(t: ToolSpec) -> ToolDesc:
         d.tooth_deg[k] = a
     d.runout_mm = t.runout_mm
     d.runout_phase_deg = t.runout_phase_deg
+    d.insert_radius = t.insert_radius
+    d.rake_f_deg = t.rake_f_deg
+    d.rake_p_deg = t.rake_p_deg
+    d.eps_r_mm = t.eps_r_mm
+    d.eps_a_mm = t.eps_a_mm
     return d
 
 

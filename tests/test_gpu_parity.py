@@ -35,6 +35,13 @@ SMALL = {
     "ball_raster_ragged": lambda: W.raster_ball_d10(width=0.403, pitch=0.0013, n_passes=4, n_edge=50,
                                                     rot_step_deg=0.5),
     "floor_flat_d12_reduced": lambda: W.floor_flat_d12(width=0.5, pitch=0.002, rot_step_deg=2.0),
+    # the paper's Case 2 face mill (round inserts, rake, per-insert runout), reduced patch
+    "paper_case1_insert": lambda: W.paper_case(0, length=0.6, width=0.4, pitch=0.004, rot_step_deg=0.25,
+                                               n_edge=60),
+    "paper_case2_insert": lambda: W.paper_case(1, length=0.6, width=0.4, pitch=0.004, rot_step_deg=0.25,
+                                               n_edge=60),
+    "paper_case3_insert": lambda: W.paper_case(2, length=0.6, width=0.4, pitch=0.004, rot_step_deg=0.25,
+                                               n_edge=60),
     "flat_tilt_runout": lambda: Workload("flat_tilt", ToolSpec("flat", 3.0, 3, [35.0, 38.0, 41.0], n_edge=20,
                                                                n_end=80, runout_mm=0.008),
                                          ProcessSpec(fz=0.05, rpm=6000, rot_step_deg=1.0, ap=0.2, tilt_deg=4.0,
