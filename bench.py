@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-paper", action="store_true")
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -339,6 +340,73 @@ def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
                               "speedup": fp64_ms / fp32_ms}}
 
 
+# mean optimised-FSM time per 10 x 5 mm surface over the nine conditions of
+# the paper's computational-performance table (Section 4.3, its CPU)
+PAPER_EFSM_S_MEAN = 0.5711
+# fixed time step that reproduces that table's trajectory-point counts
+PAPER_DT_S = 2e-7
+
+
+def paper_case2_leg(ctx, F, flush, steps=3):
+    """The paper's own performance workload: the round-insert face mill of
+    Case 2 over 10 x 5 mm at 5 um, zero runout, the nine (vc, fz, ap)
+    conditions of Section 4.3. FP64 one surface at a time, and FP32 as one
+    prepared batch of nine, each with roughness."""
+    import torch
+    from paper_2603_28160_gb300 import workloads as W
+    out = {}
+    for prec in ("fp64", "fp32"):
+        ws = W.paper_grid(precision=prec, dt_s=PAPER_DT_S)
+        tools = [ctx.tool(w.tool) for w in ws]
+        procs = [ctx.process(w.process) for w in ws]
+        outs = [F.heights_tensor(w.process) for w in ws]
+        rough = torch.zeros(len(ws) * F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ctx.predict_batch(tools, procs, outs, rough_buf=rough, counters=cnt)
+        torch.cuda.synchronize()
+        cutting = int(cnt[1].item())
+        code = F.FSM_FP64 if prec == "fp64" else F.FSM_FP32
+        b = ctx.batch(tools, procs, outs, rough_buf=rough) if prec == "fp32" else None
+
+        def one_step():
+            if b is not None:
+                b.run()
+            else:
+                for t_, p_, o_ in zip(tools, procs, outs):
+                    ctx.predict_surface(t_, p_, o_)
+                    ctx.roughness_async(o_, code, rough)
+        for _ in range(3):
+            one_step()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            one_step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        mean = sum(ms) / len(ms)
+        if b is not None:
+            b.close()
+        out[prec] = {"ms_per_9_surfaces": mean, "ms_per_surface": mean / len(ws),
+                     "surfaces_per_s": len(ws) / (mean / 1e3), "cutting": cutting,
+                     "value": cutting / (mean / 1e3), "unit": UNIT,
+                     "launch": "prepared batch of 9" if prec == "fp32" else "one surface at a time"}
+        del outs
+    torch.cuda.empty_cache()
+    grid = W.paper_grid(dt_s=PAPER_DT_S)
+    return {"workload": "paper Case 2 face mill (2 round inserts R=5, D=10, rake 0.6 deg), 10x5 mm @ 5 um, "
+                        "zero runout, 9 (vc, fz, ap) conditions of Section 4.3, 100 edge pts, fixed 0.2 us "
+                        "time step (the table's trajectory-point counts)",
+            "cells_per_surface": grid[0].process.cells,
+            "time_steps_total": sum(w.process.trajectory_steps for w in grid),
+            "trajectory_points_total": sum(w.trajectory_points for w in grid), "steps": steps, **out,
+            "paper_efsm_s_per_surface_mean": PAPER_EFSM_S_MEAN,
+            "paper_note": "context only: the paper's optimised CPU FSM on its own machine and discretisation"}
+
+
 def served_leg(ctx, F, seconds, rate, seed=5):
     """Poisson request stream through fsm_submit/fsm_poll (continuous batching,
     120 GB admission budget, 70 % FP32 / 30 % FP64, 0.25-25 Mcells)."""
@@ -474,6 +542,9 @@ def gb300_arm(args):
     large = None
     if not args.skip_large and rank == 0:
         large = large_grid_leg(ctx, F, flush)
+    paper = None
+    if not args.skip_paper and rank == 0:
+        paper = paper_case2_leg(ctx, F, flush)
     batched = None
     if not args.skip_batch:
         batched = batched_leg(ctx, F, args.batch_size, args.batch_steps, rank, ws)
@@ -532,6 +603,7 @@ def gb300_arm(args):
         "wall_s": wall,
         "fp64_single_surface": fp64,
         "large_grid": large,
+        "paper_case2": paper,
         "batched": batched,
         "served": served,
         "src_hash": src_hash(),

@@ -207,15 +207,30 @@ def paper_insert_tool(eps_r: float = 0.0, eps_a: float = 0.0, n_edge: int = 100)
 
 def face_mill_insert(vc: float, fz: float, ap: float, eps_r: float = 0.0, eps_a: float = 0.0,
                      precision: str = "fp32", pitch: float = 0.005, length: float = 10.0, width: float = 5.0,
-                     rot_step_deg: float = 0.1, n_edge: int = 100) -> Workload:
+                     rot_step_deg: float = 0.1, n_edge: int = 100, dt_s: Optional[float] = None) -> Workload:
     """One face-milling pass of the paper's insert cutter over a length x
     width patch (feed along +X through the patch centre). The grid pitch,
     angle step and edge-point count are not stated by the paper (chosen);
-    rpm follows from vc and the 10 mm cutting diameter (it labels time only)."""
+    rpm follows from vc and the 10 mm cutting diameter.
+
+    dt_s=None: fixed angle step rot_step_deg, and the pass overruns the patch
+    so the whole cutter clears it (rpm then labels time only).
+    dt_s given: fixed time step, as the paper's performance study implies --
+    its trajectory-point counts equal (tool-centre travel) / (vf * dt) with a
+    travel of the patch length (Section 4.3 table; 2e-7 s reproduces them).
+    The angle step is the nearest one with a whole number of steps per
+    revolution, and the tool centre runs from the patch's start to its end."""
     tool = paper_insert_tool(eps_r, eps_a, n_edge)
     rpm = 1000.0 * vc / (math.pi * tool.diameter)
     x0, y0, nx, ny = _patch(length, width, pitch)
-    px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, 0.0, ap, pitch)
+    if dt_s is None:
+        px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, 0.0, ap, pitch)
+    else:
+        steps_per_rev = int(round(60.0 / (rpm * dt_s)))
+        rot_step_deg = 360.0 / steps_per_rev
+        feed_per_step = tool.n_teeth * fz / steps_per_rev
+        spp = int(round(nx * pitch / feed_per_step))
+        px, py = x0 - CELL_OFFSET[0] * pitch, 0.0
     proc = ProcessSpec(fz=fz, rpm=rpm, rot_step_deg=rot_step_deg, ap=ap, pass_x0=px, pass_y0=py,
                        steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx, ny=ny, precision=precision)
     return Workload("face_mill_vc%g_fz%g_ap%g" % (vc, fz, ap), tool, proc)

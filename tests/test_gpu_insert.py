@@ -44,13 +44,16 @@ def test_paper_case2_insert(oracle_mod, i, prec):
 
 
 def test_paper_grid_batched(oracle_mod):
-    """The nine cutting conditions of the paper's parameter grid as one
-    batched FP32 launch on 2 x 1 mm patches, each map against the oracle."""
+    """The nine cutting conditions of the paper's parameter grid, with the
+    fixed 0.2 us time step of its performance table, as one batched FP32
+    launch on 10 x 0.5 mm strips at 20 um (30 edge points), each map against
+    the oracle."""
     import torch
     from paper_2603_28160_gb300 import fsm as F
     ctx = F.Context(0)
-    ws = W.paper_grid(precision="fp32", length=2.0, width=1.0)
-    refs = W.paper_grid(precision="fp64", length=2.0, width=1.0)
+    kw = dict(length=10.0, width=0.5, pitch=0.02, n_edge=30, dt_s=2e-7)
+    ws = W.paper_grid(precision="fp32", **kw)
+    refs = W.paper_grid(precision="fp64", **kw)
     tools = [ctx.tool(w.tool) for w in ws]
     procs = [ctx.process(w.process) for w in ws]
     outs = [F.heights_tensor(w.process) for w in ws]

@@ -36,3 +36,17 @@ def test_performance_table_implies_a_fixed_time_step():
         assert fsm_s / efsm_s == pytest.approx(sp, abs=0.15)  # printed speedups, truncated
     mean = sum(r[6] for r in rows) / len(rows)  # mean of the printed speedups
     assert mean == pytest.approx(GOLD["performance"]["mean_speedup"], abs=0.05)
+
+
+def test_fixed_time_step_workload_reproduces_the_point_counts():
+    """With a 0.2 us step and the tool centre travelling the 10 mm patch, the
+    workload's time-step counts are the table's trajectory points (the printed
+    counts for vc = 230 m/min differ by a few steps: 1e-5 relative)."""
+    rows = GOLD["performance"]["rows"]
+    for w, row in zip(W.paper_grid(dt_s=2e-7), rows):
+        assert w.process.n_passes == 1
+        assert abs(w.process.steps_per_pass - row[3]) <= 2e-5 * row[3], (w.name, w.process.steps_per_pass, row[3])
+        spr = 360.0 / w.process.rot_step_deg
+        assert abs(spr - round(spr)) < 1e-9
+        rpm = 1000.0 * row[0] / (math.pi * 10.0)
+        assert 60.0 / (rpm * round(spr)) == pytest.approx(2e-7, rel=1e-4)
