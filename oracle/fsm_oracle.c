@@ -408,6 +408,48 @@ int orc_fsm(const orc_tool* t, const orc_process* p, double* H, uint8_t* flags,
 /* ------------------------------------------------------------------ */
 /* Brute-force inverse: per-cell minimum over a (refined) sample set.  */
 /* ------------------------------------------------------------------ */
+/* ------------------------------------------------------------------ */
+/* Trajectory map (Section 3.1, trajectory computation module): at each */
+/* time step, the lowest point of every cutting edge and its global     */
+/* coordinates, computed from the same transformed points as the map.   */
+/* ------------------------------------------------------------------ */
+int orc_trajectory(const orc_tool* t, const orc_process* p, int64_t s0, int64_t count,
+                   double* xyz, int32_t* jmin) {
+    if (!valid(t, p) || s0 < 0 || count < 0 || !xyz || !jmin) return -1;
+    int64_t total = (int64_t)p->n_passes * p->steps_per_pass;
+    if (s0 + count > total) return -1;
+    int E = orc_points_per_tooth(t, 1);
+    int N = t->n_teeth;
+    double* q = (double*)malloc(sizeof(double) * 3 * (size_t)E * N);
+    for (int K = 0; K < N; ++K)
+        for (int j = 0; j < E; ++j) tool_point(t, p, 1, K, j, q + 3 * (K * E + j));
+    mat4 A = m_orientation(p);
+    double z_ref = resolved_z_ref(t, p);
+    for (int64_t s = s0; s < s0 + count; ++s) {                 /* time step */
+        int pass = (int)(s / p->steps_per_pass);
+        mat4 T = step_matrix(t, p, &A, z_ref, 1, pass, s % p->steps_per_pass, 0);
+        for (int K = 0; K < N; ++K) {                           /* cutting edge */
+            double best[3] = {0.0, 0.0, INFINITY};
+            int32_t bj = -1;
+            for (int j = 0; j < E; ++j) {                       /* edge point */
+                double w[3];
+                m_apply(&T, q + 3 * (K * E + j), w);
+                if (w[2] < best[2]) {  /* strict: the first point in edge order wins a tie */
+                    best[0] = w[0]; best[1] = w[1]; best[2] = w[2];
+                    bj = j;
+                }
+            }
+            size_t r = (size_t)(s - s0) * N + K;
+            xyz[3 * r] = best[0];
+            xyz[3 * r + 1] = best[1];
+            xyz[3 * r + 2] = best[2];
+            jmin[r] = bj;
+        }
+    }
+    free(q);
+    return 0;
+}
+
 int orc_gather(const orc_tool* t, const orc_process* p, int refine,
                int i0, int k0, int ni, int nk, double* Hw) {
     if (!valid(t, p) || refine < 1 || ni < 1 || nk < 1 || !Hw) return -1;

@@ -16,6 +16,8 @@
  *     extension; the paper's face mill has a vertical axis),
  *   - binning by the sampling boundaries of Eq. eq_sampling_boundaries
  *     (half-open cells) and the per-cell minimum of Section 2.3,
+ *   - the trajectory map of Section 3.1 (lowest point of each cutting edge
+ *     at each time step, with its global coordinates),
  *   - the areal (Sa, Sq, Sp, Sv, Sz, Ssk, Sku) and line (Ra, Rz) roughness
  *     indicators named in Section 4.1.2 (ISO 25178-2 / ISO 4287 definitions;
  *     the paper gives no formulas).
@@ -128,6 +130,13 @@ int orc_fsm(const orc_tool* t, const orc_process* p, double* H,
  * boundaries, tested in the centre +- pitch/2 form. Hw[nk][ni]. */
 int orc_gather(const orc_tool* t, const orc_process* p, int refine,
                int i0, int k0, int ni, int nk, double* Hw);
+
+/* Trajectory map: for the global time steps s0 .. s0+count-1 (s = pass *
+ * steps_per_pass + local step) and every tooth K, the edge point of lowest
+ * workpiece z (the first in edge order among equal z) and its coordinates:
+ * xyz[((s-s0)*n_teeth + K)*3 + d], jmin[(s-s0)*n_teeth + K]. Returns 0 or -1. */
+int orc_trajectory(const orc_tool* t, const orc_process* p, int64_t s0, int64_t count,
+                   double* xyz, int32_t* jmin);
 
 /* Areal and profile roughness of H[ny][nx]. */
 int orc_roughness(const double* H, int nx, int ny, int n_rows, int n_cols,

@@ -79,6 +79,8 @@ def lib():
                               C.c_int]
         L.orc_gather.argtypes = [P(OrcTool), P(OrcProcess), C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.c_int, P(C.c_double)]
+        L.orc_trajectory.argtypes = [P(OrcTool), P(OrcProcess), C.c_int64, C.c_int64, P(C.c_double),
+                                     P(C.c_int32)]
         L.orc_roughness.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_int, C.c_int, P(OrcRough)]
         _lib = L
     return _lib
@@ -173,6 +175,22 @@ def pose(workload, s: int, K: int, j: int) -> np.ndarray:
     if lib().orc_pose(C.byref(t), C.byref(p), int(s), int(K), int(j), w) != 0:
         raise ValueError("bad pose request")
     return np.array(list(w))
+
+
+def trajectory(workload, s0: int = 0, count=None, z_ref=None):
+    """Lowest point of every cutting edge at global steps s0 .. s0+count-1:
+    returns (xyz [count, n_teeth, 3] float64, j [count, n_teeth] int32)."""
+    t, p = make_tool(workload.tool), make_process(workload.process, z_ref)
+    total = p.n_passes * p.steps_per_pass
+    if count is None:
+        count = total - s0
+    xyz = np.empty((count, t.n_teeth, 3), np.float64)
+    j = np.empty((count, t.n_teeth), np.int32)
+    rc = lib().orc_trajectory(C.byref(t), C.byref(p), int(s0), int(count),
+                              xyz.ctypes.data_as(C.POINTER(C.c_double)), j.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc != 0:
+        raise ValueError("oracle rejected the request")
+    return xyz, j
 
 
 def roughness(H: np.ndarray, n_rows: int = 10, n_cols: int = 10) -> dict:
