@@ -219,6 +219,30 @@ fsm_status fsm_destroy_process(fsm_ctx* ctx, fsm_process* proc);
 fsm_status fsm_predict_surface(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc,
                                void* d_heights, const fsm_predict_opts* opts, void* stream);
 
+/* One record of a trajectory map (32 bytes). */
+typedef struct {
+    double x, y, z;   /* workpiece coordinates of the lowest edge point (mm) */
+    int32_t j;        /* its index along the edge (tool-description order) */
+    int32_t tooth;    /* K, 0-based */
+} fsm_traj_point;
+
+/* Trajectory map (Section 3.1, trajectory computation module; the paper's
+ * trajectory-map figures of Section 4.2): at every time step s of the tool
+ * path (s = pass * steps_per_pass + local step) and for every tooth K, the
+ * edge point of lowest workpiece z and its coordinates, computed in FP64 for
+ * either process precision with the same pose arithmetic as the FP64 map.
+ * Among points of equal z the first in edge order is reported.
+ *   d_out      caller-owned device array of at least n_passes *
+ *              steps_per_pass * n_teeth records, record s * n_teeth + K.
+ *   capacity   records d_out can hold; fewer than needed -> FSM_E_INVALID.
+ * Asynchronous on `stream`; stream-ordered scratch (tables and one int32 per
+ * spindle phase and tooth). */
+fsm_status fsm_predict_trajectory(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc,
+                                  fsm_traj_point* d_out, int64_t capacity, void* stream);
+
+/* Number of trajectory records of a tool/process pair (host only). */
+fsm_status fsm_trajectory_records(const fsm_tool* tool, const fsm_process* proc, int64_t* n);
+
 /* Autotuner (no counterpart in the paper, whose CPU loops have no launch
  * shape): times up to max_candidates (0 = all) sweep configurations -- tile
  * shape and resident CTAs per SM -- on this tool and process, writing into

@@ -332,6 +332,31 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     return FSM_OK;
 }
 
+fsm_status trajectory_one(fsm_ctx*, const fsm_tool_desc& t, const fsm_process_desc& p, fsm_traj_point* d_out,
+                          int64_t capacity, cudaStream_t st) {
+    const long long n_rec = (long long)p.n_passes * p.steps_per_pass * t.n_teeth;
+    if (capacity < n_rec) return fail(FSM_E_INVALID, "trajectory buffer holds fewer records than the tool path");
+    if (((uintptr_t)d_out & 15) != 0) return fail(FSM_E_INVALID, "d_out must be 16-byte aligned");
+    Shape sh = pick_shape(p, nullptr);
+    Surface s;
+    const size_t surf_bytes = align256(sizeof(Surface));
+    const size_t table_bytes = fill_surface(t, p, sh, &s, nullptr);
+    const size_t jmin_bytes = align256((size_t)s.S * (size_t)t.n_teeth * sizeof(int32_t));
+    void* ws = nullptr;
+    cudaError_t e = cudaMallocAsync(&ws, surf_bytes + table_bytes + jmin_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (trajectory tables)");
+    fill_surface(t, p, sh, &s, (char*)ws + surf_bytes);
+    s.heights = nullptr;
+    Surface* d_s = (Surface*)ws;
+    if ((e = launch_plan(d_s, 1, &s, st)) == cudaSuccess)
+        e = launch_trajectory(d_s, s.S, t.n_teeth, n_rec, (int32_t*)((char*)ws + surf_bytes + table_bytes), d_out,
+                              st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "trajectory kernels");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return FSM_OK;
+}
+
 fsm_status roughness_one(fsm_ctx*, const void* d_h, int precision, int nx, int ny, int n_rows, int n_cols,
                          fsm_roughness_out* d_out, cudaStream_t st) {
     RoughJob jb;
@@ -363,6 +388,21 @@ fsm_status fsm_predict_surface(fsm_ctx* ctx, const fsm_tool* tool, const fsm_pro
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     return fsm::predict_one(ctx, tool->d, proc->d, d_heights, opts, (cudaStream_t)stream);
+}
+
+fsm_status fsm_trajectory_records(const fsm_tool* tool, const fsm_process* proc, int64_t* n) {
+    if (!tool || !proc || !n) return fail(FSM_E_INVALID, "tool/proc/n is NULL");
+    *n = (int64_t)proc->d.n_passes * proc->d.steps_per_pass * tool->d.n_teeth;
+    return FSM_OK;
+}
+
+fsm_status fsm_predict_trajectory(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc,
+                                  fsm_traj_point* d_out, int64_t capacity, void* stream) {
+    if (!ctx || !tool || !proc) return fail(FSM_E_INVALID, "ctx/tool/proc is NULL");
+    if (!d_out) return fail(FSM_E_INVALID, "d_out is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return fsm::trajectory_one(ctx, tool->d, proc->d, d_out, capacity, (cudaStream_t)stream);
 }
 
 fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx, int32_t ny,

@@ -21,6 +21,11 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
                                 long long* d_counters, int grid, int threads, size_t smem,
                                 cudaStream_t st);
 
+// Trajectory map of one planned surface: argmin table d_jmin (S * n_teeth
+// int32 of scratch), then n_records = total steps * n_teeth records.
+cudaError_t launch_trajectory(const Surface* d_surf, int S, int n_teeth, long long n_records, int32_t* d_jmin,
+                              fsm_traj_point* d_out, cudaStream_t st);
+
 // Roughness of a set of maps of one precision. Map j is cut into
 // ceil(n/kChunk) chunks; d_chunk_base[j] is its first chunk (n_jobs+1
 // entries). d_part: 7 * total_chunks doubles of scratch. max_profiles = the

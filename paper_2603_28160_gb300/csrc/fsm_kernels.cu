@@ -1178,6 +1178,81 @@ __global__ void __launch_bounds__(256) profiles_kernel(const RoughJob* __restric
 // ===========================================================================
 // Launchers (called by the C ABI layer)
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// Trajectory map (Section 3.1). The tool reference moves in a horizontal
+// plane, so the height of edge point (K, j) at step s depends on the spindle
+// phase m = s mod S alone: the lowest point of each edge is tabulated once
+// per (m, K) -- one warp each, a lexicographic (z, j) minimum -- and every
+// time step then evaluates one FP64 pose per tooth, through the same pose
+// arithmetic as the FP64 map.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) traj_argmin_kernel(const Surface* __restrict__ sp, int32_t* __restrict__ jmin) {
+    const Surface& sf = *sp;
+    const int N = sf.n_teeth, E = sf.E, NE = N * E;
+    const long long wi = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wi >= (long long)sf.S * N) return;
+    const int lane = threadIdx.x & 31;
+    const int m = (int)(wi / N), K = (int)(wi - (long long)m * N);
+    const double2 cs = sf.ph64[m];
+    const double zr = sf.z_ref;
+    const double* uz = sf.tool64 + 2 * NE + K * E;
+    const double* vz = sf.tool64 + 5 * NE + K * E;
+    const double* wz = sf.tool64 + 8 * NE + K * E;
+    double bz = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    int bj = 0x7fffffff;
+    for (int j = lane; j < E; j += 32) {
+        const double z = __dadd_rn(zr, __fma_rn(cs.x, uz[j], __fma_rn(cs.y, vz[j], wz[j])));
+        if (z < bz) {
+            bz = z;
+            bj = j;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const double oz = __shfl_xor_sync(0xffffffffu, bz, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (oz < bz || (oz == bz && oj < bj)) {
+            bz = oz;
+            bj = oj;
+        }
+    }
+    if (lane == 0) jmin[wi] = bj;
+}
+
+__global__ void __launch_bounds__(256) traj_record_kernel(const Surface* __restrict__ sp,
+                                                          const int32_t* __restrict__ jmin,
+                                                          fsm_traj_point* __restrict__ out, long long n_rec) {
+    const Surface& sf = *sp;
+    const int N = sf.n_teeth, E = sf.E, S = sf.S, NE = N * E, spp = sf.steps_per_pass;
+    const double zr = sf.z_ref;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_rec;
+         r += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(r / N);  // total steps < 2^31
+        const int K = (int)(r - (long long)s * N);
+        const int p = s / spp;
+        const int m = s % S;
+        const int j = __ldg(jmin + m * N + K);
+        const Vec9 v = load_vec9(sf.tool64, NE, K * E + j);
+        const Pose64 P = pose64(v, __ldg(sf.ph64 + m), path_x(sf, s - p * spp), path_y(sf, p), zr);
+        double2* o = reinterpret_cast<double2*>(out + r);
+        o[0] = make_double2(P.x, P.y);
+        o[1] = make_double2(P.z, __hiloint2double(K, j));  // (j, tooth) as two little-endian int32
+    }
+}
+
+cudaError_t launch_trajectory(const Surface* d_surf, int S, int n_teeth, long long n_records, int32_t* d_jmin,
+                              fsm_traj_point* d_out, cudaStream_t st) {
+    const long long warps = (long long)S * n_teeth;
+    traj_argmin_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(d_surf, d_jmin);
+    if (n_records > 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long blocks = std::min<long long>((n_records + 255) / 256, (long long)sms * 8);
+        traj_record_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_surf, d_jmin, d_out, n_records);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_t st) {
     Surface dummy;
     if (one) dummy = *one;

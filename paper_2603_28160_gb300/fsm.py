@@ -90,6 +90,8 @@ SIGNATURES = {
     "fsm_submit": [_P, _P, _P, C.POINTER(C.c_uint64)],
     "fsm_poll": [_P, C.c_uint64, C.c_int32, C.POINTER(Result)],
     "fsm_release_result": [_P, C.c_uint64],
+    "fsm_predict_trajectory": [_P, _P, _P, _P, C.c_int64, _P],
+    "fsm_trajectory_records": [_P, _P, C.POINTER(C.c_int64)],
 }
 
 _lib = None
@@ -251,6 +253,18 @@ class Context:
         self._call("fsm_predict_surface", self.ptr, tool.ptr, proc.ptr, out.data_ptr(),
                    C.byref(o) if o is not None else None, _stream_ptr(stream))
 
+    def trajectory(self, tool: _Handle, proc: _Handle, out=None, stream=None):
+        """fsm_predict_trajectory into a CUDA uint8 tensor of [records, 32]
+        bytes (allocated if out is None); see trajectory_views()."""
+        n = C.c_int64()
+        self._call("fsm_trajectory_records", tool.ptr, proc.ptr, C.byref(n))
+        if out is None:
+            import torch
+            out = torch.empty((n.value, TRAJ_BYTES), dtype=torch.uint8, device="cuda")
+        self._call("fsm_predict_trajectory", self.ptr, tool.ptr, proc.ptr, out.data_ptr(),
+                   out.numel() // TRAJ_BYTES, _stream_ptr(stream))
+        return out
+
     def autotune(self, tool: _Handle, proc: _Handle, out, max_candidates: int = 0, stream=None) -> dict:
         """fsm_autotune: time sweep configurations on this workload; the
         choice is also recorded in the context for later predictions."""
@@ -344,6 +358,21 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+TRAJ_BYTES = 32  # sizeof(fsm_traj_point)
+
+
+def trajectory_views(raw, n_teeth: int):
+    """Views of a trajectory buffer: xyz [steps, n_teeth, 3] float64 and the
+    edge index j and tooth [steps, n_teeth] int32."""
+    import torch
+    rec = raw.view(-1, TRAJ_BYTES)
+    d = rec.view(-1).view(dtype=torch.float64).view(-1, 4)
+    i = rec.view(-1).view(dtype=torch.int32).view(-1, 8)
+    steps = rec.shape[0] // n_teeth
+    return (d[:, :3].reshape(steps, n_teeth, 3), i[:, 6].reshape(steps, n_teeth),
+            i[:, 7].reshape(steps, n_teeth))
 
 
 def heights_tensor(proc: ProcessSpec, device="cuda"):
