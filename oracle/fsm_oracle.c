@@ -115,7 +115,29 @@ static int valid(const orc_tool* t, const orc_process* p) {
     if (p->rot_sense != 1 && p->rot_sense != -1) return 0;
     if (p->n_passes < 1 || p->steps_per_pass < 1) return 0;
     if (p->nx < 1 || p->ny < 1) return 0;
+    if (p->surface != ORC_FLOOR && p->surface != ORC_WALL) return 0;
+    if (p->surface == ORC_WALL && p->n_passes != 1) return 0;
     return 1;
+}
+
+/* Workpiece point -> map frame: the floor keeps (x, y, z); a wall on the +Y
+ * side is sampled over (x, z) with height -y (outward normal -Y). */
+static void to_map_frame(const orc_process* p, const double w[3], double out[3]) {
+    if (p->surface == ORC_WALL) {
+        double x = w[0], y = w[1], z = w[2];
+        out[0] = x;
+        out[1] = z;
+        out[2] = -y;
+    } else {
+        out[0] = w[0];
+        out[1] = w[1];
+        out[2] = w[2];
+    }
+}
+
+/* Height of the un-machined surface in the map frame. */
+static double map_stock(const orc_process* p) {
+    return p->surface == ORC_WALL ? -p->wall_y : p->stock_z;
 }
 
 int orc_points_per_tooth(const orc_tool* t, int refine) {
@@ -327,23 +349,25 @@ static void* fsm_worker(void* arg) {
     for (int K = 0; K < N; ++K)
         for (int j = 0; j < E; ++j) tool_point(t, p, 1, K, j, q + 3 * (K * E + j));
     mat4 A = m_orientation(p);
+    const double stock = map_stock(p);
     for (int pass = job->tid; pass < p->n_passes; pass += job->n_threads) {
         for (int64_t n = 0; n < p->steps_per_pass; ++n) {          /* time step */
             mat4 T = step_matrix(t, p, &A, job->z_ref, 1, pass, n, 0);
             for (int K = 0; K < N; ++K) {                           /* tooth */
                 for (int j = 0; j < E; ++j) {                       /* edge point */
-                    double w[3];
-                    m_apply(&T, q + 3 * (K * E + j), w);
+                    double wp[3], w[3];
+                    m_apply(&T, q + 3 * (K * E + j), wp);
+                    to_map_frame(p, wp, w);
                     job->st.trajectory_points++;
                     double cx = floor((w[0] - p->x0) / p->pitch);
                     double cy = floor((w[1] - p->y0) / p->pitch);
                     int inside = cx >= 0.0 && cx < (double)p->nx && cy >= 0.0 && cy < (double)p->ny;
-                    if (w[2] < p->stock_z && job->flags) flag_point(p, w[0], w[1], job->flags);
+                    if (w[2] < stock && job->flags) flag_point(p, w[0], w[1], job->flags);
                     if (!inside) continue;
                     size_t cell = (size_t)cy * p->nx + (size_t)cx;
                     job->st.landed++;
                     job->hit[cell] = 1;
-                    if (w[2] < p->stock_z) job->st.cutting++;
+                    if (w[2] < stock) job->st.cutting++;
                     if (w[2] < job->H[cell]) job->H[cell] = w[2]; /* keep the lowest z */
                 }
             }
@@ -371,7 +395,7 @@ int orc_fsm(const orc_tool* t, const orc_process* p, double* H, uint8_t* flags,
         jobs[i].H = (i == 0) ? H : (double*)malloc(sizeof(double) * cells);
         jobs[i].flags = flags ? (i == 0 ? flags : (uint8_t*)calloc(cells, 1)) : NULL;
         jobs[i].hit = (uint8_t*)calloc(cells, 1);
-        for (size_t c = 0; c < cells; ++c) jobs[i].H[c] = p->stock_z;
+        for (size_t c = 0; c < cells; ++c) jobs[i].H[c] = map_stock(p);
         if (i == 0 && flags) memset(flags, 0, cells);
     }
     for (int i = 1; i < n_threads; ++i) pthread_create(&th[i], NULL, fsm_worker, &jobs[i]);
@@ -432,8 +456,9 @@ int orc_trajectory(const orc_tool* t, const orc_process* p, int64_t s0, int64_t 
             double best[3] = {0.0, 0.0, INFINITY};
             int32_t bj = -1;
             for (int j = 0; j < E; ++j) {                       /* edge point */
-                double w[3];
-                m_apply(&T, q + 3 * (K * E + j), w);
+                double wp[3], w[3];
+                m_apply(&T, q + 3 * (K * E + j), wp);
+                to_map_frame(p, wp, w);
                 if (w[2] < best[2]) {  /* strict: the first point in edge order wins a tie */
                     best[0] = w[0]; best[1] = w[1]; best[2] = w[2];
                     bj = j;
@@ -474,9 +499,10 @@ int orc_gather(const orc_tool* t, const orc_process* p, int refine,
             mat4 T = step_matrix(t, p, &A, z_ref, refine, pass, n / refine, n % refine);
             for (int K = 0; K < N; ++K)
                 for (int j = 0; j < E; ++j) {
-                    double w[3];
-                    m_apply(&T, q + 3 * (K * E + j), w);
-                    if (!(w[2] < p->stock_z)) continue;
+                    double wp[3], w[3];
+                    m_apply(&T, q + 3 * (K * E + j), wp);
+                    to_map_frame(p, wp, w);
+                    if (!(w[2] < map_stock(p))) continue;
                     if (w[0] < wx_lo || w[0] > wx_hi || w[1] < wy_lo || w[1] > wy_hi) continue;
                     if (np == cap) {
                         cap *= 2;
@@ -493,7 +519,7 @@ int orc_gather(const orc_tool* t, const orc_process* p, int refine,
         double yc = p->y0 + ((double)(k0 + k) + 0.5) * p->pitch;
         for (int i = 0; i < ni; ++i) {
             double xc = p->x0 + ((double)(i0 + i) + 0.5) * p->pitch;
-            double best = p->stock_z;
+            double best = map_stock(p);
             for (size_t a = 0; a < np; ++a) {
                 const double* w = pts + 3 * a;
                 if (xc - half <= w[0] && w[0] < xc + half && yc - half <= w[1] && w[1] < yc + half &&

@@ -18,6 +18,8 @@
  *     (half-open cells) and the per-cell minimum of Section 2.3,
  *   - the trajectory map of Section 3.1 (lowest point of each cutting edge
  *     at each time step, with its global coordinates),
+ *   - (extension) the side-wall surface: the same points binned on the
+ *     plane of a wall instead of the floor,
  *   - the areal (Sa, Sq, Sp, Sv, Sz, Ssk, Sku) and line (Ra, Rz) roughness
  *     indicators named in Section 4.1.2 (ISO 25178-2 / ISO 4287 definitions;
  *     the paper gives no formulas).
@@ -78,7 +80,16 @@ typedef struct {
     double x0, y0, pitch;  /* grid origin (cell corner) and sampling interval */
     int32_t nx, ny;        /* cells along X (columns) and Y (rows) */
     double z_ref_override; /* NaN: derive from the geometry (see orc_z_ref) */
+    /* which surface the map samples: ORC_FLOOR, the horizontal surface
+     * (grid over x, y; height z), or ORC_WALL, the side wall that the flank
+     * leaves on the +Y side of a single pass (grid over x and z, height
+     * along the wall's outward normal -Y, i.e. -y; un-machined at y = wall_y).
+     * The tool reference height is the same in both (orc_z_ref). */
+    int32_t surface;
+    double wall_y;
 } orc_process;
+
+enum { ORC_FLOOR = 0, ORC_WALL = 1 };
 
 typedef struct {
     int64_t trajectory_points; /* all (step, tooth, edge point) triples */
@@ -133,7 +144,9 @@ int orc_gather(const orc_tool* t, const orc_process* p, int refine,
 
 /* Trajectory map: for the global time steps s0 .. s0+count-1 (s = pass *
  * steps_per_pass + local step) and every tooth K, the edge point of lowest
- * workpiece z (the first in edge order among equal z) and its coordinates:
+ * map height (workpiece z on the floor, -y on a wall; the first in edge
+ * order among equal heights) and its map-frame coordinates (floor: x, y, z;
+ * wall: x, z, -y):
  * xyz[((s-s0)*n_teeth + K)*3 + d], jmin[(s-s0)*n_teeth + K]. Returns 0 or -1. */
 int orc_trajectory(const orc_tool* t, const orc_process* p, int64_t s0, int64_t count,
                    double* xyz, int32_t* jmin);

@@ -39,6 +39,7 @@ class OrcProcess(C.Structure):
         ("steps_per_pass", C.c_int64), ("stock_z", C.c_double),
         ("x0", C.c_double), ("y0", C.c_double), ("pitch", C.c_double),
         ("nx", C.c_int32), ("ny", C.c_int32), ("z_ref_override", C.c_double),
+        ("surface", C.c_int32), ("wall_y", C.c_double),
     ]
 
 
@@ -113,6 +114,8 @@ def make_process(proc, z_ref=None) -> OrcProcess:
                  "pitch", "nx", "ny"):
         setattr(p, name, getattr(proc, name))
     p.z_ref_override = math.nan if z_ref is None else z_ref
+    p.surface = {"floor": 0, "wall": 1}[proc.surface]
+    p.wall_y = proc.wall_y
     return p
 
 

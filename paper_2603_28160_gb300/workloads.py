@@ -87,6 +87,8 @@ class ProcessSpec:
     tilt_deg: float = 0.0
     stock_z: float = 0.0
     precision: str = "fp64"       # "fp64" or "fp32"
+    surface: str = "floor"        # "floor" (grid x, y; height z) or "wall" (+Y side wall:
+    wall_y: float = 0.0           # grid x, z; height -y; un-machined at y = wall_y)
 
     def replace(self, **kw) -> "ProcessSpec":
         return dataclasses.replace(self, **kw)
