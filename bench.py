@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-paper", action="store_true")
+    ap.add_argument("--skip-trajectory", action="store_true")
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -407,6 +408,44 @@ def paper_case2_leg(ctx, F, flush, steps=3):
             "paper_note": "context only: the paper's optimised CPU FSM on its own machine and discretisation"}
 
 
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def trajectory_leg(ctx, F, flush, steps=5):
+    """Trajectory map of the metric's workload (every time step of the 12
+    passes, every tooth): planning, the per-phase argmin table and the
+    records, timed as one call. Bound by the 32-byte record writes."""
+    import torch
+    w = workload("fp32")
+    t, p = ctx.tool(w.tool), ctx.process(w.process)
+    raw = ctx.trajectory(t, p)
+    for _ in range(3):
+        ctx.trajectory(t, p, out=raw)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.trajectory(t, p, out=raw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    mean = sum(ms) / len(ms)
+    n = raw.shape[0]
+    peak, src = measured_hbm_gbs()
+    gbs = n * F.TRAJ_BYTES / (mean / 1e3) / 1e9
+    del raw
+    return {"records": n, "bytes": n * F.TRAJ_BYTES, "ms": mean, "records_per_s": n / (mean / 1e3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": src + " copy bandwidth",
+                         "note": "algorithmic bytes = 32 B written per (step, tooth) record"}}
+
+
 def served_leg(ctx, F, seconds, rate, seed=5):
     """Poisson request stream through fsm_submit/fsm_poll (continuous batching,
     120 GB admission budget, 70 % FP32 / 30 % FP64, 0.25-25 Mcells)."""
@@ -542,6 +581,9 @@ def gb300_arm(args):
     large = None
     if not args.skip_large and rank == 0:
         large = large_grid_leg(ctx, F, flush)
+    traj = None
+    if not args.skip_trajectory and rank == 0:
+        traj = trajectory_leg(ctx, F, flush)
     paper = None
     if not args.skip_paper and rank == 0:
         paper = paper_case2_leg(ctx, F, flush)
@@ -604,6 +646,7 @@ def gb300_arm(args):
         "fp64_single_surface": fp64,
         "large_grid": large,
         "paper_case2": paper,
+        "trajectory": traj,
         "batched": batched,
         "served": served,
         "src_hash": src_hash(),

@@ -48,6 +48,7 @@ typedef enum {
 } fsm_status;
 
 enum { FSM_TOOL_FLAT = 0, FSM_TOOL_BALL = 1, FSM_TOOL_INSERT = 2 };
+enum { FSM_SURFACE_FLOOR = 0, FSM_SURFACE_WALL = 1 };
 enum { FSM_FP64 = 0, FSM_FP32 = 1 };
 
 typedef struct fsm_ctx fsm_ctx;
@@ -109,9 +110,17 @@ typedef struct {
  *   precision FSM_FP64 (double heights, all arithmetic FP64) or FSM_FP32
  *   (float heights; edge poses in FP32 tile-local coordinates, FP64 for the
  *   spindle phase, the path position and near-boundary re-binning).
+ *   surface FSM_SURFACE_FLOOR: the map covers x (columns) and y (rows) from
+ *   (x0, y0), height z, un-machined at stock_z. FSM_SURFACE_WALL (an
+ *   extension; the paper maps floors only): the side wall the flank leaves
+ *   on the +Y side of a single pass, sampled over x (columns) and z (rows)
+ *   from (x0, y0 = lowest z), height -y (the wall's outward normal is -Y),
+ *   un-machined at y = wall_y, so cells keep -wall_y until cut. The tool
+ *   reference height is the same as for the floor (stock_z - ap lowest).
  * Validation: fz, ap, pitch > 0; 360/rot_step_deg integral; rot_sense = +-1;
- * n_passes >= 1; steps_per_pass >= 1; n_passes*steps_per_pass < 2^31;
- * 1 <= nx, ny <= 65535*256; finite values. rpm only labels time. */
+ * n_passes >= 1 (== 1 for a wall); steps_per_pass >= 1;
+ * n_passes*steps_per_pass < 2^31; 1 <= nx, ny <= 65535*256; finite values.
+ * rpm only labels time. */
 typedef struct {
     double fz;
     double rpm;
@@ -133,7 +142,8 @@ typedef struct {
     int32_t nx;
     int32_t ny;
     int32_t precision;
-    int32_t reserved;
+    int32_t surface;
+    double wall_y;
 } fsm_process_desc;
 
 /* Optional launch overrides, counters and timing for the prediction calls.

@@ -73,7 +73,7 @@ static fsm_status check_tool(const fsm_tool_desc* t) {
 static fsm_status check_process(const fsm_process_desc* p) {
     if (!p) return fail(FSM_E_INVALID, "process descriptor is NULL");
     const double vals[] = {p->fz, p->rpm, p->rot_step_deg, p->phase0_deg, p->ap, p->lead_deg, p->tilt_deg,
-                           p->ae, p->pass_x0, p->pass_y0, p->stock_z, p->x0, p->y0, p->pitch};
+                           p->ae, p->pass_x0, p->pass_y0, p->stock_z, p->x0, p->y0, p->pitch, p->wall_y};
     for (double v : vals)
         if (!finite(v)) return fail(FSM_E_INVALID, "non-finite process value");
     if (!(p->fz > 0.0)) return fail(FSM_E_INVALID, "fz must be > 0");
@@ -90,6 +90,10 @@ static fsm_status check_process(const fsm_process_desc* p) {
     if ((double)p->nx * (double)p->ny > 4.0e9) return fail(FSM_E_INVALID, "grid larger than 4e9 cells");
     if (fabs(p->lead_deg) >= 89.0 || fabs(p->tilt_deg) >= 89.0) return fail(FSM_E_INVALID, "|lead|, |tilt| < 89");
     if (p->precision != FSM_FP64 && p->precision != FSM_FP32) return fail(FSM_E_INVALID, "unknown precision");
+    if (p->surface != FSM_SURFACE_FLOOR && p->surface != FSM_SURFACE_WALL)
+        return fail(FSM_E_INVALID, "unknown surface");
+    if (p->surface == FSM_SURFACE_WALL && p->n_passes != 1)
+        return fail(FSM_E_INVALID, "a wall map takes a single pass");
     return FSM_OK;
 }
 
@@ -144,6 +148,8 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     s->steps_per_pass = (int32_t)p.steps_per_pass;
     s->S = (int32_t)steps_per_rev(p.rot_step_deg);
     s->stock_z = p.stock_z;
+    s->surface = p.surface;
+    s->wall_y = p.wall_y;
     s->x0 = p.x0;
     s->y0 = p.y0;
     s->pitch = p.pitch;
@@ -279,7 +285,7 @@ fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* sm
 
 std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
     char buf[256];
-    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%.6g/%d/%d/%.6g", p.precision, t.kind, t.n_teeth,
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%.6g/%d/%d/%.6g", p.surface, p.precision, t.kind, t.n_teeth,
              t.n_edge + (t.kind == FSM_TOOL_FLAT ? t.n_end : 0), (int)steps_per_rev(p.rot_step_deg), t.diameter,
              p.nx, p.ny, p.pitch);
     return buf;

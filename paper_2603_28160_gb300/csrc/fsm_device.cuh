@@ -51,6 +51,8 @@ struct Surface {
     int32_t steps_per_pass, S;       // steps per pass, steps per revolution
     double stock_z, x0, y0, pitch;
     int32_t nx, ny, precision, E;    // E = points per tooth
+    int32_t surface, pad0;           // FSM_SURFACE_FLOOR / FSM_SURFACE_WALL
+    double wall_y;
     // ---- launch geometry (inputs) ----
     int32_t tile_x, tile_y, ntx, nty;
     // ---- tables (device pointers, inputs) ----
@@ -63,10 +65,15 @@ struct Surface {
     int* tile_queue;    // next-tile counter of a single-surface sweep (zeroed by planning)
     void* heights;    // output map
     // ---- derived (plan kernel) ----
-    double z_ref, fs, dtheta;       // reference height, feed per step, step angle (rad)
+    // Map frame: the floor's is the workpiece frame; a wall's is (x, z, -y).
+    // The tables hold map-frame vectors; the pass of pass index p runs at
+    // map y = path_y0 + p * path_dy with map height offset z_ref, and the
+    // un-machined surface sits at map height `stock`.
+    double path_y0, path_dy, stock;
+    double z_ref, fs, dtheta;       // map-frame reference height, feed per step, step angle (rad)
     double inv_pitch;               // 1 / pitch
     float reach_x, reach_y;         // max |P_x|, |P_y| over points and phases
-    float zrel_f;                   // z_ref - stock_z
+    float zrel_f;                   // z_ref - stock
     float fs_hi, fs_lo;             // fs as an unevaluated float pair (fs_hi + fs_lo)
     float fs_f, inv_fs_f, dth_f, inv_dth_f, inv_pitch_f;
     float guard_extra;              // FP32 rounding of the bin scaling, in cells

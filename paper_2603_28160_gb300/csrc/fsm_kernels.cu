@@ -79,6 +79,13 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         double half = acos(c);
         kap[0] = fmax(0.0, tau - half);
         kap[1] = fmin(0.5 * 3.14159265358979323846, tau + half);
+        if (sf.surface == 1) {  // wall map frame (x, z, -y): rows (A0, A2, -A1)
+            for (int k = 0; k < 3; ++k) {
+                const double r1 = A[3 + k];
+                A[3 + k] = A[6 + k];
+                A[6 + k] = -r1;
+            }
+        }
     }
     __syncthreads();
     const int NE = N * E;
@@ -153,8 +160,10 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         t32[1] = make_float4((float)u[1], (float)v[1], (float)w[1], (float)v[2]);
         t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
         t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
-        // lowest z of the point over a turn (exact FP64; min is order-free)
-        zlo = fmin(zlo, w[2] - sqrt(u[2] * u[2] + v[2] * v[2]));
+        // lowest workpiece z of the point over a turn (exact FP64; min is
+        // order-free): the map height on a floor, the map y on a wall
+        const int dz = sf.surface == 1 ? 1 : 2;
+        zlo = fmin(zlo, w[dz] - sqrt(u[dz] * u[dz] + v[dz] * v[dz]));
         rx = fmaxf(rx, (float)(fabs(w[0]) + sqrt(u[0] * u[0] + v[0] * v[0])));
         ry = fmaxf(ry, (float)(fabs(w[1]) + sqrt(u[1] * u[1] + v[1] * v[1])));
     }
@@ -213,15 +222,25 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
             ry = fmax(ry, sf->plan_part[4 * q + 2]);
         }
         const double dth = deg2rad(sf->rot_step_deg);
-        const double zr = sf->stock_z - sf->ap - zlo;
+        double zr = sf->stock_z - sf->ap - zlo;  // workpiece height of the tool reference
         const double fs = (double)N * sf->fz / (double)S;
+        if (sf->surface == 1) {  // wall: the pass runs at map y = its height, map z = -(its y)
+            sf->path_y0 = zr;
+            sf->path_dy = 0.0;
+            sf->stock = -sf->wall_y;
+            zr = -sf->pass_y0;
+        } else {
+            sf->path_y0 = sf->pass_y0;
+            sf->path_dy = sf->ae;
+            sf->stock = sf->stock_z;
+        }
         sf->z_ref = zr;
         sf->fs = fs;
         sf->dtheta = dth;
         sf->inv_pitch = 1.0 / sf->pitch;
         sf->reach_x = (float)rx;
         sf->reach_y = (float)ry;
-        sf->zrel_f = (float)(zr - sf->stock_z);
+        sf->zrel_f = (float)(zr - sf->stock);
         sf->fs_hi = (float)fs;
         sf->fs_lo = (float)(fs - (double)sf->fs_hi);
         sf->fs_f = (float)fs;
@@ -312,7 +331,7 @@ __device__ __forceinline__ double path_x(const Surface& sf, int32_t n) {
     return __dadd_rn(sf.pass_x0, __dmul_rn((double)n, sf.fs));
 }
 __device__ __forceinline__ double path_y(const Surface& sf, int p) {
-    return __dadd_rn(sf.pass_y0, __dmul_rn((double)p, sf.ae));
+    return __dadd_rn(sf.path_y0, __dmul_rn((double)p, sf.path_dy));
 }
 __device__ __forceinline__ Pose64 pose64(const Vec9& v, double2 cs, double xc, double yc, double zr) {
     Pose64 P;
@@ -367,7 +386,7 @@ __device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCt
         ts.dx_lo = (float)(d - (double)ts.dx_hi);
         ts.xlo = (float)(tc.X0 - sf.pass_x0) - kMarginMm;
         ts.xhi = (float)(tc.X0 + (double)tc.txc * sf.pitch - sf.pass_x0) + kMarginMm;
-        ts.zhi = (float)(sf.stock_z - sf.z_ref) + kMarginMm;
+        ts.zhi = (float)(sf.stock - sf.z_ref) + kMarginMm;
     }
 }
 
@@ -500,11 +519,11 @@ __device__ __noinline__ void rebin_flush(const Surface& sf, const TileCtx<uint32
         const Vec9 v = load_vec9(sf.tool64, NE, idx);
         const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, s - p * sf.steps_per_pass), path_y(sf, p), sf.z_ref);
         ++cnt.rebinned;
-        if (P.z < sf.stock_z) {
+        if (P.z < sf.stock) {
             const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tc.tx * sf.tile_x;
             const long long kg = bin64(P.y, sf.y0, sf.inv_pitch) - (long long)tc.ty * sf.tile_y;
             if (ig >= 0 && ig < tc.txc && kg >= 0 && kg < tc.tyc)
-                update32(tc.cells, (int)kg * sf.tile_x + (int)ig, (float)(P.z - sf.stock_z), cnt);
+                update32(tc.cells, (int)kg * sf.tile_x + (int)ig, (float)(P.z - sf.stock), cnt);
         }
     }
     __syncwarp();
@@ -670,7 +689,7 @@ __device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<un
     const int E = sf.E, NE = sf.n_teeth * E;
     const double yc = path_y(sf, p);
     const double inv_pitch = sf.inv_pitch;
-    const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock_z;
+    const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock;
     const int S = sf.S;
     const int s0 = p * sf.steps_per_pass;
     const long long ib = (long long)tc.tx * sf.tile_x, kb = (long long)tc.ty * sf.tile_y;
@@ -759,7 +778,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict
         tc.Y0 = sf.y0 + (double)(tc.ty * sf.tile_y) * sf.pitch;
         const int ncell = sf.tile_x * sf.tile_y;
         Cell init;
-        if constexpr (FP64) init = (Cell)enc64((unsigned long long)__double_as_longlong(sf.stock_z));
+        if constexpr (FP64) init = (Cell)enc64((unsigned long long)__double_as_longlong(sf.stock));
         else init = (Cell)enc32(__float_as_uint(0.0f));  // FP32 cells hold heights relative to the stock
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cells[c] = init;
         fill_tile_shared(sf, tc, ts);
@@ -807,7 +826,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict
             }
         } else {
             float* out = reinterpret_cast<float*>(sf.heights);
-            const float st = (float)sf.stock_z;
+            const float st = (float)sf.stock;
             const bool vec = ((sf.nx & 3) == 0) && ((tc.txc & 3) == 0) && ((sf.tile_x & 3) == 0) &&
                              ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
             if (vec) {

@@ -40,7 +40,8 @@ class ProcessDesc(C.Structure):
                 ("ap", C.c_double), ("lead_deg", C.c_double), ("tilt_deg", C.c_double), ("ae", C.c_double),
                 ("pass_x0", C.c_double), ("pass_y0", C.c_double), ("steps_per_pass", C.c_int64),
                 ("stock_z", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("pitch", C.c_double),
-                ("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32), ("surface", C.c_int32),
+                ("wall_y", C.c_double)]
 
 
 class PredictOpts(C.Structure):
@@ -147,6 +148,8 @@ def process_desc(p: ProcessSpec) -> ProcessDesc:
                  "nx", "ny"):
         setattr(d, name, getattr(p, name))
     d.precision = {"fp64": FSM_FP64, "fp32": FSM_FP32}[p.precision]
+    d.surface = {"floor": 0, "wall": 1}[p.surface]
+    d.wall_y = p.wall_y
     return d
 
 

@@ -192,6 +192,33 @@ def floor_flat_d12(seed: int = 2603, precision: str = "fp32", width: float = 20.
     return Workload("floor_flat_d12", tool, proc)
 
 
+def side_wall_flat_d12(seed: int = 2603, precision: str = "fp32", length: float = 20.0, height: float = 1.0,
+                       pitch: float = 0.002, rot_step_deg: float = 0.05, radial_depth: float = 0.3,
+                       n_edge: Optional[int] = None) -> Workload:
+    """The side of the side-plus-floor finish: the wall the flank of the
+    floor_flat_d12 tool (flat D=12, 3 flutes 35/38/41 deg, runout 8 um, the
+    same seeded fz) leaves on the +Y side of one pass along +X, taking a
+    radial depth of 0.3 mm and ap = `height`. Map: length x height at 2 um
+    over x and z, height -y. Flank points every pitch/2 along the axis (so
+    every row of the map holds a sample), 0.05 deg per step."""
+    rng = np.random.default_rng(seed)
+    fz = float(rng.uniform(0.04, 0.15))
+    D = 12.0
+    if n_edge is None:
+        n_edge = int(math.ceil(height / (pitch / 2))) + 1
+    tool = ToolSpec("flat", D, 3, [35.0, 38.0, 41.0], runout_mm=0.008, runout_phase_deg=0.0, n_edge=n_edge,
+                    n_end=0)
+    nx = int(round(length / pitch))
+    ny = int(round(height / pitch))
+    x0 = -0.5 * nx * pitch + CELL_OFFSET[0] * pitch
+    y0 = -height + CELL_OFFSET[1] * pitch   # map rows run over z from the tool tip up
+    px, py, spp = plan_passes(tool, fz, rot_step_deg, nx * pitch, 0.0, 0.0, height, pitch)
+    proc = ProcessSpec(fz=fz, rpm=6000, rot_step_deg=rot_step_deg, ap=height, pass_x0=px, pass_y0=py,
+                       steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx, ny=ny, precision=precision,
+                       surface="wall", wall_y=0.5 * D - radial_depth)
+    return Workload("side_wall_flat_d12", tool, proc)
+
+
 # Case 2 of the paper (Section 4.2.1): face mill R217.29-2520.3-05.2.070,
 # cutting diameter 10 mm, two round inserts of radius 5 mm, radial rake 0.6,
 # axial rake 0; (vc m/min, fz mm, ap mm, eps_r mm, eps_a mm) per case
