@@ -613,3 +613,66 @@ int orc_roughness(const double* H, int nx, int ny, int n_rows, int n_cols, orc_r
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* ISO 16610-61 areal Gaussian filter (see fsm_oracle.h).              */
+/* ------------------------------------------------------------------ */
+static int gauss_weights(double pitch, double lambda, double** g_out) {
+    int T = (int)floor(lambda / pitch + 1e-9);
+    double a = sqrt(log(2.0) / M_PI) * lambda;  /* alpha * lambda */
+    double* g = (double*)malloc(sizeof(double) * (size_t)(2 * T + 1));
+    for (int t = -T; t <= T; ++t) {
+        double x = (double)t * pitch / a;
+        g[t + T] = exp(-M_PI * x * x) / a;   /* s(t * pitch) */
+    }
+    *g_out = g;
+    return T;
+}
+
+/* one line of n samples with stride `stride`: out[i] = sum_t g[t] in[i+t] /
+ * sum_t g[t], t over the weights whose sample lies inside the line */
+static void gauss_line(const double* in, double* out, int n, size_t stride, const double* g, int T) {
+    for (int i = 0; i < n; ++i) {
+        double num = 0.0, den = 0.0;
+        for (int t = -T; t <= T; ++t) {
+            int j = i + t;
+            if (j < 0 || j >= n) continue;
+            num += g[t + T] * in[(size_t)j * stride];
+            den += g[t + T];
+        }
+        out[(size_t)i * stride] = num / den;
+    }
+}
+
+int orc_gauss_filter(const double* H, int nx, int ny, double pitch, double lambda, double* out) {
+    if (!H || !out || H == out || nx < 1 || ny < 1 || !(pitch > 0.0) || !(lambda > 0.0)) return -1;
+    double* g;
+    int T = gauss_weights(pitch, lambda, &g);
+    size_t cells = (size_t)nx * (size_t)ny;
+    double* tmp = (double*)malloc(sizeof(double) * cells);
+    for (int k = 0; k < ny; ++k)   /* rows: along x */
+        gauss_line(H + (size_t)k * nx, tmp + (size_t)k * nx, nx, 1, g, T);
+    for (int i = 0; i < nx; ++i)   /* columns: along y */
+        gauss_line(tmp + i, out + i, ny, (size_t)nx, g, T);
+    free(tmp);
+    free(g);
+    return 0;
+}
+
+int orc_sl_surface(const double* H, int nx, int ny, double pitch, double lambda_s, double lambda_c,
+                   double* out) {
+    if (!H || !out || H == out || nx < 1 || ny < 1 || !(pitch > 0.0) || lambda_s < 0.0 || lambda_c < 0.0)
+        return -1;
+    size_t cells = (size_t)nx * (size_t)ny;
+    double* S = (double*)malloc(sizeof(double) * cells);
+    if (lambda_s > 0.0) orc_gauss_filter(H, nx, ny, pitch, lambda_s, S);
+    else memcpy(S, H, sizeof(double) * cells);
+    if (lambda_c > 0.0) {
+        orc_gauss_filter(S, nx, ny, pitch, lambda_c, out);  /* the mean surface */
+        for (size_t c = 0; c < cells; ++c) out[c] = S[c] - out[c];
+    } else {
+        memcpy(out, S, sizeof(double) * cells);
+    }
+    free(S);
+    return 0;
+}

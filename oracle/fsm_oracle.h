@@ -20,6 +20,8 @@
  *     at each time step, with its global coordinates),
  *   - (extension) the side-wall surface: the same points binned on the
  *     plane of a wall instead of the floor,
+ *   - (extension) the ISO Gaussian S- and L-filters that the paper applies
+ *     to its measured surfaces (Section 4.1.1), for comparing predictions,
  *   - the areal (Sa, Sq, Sp, Sv, Sz, Ssk, Sku) and line (Ra, Rz) roughness
  *     indicators named in Section 4.1.2 (ISO 25178-2 / ISO 4287 definitions;
  *     the paper gives no formulas).
@@ -154,6 +156,22 @@ int orc_trajectory(const orc_tool* t, const orc_process* p, int64_t s0, int64_t 
 /* Areal and profile roughness of H[ny][nx]. */
 int orc_roughness(const double* H, int nx, int ny, int n_rows, int n_cols,
                   orc_rough* out);
+
+/* Areal Gaussian filtering (ISO 16610-61 weighting function; the paper's
+ * measurements use an S-filter of 10 um and an L-filter of 0.8 mm, Section
+ * 4.1.1). Weighting function s(x) = exp(-pi (x / (alpha lambda))^2) / (alpha
+ * lambda), alpha = sqrt(ln 2 / pi), sampled at the cells t * pitch for
+ * |t| <= T = floor(lambda / pitch) (truncated at +-lambda) and applied with
+ * the zero-order end correction: each output divides by the sum of the
+ * weights that fall inside the map (ISO 16610-28). Rows (x) then columns (y);
+ * for a rectangle this equals the 2D weighting function (it is separable).
+ *   orc_gauss_filter: out = G_lambda * H (lambda > 0).
+ *   orc_sl_surface:   S = G_ls * H (H itself if lambda_s == 0), then
+ *                     out = S - G_lc * S (S itself if lambda_c == 0).
+ * out may not alias H. Returns 0 or -1. */
+int orc_gauss_filter(const double* H, int nx, int ny, double pitch, double lambda, double* out);
+int orc_sl_surface(const double* H, int nx, int ny, double pitch, double lambda_s, double lambda_c,
+                   double* out);
 
 #ifdef __cplusplus
 }

@@ -82,6 +82,9 @@ def lib():
                                  C.c_int, P(C.c_double)]
         L.orc_trajectory.argtypes = [P(OrcTool), P(OrcProcess), C.c_int64, C.c_int64, P(C.c_double),
                                      P(C.c_int32)]
+        L.orc_gauss_filter.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double, P(C.c_double)]
+        L.orc_sl_surface.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     P(C.c_double)]
         L.orc_roughness.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_int, C.c_int, P(OrcRough)]
         _lib = L
     return _lib
@@ -194,6 +197,28 @@ def trajectory(workload, s0: int = 0, count=None, z_ref=None):
     if rc != 0:
         raise ValueError("oracle rejected the request")
     return xyz, j
+
+
+def gauss_filter(H: np.ndarray, pitch: float, lam: float) -> np.ndarray:
+    """ISO 16610-61 Gaussian low-pass of H (cutoff lam), zero-order end correction."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    ny, nx = H.shape
+    out = np.empty_like(H)
+    if lib().orc_gauss_filter(H.ctypes.data_as(C.POINTER(C.c_double)), nx, ny, float(pitch), float(lam),
+                              out.ctypes.data_as(C.POINTER(C.c_double))) != 0:
+        raise ValueError("bad filter request")
+    return out
+
+
+def sl_surface(H: np.ndarray, pitch: float, lambda_s: float, lambda_c: float) -> np.ndarray:
+    """S-filter (lambda_s) then remove the L-filter mean surface (lambda_c)."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    ny, nx = H.shape
+    out = np.empty_like(H)
+    if lib().orc_sl_surface(H.ctypes.data_as(C.POINTER(C.c_double)), nx, ny, float(pitch), float(lambda_s),
+                            float(lambda_c), out.ctypes.data_as(C.POINTER(C.c_double))) != 0:
+        raise ValueError("bad filter request")
+    return out
 
 
 def roughness(H: np.ndarray, n_rows: int = 10, n_cols: int = 10) -> dict:
