@@ -298,6 +298,29 @@ fsm_status fsm_roughness_noalloc(fsm_ctx* ctx, const void* d_heights, int32_t pr
                                  int32_t ny, int32_t n_rows, int32_t n_cols,
                                  fsm_roughness_out* d_out, void* stream);
 
+/* ISO 16610-61 areal Gaussian filtering of a device height map (an
+ * extension for comparing predictions with measured surfaces: the paper's
+ * profilometer applies an S-filter of 10 um and an L-filter of 0.8 mm,
+ * Section 4.1.1).
+ *   Weighting function s(x) = exp(-pi (x / (alpha lambda))^2) / (alpha
+ *   lambda), alpha = sqrt(ln 2 / pi) (50 % transmission at lambda), sampled
+ *   at the cells t * pitch for |t| <= floor(lambda / pitch), with the
+ *   zero-order end correction: each output divides by the sum of the weights
+ *   that fall inside the map. Applied along rows and columns (the areal
+ *   function is separable).
+ *   The S-filter gives the S-F surface S = s_{lambda_s} * H (S = H when
+ *   lambda_s == 0); d_out = S - s_{lambda_c} * S, the SL-surface (d_out = S
+ *   when lambda_c == 0).
+ *   precision  FSM_FP64: doubles in and out, sums in double-float arithmetic
+ *              (about 1e-14 relative); FSM_FP32: floats, FP32 sums.
+ *   d_out      caller-owned device buffer of ny*nx values (row-major like
+ *              d_heights), not d_heights itself.
+ * Validation: nx, ny >= 1; pitch > 0; lambda_s, lambda_c >= 0; all finite;
+ * lambda / pitch <= 4096. Scratch: three map-sized stream-ordered device
+ * buffers. Asynchronous on `stream`. */
+fsm_status fsm_filter(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx, int32_t ny,
+                      double pitch, double lambda_s, double lambda_c, void* d_out, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Batched prediction                                                      */
 /* ---------------------------------------------------------------------- */

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libfsm.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["fsm_kernels.cu", "fsm_api.cpp", "fsm_batch.cpp", "fsm_serve.cpp"]
+SOURCES = ["fsm_kernels.cu", "fsm_filter.cu", "fsm_api.cpp", "fsm_batch.cpp", "fsm_serve.cpp"]
 
 
 def nvcc():

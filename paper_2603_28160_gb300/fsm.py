@@ -93,6 +93,7 @@ SIGNATURES = {
     "fsm_release_result": [_P, C.c_uint64],
     "fsm_predict_trajectory": [_P, _P, _P, _P, C.c_int64, _P],
     "fsm_trajectory_records": [_P, _P, C.POINTER(C.c_int64)],
+    "fsm_filter": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
 }
 
 _lib = None
@@ -266,6 +267,18 @@ class Context:
             out = torch.empty((n.value, TRAJ_BYTES), dtype=torch.uint8, device="cuda")
         self._call("fsm_predict_trajectory", self.ptr, tool.ptr, proc.ptr, out.data_ptr(),
                    out.numel() // TRAJ_BYTES, _stream_ptr(stream))
+        return out
+
+    def filter(self, heights, pitch: float, lambda_s: float, lambda_c: float, out=None, stream=None):
+        """fsm_filter: ISO Gaussian S-filter (lambda_s) and L-filter
+        (lambda_c) of a CUDA height map; returns the SL-surface tensor."""
+        import torch
+        ny, nx = heights.shape
+        prec = FSM_FP64 if heights.dtype == torch.float64 else FSM_FP32
+        if out is None:
+            out = torch.empty_like(heights)
+        self._call("fsm_filter", self.ptr, heights.data_ptr(), prec, nx, ny, float(pitch), float(lambda_s),
+                   float(lambda_c), out.data_ptr(), _stream_ptr(stream))
         return out
 
     def autotune(self, tool: _Handle, proc: _Handle, out, max_candidates: int = 0, stream=None) -> dict:
