@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-paper", action="store_true")
     ap.add_argument("--skip-trajectory", action="store_true")
+    ap.add_argument("--skip-wall", action="store_true")
+    ap.add_argument("--skip-filter", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="only the single-surface FP32 and FP64 steps (profiling runs)")
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -53,6 +57,9 @@ def parse():
     ap.add_argument("--width", type=float, default=5.0,
                     help="patch width in mm (5.0 = the measured configuration; smaller for profiling)")
     args = ap.parse_args()
+    if args.skip_extras:
+        for k in ("cpu_baseline", "batch", "large", "serve", "paper", "trajectory", "wall", "filter"):
+            setattr(args, "skip_" + k, True)
     global WIDTH
     WIDTH = args.width
     return args
@@ -261,6 +268,31 @@ def large_grid_leg(ctx, F, flush, steps=2):
             "value": cutting / (ms / 1e3), "unit": UNIT, "surfaces_per_s": 1e3 / ms}
 
 
+def side_wall_leg(ctx, F, flush, steps=3):
+    """The side of the side-plus-floor finish: the 20 x 1 mm wall at 2 um
+    (5 Mcells) that the flat D=12 flank leaves on one pass, FP32, one
+    surface per step (planning, sweep, roughness)."""
+    import torch
+    from paper_2603_28160_gb300 import workloads as W
+    w = W.side_wall_flat_d12(precision="fp32")
+    t, p = ctx.tool(w.tool), ctx.process(w.process)
+    out = F.heights_tensor(w.process)
+    rough = torch.zeros(F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    ctx.predict_surface(t, p, out, counters=cnt)
+    torch.cuda.synchronize()
+    cutting = int(cnt[1].item())
+    step_ms, sweep_ms = time_steps(ctx, F, t, p, out, rough, steps, flush, "fp32")
+    ms = sum(step_ms) / len(step_ms)
+    del out
+    return {"workload": "side_wall_flat_d12: flank of flat D=12, 3 flutes 35/38/41 deg, runout 8 um, radial depth "
+                        "0.3, one pass, %d flank pts, 0.05 deg/step; wall map 20x1 mm @ 2 um over x and z"
+                        % w.tool.n_edge,
+            "cells": w.process.cells, "trajectory_points": w.trajectory_points, "cutting": cutting, "steps": steps,
+            "ms_per_step": ms, "sweep_ms": sum(sweep_ms) / len(sweep_ms), "value": cutting / (ms / 1e3),
+            "unit": UNIT, "surfaces_per_s": 1e3 / ms}
+
+
 def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
     """The Latin-hypercube batch (FP32) in one persistent launch per precision,
     prepared once and replayed as a CUDA graph. With several ranks each rank
@@ -446,6 +478,42 @@ def trajectory_leg(ctx, F, flush, steps=5):
                          "note": "algorithmic bytes = 32 B written per (step, tooth) record"}}
 
 
+def filter_leg(ctx, F, flush, steps=3):
+    """The paper's measurement filters (S 10 um, L 0.8 mm) on the metric's
+    25 Mcell map at 1 um, FP32 and FP64 maps."""
+    import torch
+    pitch, ls, lc = 0.001, 0.010, 0.8
+    ts, tc = int(ls / pitch + 1e-9), int(lc / pitch + 1e-9)
+    fma_per_cell = 2 * (2 * ts + 1) + 2 * (2 * tc + 1)
+    out = {"lambda_s_mm": ls, "lambda_c_mm": lc, "taps_per_cell": fma_per_cell}
+    for prec in ("fp32", "fp64"):
+        w = workload(prec)
+        H = F.heights_tensor(w.process)
+        ctx.predict_surface(ctx.tool(w.tool), ctx.process(w.process), H)
+        sl = torch.empty_like(H)
+        for _ in range(2):
+            ctx.filter(H, pitch, ls, lc, out=sl)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.filter(H, pitch, ls, lc, out=sl)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        mean = sum(ms) / len(ms)
+        cells = H.numel()
+        tflops = 2.0 * fma_per_cell * cells / (mean / 1e3) / 1e12
+        out[prec] = {"ms": mean, "cells_per_s": cells / (mean / 1e3),
+                     "achieved_tflops": tflops,
+                     "arith": "FP32" if prec == "fp32" else "double-float on the FP32 pipes (~11 FP32 ops per tap)"}
+        del H, sl
+    torch.cuda.empty_cache()
+    return out
+
+
 def served_leg(ctx, F, seconds, rate, seed=5):
     """Poisson request stream through fsm_submit/fsm_poll (continuous batching,
     120 GB admission budget, 70 % FP32 / 30 % FP64, 0.25-25 Mcells)."""
@@ -581,6 +649,12 @@ def gb300_arm(args):
     large = None
     if not args.skip_large and rank == 0:
         large = large_grid_leg(ctx, F, flush)
+    filt = None
+    if not args.skip_filter and rank == 0:
+        filt = filter_leg(ctx, F, flush)
+    wall = None
+    if not args.skip_wall and rank == 0:
+        wall = side_wall_leg(ctx, F, flush)
     traj = None
     if not args.skip_trajectory and rank == 0:
         traj = trajectory_leg(ctx, F, flush)
@@ -647,6 +721,8 @@ def gb300_arm(args):
         "large_grid": large,
         "paper_case2": paper,
         "trajectory": traj,
+        "side_wall": wall,
+        "iso_filter": filt,
         "batched": batched,
         "served": served,
         "src_hash": src_hash(),

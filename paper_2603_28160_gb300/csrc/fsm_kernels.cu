@@ -1239,22 +1239,25 @@ __global__ void __launch_bounds__(256) traj_argmin_kernel(const Surface* __restr
 
 __global__ void __launch_bounds__(256) traj_record_kernel(const Surface* __restrict__ sp,
                                                           const int32_t* __restrict__ jmin,
-                                                          fsm_traj_point* __restrict__ out, long long n_rec) {
+                                                          fsm_traj_point* __restrict__ out, int n_steps) {
     const Surface& sf = *sp;
     const int N = sf.n_teeth, E = sf.E, S = sf.S, NE = N * E, spp = sf.steps_per_pass;
     const double zr = sf.z_ref;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_rec;
-         r += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(r / N);  // total steps < 2^31
-        const int K = (int)(r - (long long)s * N);
+    // one thread per time step writes its n_teeth consecutive records
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_steps; s += gridDim.x * blockDim.x) {
         const int p = s / spp;
         const int m = s % S;
-        const int j = __ldg(jmin + m * N + K);
-        const Vec9 v = load_vec9(sf.tool64, NE, K * E + j);
-        const Pose64 P = pose64(v, __ldg(sf.ph64 + m), path_x(sf, s - p * spp), path_y(sf, p), zr);
-        double2* o = reinterpret_cast<double2*>(out + r);
-        o[0] = make_double2(P.x, P.y);
-        o[1] = make_double2(P.z, __hiloint2double(K, j));  // (j, tooth) as two little-endian int32
+        const double xc = path_x(sf, s - p * spp), yc = path_y(sf, p);
+        const double2 cs = __ldg(sf.ph64 + m);
+        fsm_traj_point* o = out + (size_t)s * N;
+        for (int K = 0; K < N; ++K) {
+            const int j = __ldg(jmin + m * N + K);
+            const Vec9 v = load_vec9(sf.tool64, NE, K * E + j);
+            const Pose64 P = pose64(v, cs, xc, yc, zr);
+            double2* d = reinterpret_cast<double2*>(o + K);
+            d[0] = make_double2(P.x, P.y);
+            d[1] = make_double2(P.z, __hiloint2double(K, j));  // (j, tooth) as two little-endian int32
+        }
     }
 }
 
@@ -1262,12 +1265,13 @@ cudaError_t launch_trajectory(const Surface* d_surf, int S, int n_teeth, long lo
                               fsm_traj_point* d_out, cudaStream_t st) {
     const long long warps = (long long)S * n_teeth;
     traj_argmin_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(d_surf, d_jmin);
-    if (n_records > 0) {
+    const int n_steps = (int)(n_records / n_teeth);  // total steps < 2^31
+    if (n_steps > 0) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long blocks = std::min<long long>((n_records + 255) / 256, (long long)sms * 8);
-        traj_record_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_surf, d_jmin, d_out, n_records);
+        const int blocks = (int)std::min<long long>((n_steps + 255) / 256, (long long)sms * 8);
+        traj_record_kernel<<<blocks, 256, 0, st>>>(d_surf, d_jmin, d_out, n_steps);
     }
     return cudaGetLastError();
 }
