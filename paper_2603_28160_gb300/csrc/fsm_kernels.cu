@@ -3,7 +3,7 @@
 //   plan_kernel      edge, phase and path tables of each surface in FP64
 //                    (Section 2.2 discretisation; Section 3.2 "tool geometry"
 //                    and "kinematics" modules precompute points and trig)
-//   sweep_kernel<T>  persistent tile sweep (Section 2.3 and the "surface
+//   sweep_kernel<..> persistent tile sweep (Section 2.3 and the "surface
 //                    computation module" of Section 3.2): a tile of the height
 //                    map lives in shared memory, every edge point that can
 //                    land in the tile below the stock is evaluated, binned by
@@ -501,29 +501,33 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
 // FP32 path: tile-local FP32 poses; points whose FP32 cell is ambiguous and
 // that could lower a cell are re-binned in FP64, 32 at a time.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void update32(uint32_t* cells, int idx, float zrel, Counters& c) {
+__device__ __forceinline__ bool update32(uint32_t* cells, int idx, float zrel) {
     const uint32_t e = enc32(__float_as_uint(zrel));
     if (e < cells[idx]) {
         atomicMin(cells + idx, e);
-        ++c.atomics;
+        return true;
     }
+    return false;
 }
 
-// Re-bin queued points in FP64 (lanes < count take one entry each).
-__device__ __noinline__ void rebin_flush(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws, int p,
-                                         int count, Counters& cnt) {
+// Re-bin queued points in FP64 (lanes < count take one entry each). Takes
+// the tile by value and returns this lane's (re-binned, atomics) counts, so
+// the caller's counters stay in registers.
+__device__ __noinline__ uint2 rebin_flush(const Surface& sf, uint32_t* cells, int tx, int ty, int txc, int tyc,
+                                          WarpScratch& ws, int p, int count) {
     const int lane = threadIdx.x & 31;
+    uint2 c = make_uint2(0u, 0u);
     if (lane < count) {
         const int NE = sf.n_teeth * sf.E;
         const int s = ws.q_s[lane], m = ws.q_m[lane], idx = ws.q_idx[lane];
         const Vec9 v = load_vec9(sf.tool64, NE, idx);
         const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, s - p * sf.steps_per_pass), path_y(sf, p), sf.z_ref);
-        ++cnt.rebinned;
+        c.x = 1u;
         if (P.z < sf.stock) {
-            const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tc.tx * sf.tile_x;
-            const long long kg = bin64(P.y, sf.y0, sf.inv_pitch) - (long long)tc.ty * sf.tile_y;
-            if (ig >= 0 && ig < tc.txc && kg >= 0 && kg < tc.tyc)
-                update32(tc.cells, (int)kg * sf.tile_x + (int)ig, (float)(P.z - sf.stock), cnt);
+            const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tx * sf.tile_x;
+            const long long kg = bin64(P.y, sf.y0, sf.inv_pitch) - (long long)ty * sf.tile_y;
+            if (ig >= 0 && ig < txc && kg >= 0 && kg < tyc)
+                c.y = update32(cells, (int)kg * sf.tile_x + (int)ig, (float)(P.z - sf.stock)) ? 1u : 0u;
         }
     }
     __syncwarp();
@@ -542,6 +546,14 @@ __device__ __noinline__ void rebin_flush(const Surface& sf, const TileCtx<uint32
         ws.q_idx[lane] = idx;
     }
     __syncwarp();
+    return c;
+}
+
+__device__ __forceinline__ void rebin_flush_count(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws,
+                                                  int p, int count, Counters& cnt) {
+    const uint2 c = rebin_flush(sf, tc.cells, tc.tx, tc.ty, tc.txc, tc.tyc, ws, p, count);
+    cnt.rebinned += c.x;
+    cnt.atomics += c.y;
 }
 
 // Queue this iteration's re-bins (warp-cooperative) and flush full batches.
@@ -559,7 +571,7 @@ __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint
     qn += __popc(bal);
     __syncwarp();
     if (qn >= 32) {
-        rebin_flush(sf, tc, ws, p, qn, cnt);
+        rebin_flush_count(sf, tc, ws, p, qn, cnt);
         qn -= 32;
     }
 }
@@ -630,6 +642,7 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
         const int tmax = max(tot, __shfl_xor_sync(0xffffffffu, tot, 16));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
+        const float hg = 0.5f - gc;
         for (int base = 0; base < tmax; base += 32) {
             const int ta = base + hl, tb = base + 16 + hl;
             const bool va = ta < tot, vb = tb < tot;
@@ -653,8 +666,9 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
             const bool in_a = cut_a && (unsigned)ia < (unsigned)txc && (unsigned)ka < (unsigned)tyc;
             const bool in_b = cut_b && (unsigned)ib < (unsigned)txc && (unsigned)kb < (unsigned)tyc;
             cnt.cutting += (unsigned)in_a + (unsigned)in_b;
-            const bool amb_a = rxa < gc || rxa > 1.f - gc || rya < gc || rya > 1.f - gc;
-            const bool amb_b = rxb < gc || rxb > 1.f - gc || ryb < gc || ryb > 1.f - gc;
+            // within gc of a cell boundary: |r - 1/2| > 1/2 - gc on either axis
+            const bool amb_a = fmaxf(fabsf(rxa - 0.5f), fabsf(rya - 0.5f)) > hg;
+            const bool amb_b = fmaxf(fabsf(rxb - 0.5f), fabsf(ryb - 0.5f)) > hg;
             const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
             const int cia = ka * tile_x + ia, cib = kb * tile_x + ib;
             const uint32_t ea = enc32(__float_as_uint(za)), eb = enc32(__float_as_uint(zb2));
@@ -673,11 +687,13 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
                 wa = ambiguous_may_lower(cells, tile_x, txc, tyc, ia, ka, rxa, rya, gc, za, eps_z);
             if (cut_b && amb_b)
                 wb = ambiguous_may_lower(cells, tile_x, txc, tyc, ib, kb, rxb, ryb, gc, zb2, eps_z);
-            rebin_push(sf, tc, ws, p, wa, sa, ma, idx, qn, cnt);
-            rebin_push(sf, tc, ws, p, wb, sb, mb, idx, qn, cnt);
+            if (__any_sync(0xffffffffu, wa || wb)) {
+                rebin_push(sf, tc, ws, p, wa, sa, ma, idx, qn, cnt);
+                rebin_push(sf, tc, ws, p, wb, sb, mb, idx, qn, cnt);
+            }
         }
     }
-    if (qn > 0) rebin_flush(sf, tc, ws, p, qn, cnt);
+    if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -740,7 +756,7 @@ __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) 
 // (tile_base[s] = first tile of surface s); CTAs take tiles in a static
 // stride, or from *queue when it is not NULL. Inside a tile, warps take
 // (pass, tooth, 32-point group) tasks from a shared counter.
-template <bool FP64>
+template <bool FP64, bool kCount>
 __global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
                                                        const int* __restrict__ tile_base, int total_tiles,
                                                        int* queue, long long* counters) {
@@ -852,7 +868,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict
         }
         __syncthreads();
     }
-    warp_flush(cnt, counters);
+    if constexpr (kCount) warp_flush(cnt, counters);
 }
 
 // ===========================================================================
@@ -1300,12 +1316,22 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,
                                 cudaStream_t st) {
-    if (precision == 0)
-        sweep_kernel<true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles, d_queue,
-                                                        d_counters);
-    else
-        sweep_kernel<false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles, d_queue,
-                                                         d_counters);
+    // counting is a separate instantiation: without it the counters are dead code
+    if (precision == 0) {
+        if (d_counters)
+            sweep_kernel<true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                  d_queue, d_counters);
+        else
+            sweep_kernel<true, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                   d_queue, nullptr);
+    } else {
+        if (d_counters)
+            sweep_kernel<false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                   d_queue, d_counters);
+        else
+            sweep_kernel<false, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                    d_queue, nullptr);
+    }
     return cudaGetLastError();
 }
 
@@ -1321,19 +1347,25 @@ static cudaError_t allow_dynamic_smem(K kernel, size_t max_bytes) {
 }
 
 cudaError_t sweep_allow_smem(size_t max_bytes) {
-    cudaError_t e = allow_dynamic_smem(sweep_kernel<true>, max_bytes);
-    if (e != cudaSuccess) return e;
-    return allow_dynamic_smem(sweep_kernel<false>, max_bytes);
+    cudaError_t e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, false>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<false, true>, max_bytes)) != cudaSuccess) return e;
+    return allow_dynamic_smem(sweep_kernel<false, false>, max_bytes);
 }
 
+// Resident CTAs per SM: the smaller of the counting and plain instantiations.
 int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
-    int nb = 0;
-    cudaError_t e;
-    if (precision == 0)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<true>, threads, smem);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false>, threads, smem);
-    return e == cudaSuccess ? nb : 0;
+    int a = 0, b = 0;
+    cudaError_t e1, e2;
+    if (precision == 0) {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<true, true>, threads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<true, false>, threads, smem);
+    } else {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<false, true>, threads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<false, false>, threads, smem);
+    }
+    return (e1 == cudaSuccess && e2 == cudaSuccess) ? min(a, b) : 0;
 }
 
 __global__ void rough_setup_one_kernel(RoughJob jb, int chunks, RoughJob* d_job, int* d_base) {
