@@ -394,12 +394,18 @@ def paper_case2_leg(ctx, F, flush, steps=3):
         procs = [ctx.process(w.process) for w in ws]
         outs = [F.heights_tensor(w.process) for w in ws]
         rough = torch.zeros(len(ws) * F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+        # the library's autotuner picks the sweep shape on the first condition
+        # (recorded in the context for the single-surface calls; passed to the
+        # batch explicitly)
+        tuned = ctx.autotune(tools[0], procs[0], outs[0])
         cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
-        ctx.predict_batch(tools, procs, outs, rough_buf=rough, counters=cnt)
+        ctx.predict_batch(tools, procs, outs, rough_buf=rough, counters=cnt, tile=tuned["tile"],
+                          threads=tuned["threads"])
         torch.cuda.synchronize()
         cutting = int(cnt[1].item())
         code = F.FSM_FP64 if prec == "fp64" else F.FSM_FP32
-        b = ctx.batch(tools, procs, outs, rough_buf=rough) if prec == "fp32" else None
+        b = ctx.batch(tools, procs, outs, rough_buf=rough, tile=tuned["tile"],
+                      threads=tuned["threads"]) if prec == "fp32" else None
 
         def one_step():
             if b is not None:
@@ -424,6 +430,7 @@ def paper_case2_leg(ctx, F, flush, steps=3):
         if b is not None:
             b.close()
         out[prec] = {"ms_per_9_surfaces": mean, "ms_per_surface": mean / len(ws),
+                     "sweep_shape": {"tile": list(tuned["tile"]), "threads": tuned["threads"]},
                      "surfaces_per_s": len(ws) / (mean / 1e3), "cutting": cutting,
                      "value": cutting / (mean / 1e3), "unit": UNIT,
                      "launch": "prepared batch of 9" if prec == "fp32" else "one surface at a time"}

@@ -149,7 +149,7 @@ typedef struct {
 /* Optional launch overrides, counters and timing for the prediction calls.
  *   tile_x, tile_y    shared-memory tile in cells (0 = library default;
  *                     tile_x a multiple of 4)
- *   block_threads     threads per CTA (0 = default)
+ *   block_threads     threads per CTA, a multiple of 32 in 64..512 (0 = default)
  *   ctas_per_sm       cap on resident CTAs per SM (0 = as many as fit)
  *   d_counters        NULL, or device int64_t[4] the sweep ADDS to:
  *                     [0] edge-point poses evaluated,

@@ -99,13 +99,34 @@ static fsm_status check_process(const fsm_process_desc* p) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o) {
+Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm_process_desc* const* group,
+                 int n_group, int sm_count) {
+    // Default ladder, measured on GB300: 16 warps sharing one large, wide
+    // tile amortise the per-tile enumeration best (5x5 mm, 1 um ball raster:
+    // FP32 512x48 1.62 ms vs 256x48 with 8 warps 2.19 ms; FP64 256x64 13.1 ms
+    // vs 128x64 15.4 ms), while wide, short tiles keep per-arc x ranges
+    // tight. A step down is taken while the surfaces have fewer tiles than
+    // there are resident CTAs (small maps: the 2 Mcell face-milled patch runs
+    // 0.33 ms at 128x32 against 0.99 ms at 512x48).
+    struct Level { int tx, ty, threads, ctas; };
+    static const Level l32[] = {{512, 48, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
+    static const Level l64[] = {{256, 64, 512, 1}, {128, 64, 256, 2}, {128, 32, 256, 2}};
+    const Level* lv = p.precision == FSM_FP64 ? l64 : l32;
+    int pick = 0;
+    if (group && n_group > 0 && sm_count > 0) {
+        for (pick = 0; pick < 2; ++pick) {
+            long long tiles = 0;
+            for (int i = 0; i < n_group; ++i)
+                if (group[i]->precision == p.precision)
+                    tiles += (long long)((group[i]->nx + lv[pick].tx - 1) / lv[pick].tx) *
+                             ((group[i]->ny + lv[pick].ty - 1) / lv[pick].ty);
+            if (tiles >= (long long)sm_count * lv[pick].ctas) break;
+        }
+    }
     Shape s;
-    // measured on the 5x5 mm, 1 um ball raster: wide, short tiles keep the
-    // per-arc x ranges tight (FP32 256x48: 2.86 ms, 128x128: 3.39 ms)
-    s.tile_x = p.precision == FSM_FP64 ? 128 : 256;
-    s.tile_y = p.precision == FSM_FP64 ? 64 : 48;
-    s.threads = 256;
+    s.tile_x = lv[pick].tx;
+    s.tile_y = lv[pick].ty;
+    s.threads = lv[pick].threads;
     if (o) {
         if (o->tile_x > 0) s.tile_x = o->tile_x;
         if (o->tile_y > 0) s.tile_y = o->tile_y;
@@ -269,8 +290,8 @@ namespace fsm {
 
 // Launch configuration of the sweep for one precision; checks shared memory.
 fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* smem, int* blocks_per_sm) {
-    if (sh.threads < 64 || sh.threads > 256 || (sh.threads & 31))
-        return fail(FSM_E_INVALID, "block_threads must be a multiple of 32 in 64..256");
+    if (sh.threads < 64 || sh.threads > 512 || (sh.threads & 31))
+        return fail(FSM_E_INVALID, "block_threads must be a multiple of 32 in 64..512");
     if (sh.tile_x < 4 || sh.tile_y < 1 || (sh.tile_x & 3)) return fail(FSM_E_INVALID, "tile_x must be a multiple of 4");
     *smem = sweep_smem_bytes(precision, sh.tile_x, sh.tile_y, sh.threads);
     if (*smem + 1024 > ctx->smem_optin) return fail(FSM_E_INVALID, "tile does not fit in shared memory");
@@ -293,7 +314,8 @@ std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
 
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st) {
-    Shape sh = pick_shape(p, opts);
+    const fsm_process_desc* self = &p;
+    Shape sh = pick_shape(p, opts, &self, 1, ctx->sm_count);
     fsm_predict_opts tuned_opts;
     if (!opts || opts->tile_x <= 0) {  // an autotuned shape for this workload, if any
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -301,6 +323,7 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
         if (it != ctx->tuned.end()) {
             sh.tile_x = it->second[0];
             sh.tile_y = it->second[1];
+            sh.threads = it->second[3];
             if (opts) tuned_opts = *opts;
             else memset(&tuned_opts, 0, sizeof tuned_opts);
             tuned_opts.ctas_per_sm = it->second[2];
@@ -431,11 +454,15 @@ extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
-    // candidates: wide, short tiles first (they keep per-arc x ranges tight)
-    static const int c32[][2] = {{256, 48}, {512, 32}, {256, 64}, {384, 32}, {128, 64}, {512, 24}, {192, 64}, {128, 128}};
-    static const int c64[][2] = {{128, 64}, {256, 32}, {128, 32}, {64, 64}, {256, 24}, {192, 32}};
+    // candidates (tile_x, tile_y, threads): wide, short tiles shared by many
+    // warps first (they amortise the enumeration and keep x ranges tight)
+    static const int c32[][3] = {{512, 48, 512}, {448, 48, 512}, {512, 40, 512}, {512, 24, 256}, {256, 96, 512},
+                                 {384, 64, 512}, {768, 32, 512}, {512, 56, 512}, {256, 48, 256}, {256, 64, 256},
+                                 {128, 48, 256}, {128, 32, 256}, {64, 32, 256}};
+    static const int c64[][3] = {{256, 64, 512}, {256, 48, 512}, {192, 64, 384}, {192, 80, 512}, {128, 64, 256},
+                                 {256, 32, 256}, {128, 96, 512}, {128, 32, 256}, {64, 64, 256}, {64, 32, 256}};
     const bool f64 = proc->d.precision == FSM_FP64;
-    const int nshape = f64 ? 6 : 8;
+    const int nshape = f64 ? 10 : 13;
     cudaEvent_t ev[2];
     if ((e = cudaEventCreate(&ev[0])) != cudaSuccess || (e = cudaEventCreate(&ev[1])) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate");
@@ -451,7 +478,7 @@ extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm
             memset(&o, 0, sizeof o);
             o.tile_x = f64 ? c64[si][0] : c32[si][0];
             o.tile_y = f64 ? c64[si][1] : c32[si][1];
-            o.block_threads = 256;
+            o.block_threads = f64 ? c64[si][2] : c32[si][2];
             o.ctas_per_sm = cps;
             size_t smem;
             int bps;
@@ -486,6 +513,6 @@ extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm
     *best = bo;
     if (best_ms) *best_ms = best_t;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    ctx->tuned[tune_key(tool->d, proc->d)] = {bo.tile_x, bo.tile_y, bo.ctas_per_sm};
+    ctx->tuned[tune_key(tool->d, proc->d)] = {bo.tile_x, bo.tile_y, bo.ctas_per_sm, bo.block_threads};
     return FSM_OK;
 }

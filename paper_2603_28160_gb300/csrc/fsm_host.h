@@ -28,8 +28,8 @@ struct fsm_ctx {
     size_t smem_optin = 0;
     std::mutex mu;
     fsm::Server* server = nullptr;
-    // autotuned sweep shapes: workload signature -> (tile_x, tile_y, ctas_per_sm)
-    std::map<std::string, std::array<int, 3>> tuned;
+    // autotuned sweep shapes: workload signature -> (tile_x, tile_y, ctas_per_sm, threads)
+    std::map<std::string, std::array<int, 4>> tuned;
 };
 
 namespace fsm {
@@ -75,7 +75,10 @@ struct Shape {
 size_t align256(size_t v);
 // Key of the autotuner's table for a tool/process pair.
 std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p);
-Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o);
+// Sweep shape: the caller's override, else the default ladder step for this
+// precision given the tiles of the surfaces in `group` (may be NULL).
+Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm_process_desc* const* group = nullptr,
+                 int n_group = 0, int sm_count = 0);
 // Fill a device plan from the descriptors. Table pointers are laid out from
 // `base`; returns the table bytes (call with base = NULL to size).
 size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh, Surface* s,

@@ -757,7 +757,7 @@ __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) 
 // stride, or from *queue when it is not NULL. Inside a tile, warps take
 // (pass, tooth, 32-point group) tasks from a shared counter.
 template <bool FP64, bool kCount>
-__global__ void __launch_bounds__(256, 2) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
                                                        const int* __restrict__ tile_base, int total_tiles,
                                                        int* queue, long long* counters) {
     using Cell = typename std::conditional<FP64, unsigned long long, uint32_t>::type;
