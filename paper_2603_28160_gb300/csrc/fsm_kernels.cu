@@ -98,11 +98,15 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         if (sf.kind == 2) {  // round insert: lower semicircle, rake, per-insert runout, tooth angle
             const double Ri = sf.insert_radius;
             const double gf = deg2rad(sf.rake_f_deg), gp = deg2rad(sf.rake_p_deg);
-            const double dl_ap = sf.ap >= Ri ? Ri : sqrt(Ri * Ri - (Ri - sf.ap) * (Ri - sf.ap));
+            // unfused products: R^2 - l^2 must be exactly 0 at l = +-R (an fma
+            // would leave its rounding error there, possibly negative)
+            const double rr = __dmul_rn(Ri, Ri);
+            const double imm = Ri - sf.ap;
+            const double dl_ap = sf.ap >= Ri ? Ri : sqrt(fmax(__dsub_rn(rr, __dmul_rn(imm, imm)), 0.0));
             const double dl_fz = sf.fz / (2.0 * cos(gf));
             const double dL = fmin(fmax(dl_ap, dl_fz), Ri);
             const double l = -dL + 2.0 * dL * ((double)j / (double)(E - 1));
-            const double zc = Ri - sqrt(Ri * Ri - l * l);
+            const double zc = Ri - sqrt(fmax(__dsub_rn(rr, __dmul_rn(l, l)), 0.0));
             // insert frame -> tool frame (x along the radius at the tooth's reference)
             const double xt = cos(gf) * l + sin(gf) * sin(gp) * zc + R + (double)K * sf.eps_r_mm;
             const double yt = -sin(gf) * l + cos(gf) * sin(gp) * zc;

@@ -44,9 +44,10 @@ def test_struct_sizes_match_the_header():
 #include <stddef.h>
 #include "fsm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(fsm_tool_desc), sizeof(fsm_process_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fsm_tool_desc), sizeof(fsm_process_desc),
          sizeof(fsm_predict_opts), sizeof(fsm_roughness_out), sizeof(fsm_result),
-         offsetof(fsm_process_desc, steps_per_pass), offsetof(fsm_roughness_out, Ra_row));
+         offsetof(fsm_process_desc, steps_per_pass), offsetof(fsm_roughness_out, Ra_row),
+         sizeof(fsm_traj_point), offsetof(fsm_process_desc, wall_y));
   return 0;
 }
 '''
@@ -58,7 +59,7 @@ int main(void) {
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(fsm.ToolDesc), ctypes.sizeof(fsm.ProcessDesc), ctypes.sizeof(fsm.PredictOpts),
             ctypes.sizeof(fsm.RoughnessOut), ctypes.sizeof(fsm.Result), fsm.ProcessDesc.steps_per_pass.offset,
-            fsm.RoughnessOut.Ra_row.offset]
+            fsm.RoughnessOut.Ra_row.offset, fsm.TRAJ_BYTES, fsm.ProcessDesc.wall_y.offset]
     assert got == want
 
 
