@@ -659,9 +659,9 @@ def gb300_arm(args):
     filt = None
     if not args.skip_filter and rank == 0:
         filt = filter_leg(ctx, F, flush)
-    wall = None
+    side = None
     if not args.skip_wall and rank == 0:
-        wall = side_wall_leg(ctx, F, flush)
+        side = side_wall_leg(ctx, F, flush)
     traj = None
     if not args.skip_trajectory and rank == 0:
         traj = trajectory_leg(ctx, F, flush)
@@ -728,7 +728,7 @@ def gb300_arm(args):
         "large_grid": large,
         "paper_case2": paper,
         "trajectory": traj,
-        "side_wall": wall,
+        "side_wall": side,
         "iso_filter": filt,
         "batched": batched,
         "served": served,
