@@ -103,12 +103,14 @@ static int64_t steps_per_rev(const orc_process* p) {
 
 static int valid(const orc_tool* t, const orc_process* p) {
     if (!t || !p) return 0;
-    if (t->kind != ORC_FLAT && t->kind != ORC_BALL && t->kind != ORC_INSERT) return 0;
+    if (t->kind != ORC_FLAT && t->kind != ORC_BALL && t->kind != ORC_INSERT && t->kind != ORC_TORUS) return 0;
     if (t->kind == ORC_INSERT && !(t->insert_radius > 0.0)) return 0;
+    if (t->kind == ORC_TORUS && !(t->corner_radius > 0.0 && t->corner_radius <= 0.5 * t->diameter)) return 0;
     if (t->n_teeth < 1 || t->n_teeth > ORC_MAX_TEETH) return 0;
     if (t->n_edge < 2) return 0;
-    if (t->kind == ORC_FLAT && (t->n_end == 1 || t->n_end < 0)) return 0;
-    if (t->kind != ORC_FLAT && t->n_end != 0) return 0;
+    int has_end = t->kind == ORC_FLAT || t->kind == ORC_TORUS;
+    if (has_end && (t->n_end == 1 || t->n_end < 0)) return 0;
+    if (!has_end && t->n_end != 0) return 0;
     if (!(t->diameter > 0.0)) return 0;
     if (steps_per_rev(p) < 0) return 0;
     if (!(p->fz > 0.0) || !(p->ap > 0.0) || !(p->pitch > 0.0)) return 0;
@@ -117,6 +119,7 @@ static int valid(const orc_tool* t, const orc_process* p) {
     if (p->nx < 1 || p->ny < 1) return 0;
     if (p->surface != ORC_FLOOR && p->surface != ORC_WALL) return 0;
     if (p->surface == ORC_WALL && p->n_passes != 1) return 0;
+    if (p->pass_mode != ORC_ONE_WAY && p->pass_mode != ORC_ZIGZAG) return 0;
     return 1;
 }
 
@@ -143,7 +146,7 @@ static double map_stock(const orc_process* p) {
 int orc_points_per_tooth(const orc_tool* t, int refine) {
     if (!t || refine < 1 || t->n_edge < 2) return -1;
     int edge = (t->n_edge - 1) * refine + 1;
-    int end = (t->kind == ORC_FLAT && t->n_end >= 2) ? (t->n_end - 1) * refine + 1 : 0;
+    int end = ((t->kind == ORC_FLAT || t->kind == ORC_TORUS) && t->n_end >= 2) ? (t->n_end - 1) * refine + 1 : 0;
     return edge + end;
 }
 
@@ -181,6 +184,31 @@ static void profile_point(const orc_tool* t, const orc_process* p, int refine,
             int f = j - end;
             *r = R;
             *h = p->ap * ((double)f / (double)(edge - 1));
+        }
+        return;
+    }
+    if (t->kind == ORC_TORUS) {
+        /* bottom flat r in [0, R - rc] at h = 0, then points uniform in arc
+         * length along the corner arc (centre (R - rc, rc)) and the flank,
+         * from the bottom up to height ap */
+        double rc = t->corner_radius;
+        int end = t->n_end >= 2 ? (t->n_end - 1) * refine + 1 : 0;
+        if (j < end) {
+            *r = (R - rc) * ((double)j / (double)(end - 1));
+            *h = 0.0;
+            return;
+        }
+        double arc_top = p->ap >= rc ? 0.5 * M_PI : acos(1.0 - p->ap / rc);
+        double len_arc = rc * arc_top;
+        double len = len_arc + (p->ap > rc ? p->ap - rc : 0.0);
+        double s_along = len * ((double)(j - end) / (double)(edge - 1));
+        if (s_along <= len_arc) {
+            double kappa = s_along / rc;
+            *r = R - rc + rc * sin(kappa);
+            *h = rc * (1.0 - cos(kappa));
+        } else {
+            *r = R;
+            *h = rc + (s_along - len_arc);
         }
         return;
     }
@@ -285,7 +313,11 @@ static mat4 step_matrix(const orc_tool* t, const orc_process* p, const mat4* A,
     double theta = (p->phase0_deg + (double)p->rot_sense *
                     ((double)m * p->rot_step_deg +
                      (double)nr * (p->rot_step_deg / (double)refine))) * DEG;
-    double xc = p->pass_x0 + ((double)nq * fs + (double)nr * (fs / (double)refine));
+    double xc;
+    if (p->pass_mode == ORC_ZIGZAG && (pass & 1)) /* run back: step n sits at step spp-1-n */
+        xc = p->pass_x0 + ((double)(p->steps_per_pass - 1 - nq) * fs - (double)nr * (fs / (double)refine));
+    else
+        xc = p->pass_x0 + ((double)nq * fs + (double)nr * (fs / (double)refine));
     double yc = p->pass_y0 + (double)pass * p->ae;
     mat4 tsw = m_translate(xc, yc, z_ref);
     mat4 tts = m_tool_to_spindle(theta);

@@ -43,14 +43,14 @@ extern "C" {
 
 #define ORC_MAX_TEETH 16
 
-enum { ORC_FLAT = 0, ORC_BALL = 1, ORC_INSERT = 2 };
+enum { ORC_FLAT = 0, ORC_BALL = 1, ORC_INSERT = 2, ORC_TORUS = 3 };
 
 /* Cutting tool. Angles in degrees, lengths in mm. */
 typedef struct {
-    int32_t kind;          /* ORC_FLAT or ORC_BALL */
+    int32_t kind;          /* ORC_FLAT, ORC_BALL, ORC_INSERT or ORC_TORUS */
     int32_t n_teeth;       /* 1..ORC_MAX_TEETH */
     int32_t n_edge;        /* flank (flat) or meridian (ball) points, >= 2 */
-    int32_t n_end;         /* flat bottom-edge points, 0 or >= 2 (ball: 0) */
+    int32_t n_end;         /* flat bottom-edge points, 0 or >= 2 (flat, torus; else 0) */
     double diameter;       /* D */
     double helix_deg[ORC_MAX_TEETH];  /* helix angle of each tooth */
     double tooth_deg[ORC_MAX_TEETH];  /* angular position of each tooth */
@@ -62,6 +62,10 @@ typedef struct {
     double insert_radius;
     double rake_f_deg, rake_p_deg;
     double eps_r_mm, eps_a_mm;
+    /* bull-nose end mill (ORC_TORUS, an extension): corner radius rc,
+     * 0 < rc <= D/2; n_end bottom points on the flat part, n_edge points
+     * along the corner arc and the flank */
+    double corner_radius;
 } orc_tool;
 
 /* Process and workpiece grid. */
@@ -89,7 +93,13 @@ typedef struct {
      * The tool reference height is the same in both (orc_z_ref). */
     int32_t surface;
     double wall_y;
+    /* ORC_ONE_WAY: every pass runs along +X from pass_x0; ORC_ZIGZAG: odd
+     * passes run back along -X over the same stretch (step n of an odd pass
+     * is where step steps_per_pass-1-n of an even pass is) */
+    int32_t pass_mode;
 } orc_process;
+
+enum { ORC_ONE_WAY = 0, ORC_ZIGZAG = 1 };
 
 enum { ORC_FLOOR = 0, ORC_WALL = 1 };
 

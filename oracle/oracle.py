@@ -26,7 +26,7 @@ class OrcTool(C.Structure):
         ("helix_deg", C.c_double * MAX_TEETH), ("tooth_deg", C.c_double * MAX_TEETH),
         ("runout_mm", C.c_double), ("runout_phase_deg", C.c_double),
         ("insert_radius", C.c_double), ("rake_f_deg", C.c_double), ("rake_p_deg", C.c_double),
-        ("eps_r_mm", C.c_double), ("eps_a_mm", C.c_double),
+        ("eps_r_mm", C.c_double), ("eps_a_mm", C.c_double), ("corner_radius", C.c_double),
     ]
 
 
@@ -39,7 +39,7 @@ class OrcProcess(C.Structure):
         ("steps_per_pass", C.c_int64), ("stock_z", C.c_double),
         ("x0", C.c_double), ("y0", C.c_double), ("pitch", C.c_double),
         ("nx", C.c_int32), ("ny", C.c_int32), ("z_ref_override", C.c_double),
-        ("surface", C.c_int32), ("wall_y", C.c_double),
+        ("surface", C.c_int32), ("wall_y", C.c_double), ("pass_mode", C.c_int32),
     ]
 
 
@@ -92,10 +92,10 @@ def lib():
 
 def make_tool(tool) -> OrcTool:
     t = OrcTool()
-    t.kind = {"flat": 0, "ball": 1, "insert": 2}[tool.kind]
+    t.kind = {"flat": 0, "ball": 1, "insert": 2, "torus": 3}[tool.kind]
     t.n_teeth = tool.n_teeth
     t.n_edge = tool.n_edge
-    t.n_end = tool.n_end if tool.kind == "flat" else 0
+    t.n_end = tool.n_end if tool.kind in ("flat", "torus") else 0
     t.diameter = tool.diameter
     for k, (h, a) in enumerate(zip(tool.helix(), tool.teeth_angles())):
         t.helix_deg[k] = h
@@ -107,6 +107,7 @@ def make_tool(tool) -> OrcTool:
     t.rake_p_deg = tool.rake_p_deg
     t.eps_r_mm = tool.eps_r_mm
     t.eps_a_mm = tool.eps_a_mm
+    t.corner_radius = tool.corner_radius
     return t
 
 
@@ -119,6 +120,7 @@ def make_process(proc, z_ref=None) -> OrcProcess:
     p.z_ref_override = math.nan if z_ref is None else z_ref
     p.surface = {"floor": 0, "wall": 1}[proc.surface]
     p.wall_y = proc.wall_y
+    p.pass_mode = {"one_way": 0, "zigzag": 1}[proc.pass_mode]
     return p
 
 

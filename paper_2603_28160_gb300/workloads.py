@@ -38,20 +38,21 @@ CELL_OFFSET = (0.318309886183791, 0.367879441171442)
 
 @dataclass
 class ToolSpec:
-    kind: str                     # "flat", "ball" or "insert" (round inserts)
+    kind: str                     # "flat", "ball", "insert" (round inserts) or "torus" (bull-nose)
     diameter: float               # mm (inserts: radius of the inserts' lowest points x 2)
     n_teeth: int
     helix_deg: List[float]        # one per tooth
     tooth_deg: Optional[List[float]] = None  # angular positions; None = even pitch
     runout_mm: float = 0.0        # spindle-axis offset, rotates with the tool
     runout_phase_deg: float = 0.0
-    n_edge: int = 50              # flank (flat) / meridian (ball) points
-    n_end: int = 0                # flat bottom-edge points (0 or >= 2)
+    n_edge: int = 50              # flank (flat) / meridian (ball) / corner + flank (torus) points
+    n_end: int = 0                # flat / torus bottom-edge points (0 or >= 2)
     insert_radius: float = 0.0    # round insert radius R
     rake_f_deg: float = 0.0       # radial rake (gamma_f)
     rake_p_deg: float = 0.0       # axial rake (gamma_p)
     eps_r_mm: float = 0.0         # insert K sits K * eps_r further out ...
     eps_a_mm: float = 0.0         # ... and K * eps_a higher
+    corner_radius: float = 0.0    # torus: corner radius rc, 0 < rc <= D/2
 
     def teeth_angles(self) -> List[float]:
         if self.tooth_deg is not None:
@@ -89,6 +90,7 @@ class ProcessSpec:
     precision: str = "fp64"       # "fp64" or "fp32"
     surface: str = "floor"        # "floor" (grid x, y; height z) or "wall" (+Y side wall:
     wall_y: float = 0.0           # grid x, z; height -y; un-machined at y = wall_y)
+    pass_mode: str = "one_way"    # "one_way" or "zigzag" (odd passes run back along -X)
 
     def replace(self, **kw) -> "ProcessSpec":
         return dataclasses.replace(self, **kw)
@@ -112,7 +114,7 @@ class Workload:
     @property
     def trajectory_points(self) -> int:
         """Every (time step, tooth, edge point) triple of the tool path."""
-        per_tooth = self.tool.n_edge + (self.tool.n_end if self.tool.kind == "flat" else 0)
+        per_tooth = self.tool.n_edge + (self.tool.n_end if self.tool.kind in ("flat", "torus") else 0)
         return self.process.trajectory_steps * self.tool.n_teeth * per_tooth
 
 
