@@ -47,8 +47,9 @@ typedef enum {
     FSM_E_STATE = -6          /* wrong call order (e.g. unknown ticket) */
 } fsm_status;
 
-enum { FSM_TOOL_FLAT = 0, FSM_TOOL_BALL = 1, FSM_TOOL_INSERT = 2 };
+enum { FSM_TOOL_FLAT = 0, FSM_TOOL_BALL = 1, FSM_TOOL_INSERT = 2, FSM_TOOL_TORUS = 3 };
 enum { FSM_SURFACE_FLOOR = 0, FSM_SURFACE_WALL = 1 };
+enum { FSM_PASS_ONE_WAY = 0, FSM_PASS_ZIGZAG = 1 };
 enum { FSM_FP64 = 0, FSM_FP32 = 1 };
 
 typedef struct fsm_ctx fsm_ctx;
@@ -74,11 +75,17 @@ typedef struct fsm_process fsm_process;
  *             placed by Eq. eq_cutting_edge_to_tool: radial/axial rake
  *             rotation, lowest point at radius D/2 + K eps_r and height
  *             K eps_a for insert K = 0..n_teeth-1 (the paper's K-1).
+ *             FSM_TOOL_TORUS (an extension): bull-nose end mill with corner
+ *             radius corner_radius = rc: n_end bottom points at h = 0, r
+ *             uniform in [0, D/2 - rc], then n_edge points uniform in arc
+ *             length along the corner arc (centre (D/2 - rc, rc)) and the
+ *             flank, from the bottom up to height ap.
  *   runout    spindle-axis offset of radius runout_mm at runout_phase_deg in
  *             the rotating frame.
- * Validation: 1 <= n_teeth <= 16, n_edge >= 2, n_end == 0 or >= 2 (flat),
- * n_end == 0 (ball, insert), D > 0, runout >= 0, insert_radius > 0 (insert),
- * all values finite. helix_deg is ignored for inserts. */
+ * Validation: 1 <= n_teeth <= 16, n_edge >= 2, n_end == 0 or >= 2 (flat,
+ * torus), n_end == 0 (ball, insert), D > 0, runout >= 0, insert_radius > 0
+ * (insert), 0 < corner_radius <= D/2 (torus), all values finite. helix_deg
+ * is ignored for inserts. */
 typedef struct {
     int32_t kind;
     int32_t n_teeth;
@@ -94,6 +101,7 @@ typedef struct {
     double rake_p_deg;
     double eps_r_mm;
     double eps_a_mm;
+    double corner_radius;
 } fsm_tool_desc;
 
 /* Cutting conditions, tool path and sampling grid (Sections 2.1-2.2).
@@ -117,6 +125,9 @@ typedef struct {
  *   from (x0, y0 = lowest z), height -y (the wall's outward normal is -Y),
  *   un-machined at y = wall_y, so cells keep -wall_y until cut. The tool
  *   reference height is the same as for the floor (stock_z - ap lowest).
+ *   pass_mode FSM_PASS_ONE_WAY: every pass runs along +X from pass_x0;
+ *   FSM_PASS_ZIGZAG: odd passes run back along -X over the same stretch
+ *   (their step n is where step steps_per_pass-1-n of an even pass is).
  * Validation: fz, ap, pitch > 0; 360/rot_step_deg integral; rot_sense = +-1;
  * n_passes >= 1 (== 1 for a wall); steps_per_pass >= 1;
  * n_passes*steps_per_pass < 2^31; 1 <= nx, ny <= 65535*256; finite values.
@@ -144,6 +155,8 @@ typedef struct {
     int32_t precision;
     int32_t surface;
     double wall_y;
+    int32_t pass_mode;
+    int32_t reserved;
 } fsm_process_desc;
 
 /* Optional launch overrides, counters and timing for the prediction calls.

@@ -45,8 +45,12 @@ static int64_t steps_per_rev(double step_deg) {
 
 static fsm_status check_tool(const fsm_tool_desc* t) {
     if (!t) return fail(FSM_E_INVALID, "tool descriptor is NULL");
-    if (t->kind != FSM_TOOL_FLAT && t->kind != FSM_TOOL_BALL && t->kind != FSM_TOOL_INSERT)
+    if (t->kind != FSM_TOOL_FLAT && t->kind != FSM_TOOL_BALL && t->kind != FSM_TOOL_INSERT &&
+        t->kind != FSM_TOOL_TORUS)
         return fail(FSM_E_INVALID, "unknown tool kind");
+    if (t->kind == FSM_TOOL_TORUS &&
+        !(t->corner_radius > 0.0 && t->corner_radius <= 0.5 * t->diameter && finite(t->corner_radius)))
+        return fail(FSM_E_INVALID, "corner_radius must be in (0, D/2]");
     if (t->kind == FSM_TOOL_INSERT) {
         if (!(t->insert_radius > 0.0) || !finite(t->insert_radius)) return fail(FSM_E_INVALID, "insert_radius must be > 0");
         const double v[] = {t->rake_f_deg, t->rake_p_deg, t->eps_r_mm, t->eps_a_mm};
@@ -56,9 +60,9 @@ static fsm_status check_tool(const fsm_tool_desc* t) {
     }
     if (t->n_teeth < 1 || t->n_teeth > FSM_MAX_TEETH) return fail(FSM_E_INVALID, "n_teeth must be 1..16");
     if (t->n_edge < 2) return fail(FSM_E_INVALID, "n_edge must be >= 2");
-    if (t->kind == FSM_TOOL_FLAT && (t->n_end < 0 || t->n_end == 1))
-        return fail(FSM_E_INVALID, "n_end must be 0 or >= 2");
-    if (t->kind != FSM_TOOL_FLAT && t->n_end != 0) return fail(FSM_E_INVALID, "only a flat end has n_end > 0");
+    const bool has_end = t->kind == FSM_TOOL_FLAT || t->kind == FSM_TOOL_TORUS;
+    if (has_end && (t->n_end < 0 || t->n_end == 1)) return fail(FSM_E_INVALID, "n_end must be 0 or >= 2");
+    if (!has_end && t->n_end != 0) return fail(FSM_E_INVALID, "only flat and torus ends have n_end > 0");
     if ((int64_t)t->n_teeth * (t->n_edge + t->n_end) > (1 << 22))
         return fail(FSM_E_INVALID, "too many edge points");
     if (!(t->diameter > 0.0) || !finite(t->diameter)) return fail(FSM_E_INVALID, "diameter must be > 0");
@@ -94,6 +98,8 @@ static fsm_status check_process(const fsm_process_desc* p) {
         return fail(FSM_E_INVALID, "unknown surface");
     if (p->surface == FSM_SURFACE_WALL && p->n_passes != 1)
         return fail(FSM_E_INVALID, "a wall map takes a single pass");
+    if (p->pass_mode != FSM_PASS_ONE_WAY && p->pass_mode != FSM_PASS_ZIGZAG)
+        return fail(FSM_E_INVALID, "unknown pass_mode");
     return FSM_OK;
 }
 
@@ -142,7 +148,8 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     s->kind = t.kind;
     s->n_teeth = t.n_teeth;
     s->n_edge = t.n_edge;
-    s->n_end = t.kind == FSM_TOOL_FLAT ? t.n_end : 0;
+    s->n_end = (t.kind == FSM_TOOL_FLAT || t.kind == FSM_TOOL_TORUS) ? t.n_end : 0;
+    s->corner_radius = t.corner_radius;
     s->diameter = t.diameter;
     s->runout_mm = t.runout_mm;
     s->runout_phase_deg = t.runout_phase_deg;
@@ -171,6 +178,7 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     s->stock_z = p.stock_z;
     s->surface = p.surface;
     s->wall_y = p.wall_y;
+    s->pass_mode = p.pass_mode;
     s->x0 = p.x0;
     s->y0 = p.y0;
     s->pitch = p.pitch;
@@ -307,7 +315,8 @@ fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* sm
 std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
     char buf[256];
     snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%.6g/%d/%d/%.6g", p.surface, p.precision, t.kind, t.n_teeth,
-             t.n_edge + (t.kind == FSM_TOOL_FLAT ? t.n_end : 0), (int)steps_per_rev(p.rot_step_deg), t.diameter,
+             t.n_edge + ((t.kind == FSM_TOOL_FLAT || t.kind == FSM_TOOL_TORUS) ? t.n_end : 0),
+             (int)steps_per_rev(p.rot_step_deg), t.diameter,
              p.nx, p.ny, p.pitch);
     return buf;
 }

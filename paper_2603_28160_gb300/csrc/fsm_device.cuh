@@ -44,6 +44,7 @@ struct Surface {
     double helix_deg[kMaxTeeth];
     double tooth_deg[kMaxTeeth];
     double insert_radius, rake_f_deg, rake_p_deg, eps_r_mm, eps_a_mm;
+    double corner_radius;
     // ---- process (inputs) ----
     double fz, rot_step_deg, phase0_deg;
     int32_t rot_sense, n_passes;
@@ -51,7 +52,7 @@ struct Surface {
     int32_t steps_per_pass, S;       // steps per pass, steps per revolution
     double stock_z, x0, y0, pitch;
     int32_t nx, ny, precision, E;    // E = points per tooth
-    int32_t surface, pad0;           // FSM_SURFACE_FLOOR / FSM_SURFACE_WALL
+    int32_t surface, pass_mode;      // FSM_SURFACE_*, FSM_PASS_*
     double wall_y;
     // ---- launch geometry (inputs) ----
     int32_t tile_x, tile_y, ntx, nty;
@@ -275,6 +276,7 @@ struct TileFrame {
     int32_t s0, n_steps;
     float inv_dth, dth;
     int32_t S;
+    int32_t reversed;   // the pass runs back: step n sits at step n_steps-1-n
 };
 
 // All runs of one edge point for one (tile, pass): the steps at which it can
@@ -302,6 +304,11 @@ FSM_HD int point_runs(const PointGeom& g, const TileFrame& f, Run* runs) {
         if (nlo < 0.f) nlo = 0.f;
         if (nhi > (float)(f.n_steps - 1)) nhi = (float)(f.n_steps - 1);
         if (nlo > nhi) continue;
+        if (f.reversed) {  // the window was found for the mirrored step index
+            const float lo2 = (float)(f.n_steps - 1) - nhi;
+            nhi = (float)(f.n_steps - 1) - nlo;
+            nlo = lo2;
+        }
         runs[nr].m0 = ia[a].m0;
         runs[nr].len = ia[a].len;
         runs[nr].s_lo = f.s0 + (int32_t)nlo;

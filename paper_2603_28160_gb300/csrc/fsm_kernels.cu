@@ -126,6 +126,25 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
                     r = R;
                     h = sf.ap * ((double)(j - sf.n_end) / (double)(sf.n_edge - 1));
                 }
+            } else if (sf.kind == 3) {  // torus: bottom flat, then the corner arc and flank by arc length
+                const double rc = sf.corner_radius;
+                if (j < sf.n_end) {
+                    r = (R - rc) * ((double)j / (double)(sf.n_end - 1));
+                    h = 0.0;
+                } else {
+                    const double arc_top = sf.ap >= rc ? 0.5 * 3.14159265358979323846 : acos(1.0 - sf.ap / rc);
+                    const double len_arc = rc * arc_top;
+                    const double len = len_arc + (sf.ap > rc ? sf.ap - rc : 0.0);
+                    const double sa = len * ((double)(j - sf.n_end) / (double)(sf.n_edge - 1));
+                    if (sa <= len_arc) {
+                        const double kappa = sa / rc;
+                        r = R - rc + rc * sin(kappa);
+                        h = rc * (1.0 - cos(kappa));
+                    } else {
+                        r = R;
+                        h = rc + (sa - len_arc);
+                    }
+                }
             } else {              // ball: uniform in polar angle over the engaged cap
                 double kappa = kap[0] + (kap[1] - kap[0]) * ((double)j / (double)(E - 1));
                 r = R * sin(kappa);
@@ -331,8 +350,11 @@ __device__ __forceinline__ Vec9 load_vec9(const double* t64, int NE, int idx) {
 // Every FP64 pose of the library goes through these functions, with each
 // rounding step spelled out, so the FP64 path and the FP32 path's re-binning
 // assign a point to the same cell.
-__device__ __forceinline__ double path_x(const Surface& sf, int32_t n) {
-    return __dadd_rn(sf.pass_x0, __dmul_rn((double)n, sf.fs));
+__device__ __forceinline__ bool pass_reversed(const Surface& sf, int p) { return sf.pass_mode == 1 && (p & 1); }
+// tool reference x at local step n of pass p (a zig-zag return pass runs back)
+__device__ __forceinline__ double path_x(const Surface& sf, int p, int32_t n) {
+    const int32_t k = pass_reversed(sf, p) ? sf.steps_per_pass - 1 - n : n;
+    return __dadd_rn(sf.pass_x0, __dmul_rn((double)k, sf.fs));
 }
 __device__ __forceinline__ double path_y(const Surface& sf, int p) {
     return __dadd_rn(sf.path_y0, __dmul_rn((double)p, sf.path_dy));
@@ -462,6 +484,7 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         f.dth = sf.dth_f;
         f.inv_dth = sf.inv_dth_f;
         f.S = sf.S;
+        f.reversed = pass_reversed(sf, p) ? 1 : 0;
         Run runs[kMaxArcs];
         const int n = point_runs(geo, f, runs);
         // FP32 error bounds of z and of the tile-local x, y for this point
@@ -483,7 +506,8 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
             r.len0 = it.len0;
             r.total = it.total;
             const int32_t sA = it.occ0 + it.first_off;
-            r.dxA = df_affine(ts.dx_hi, ts.dx_lo, sA - f.s0, sf.fs_hi, sf.fs_lo);
+            const int32_t nA = f.reversed ? f.n_steps - 1 - (sA - f.s0) : sA - f.s0;
+            r.dxA = df_affine(ts.dx_hi, ts.dx_lo, nA, sf.fs_hi, sf.fs_lo);
             const float span_mm = (float)(runs[a].s_hi - runs[a].s_lo) * sf.fs_f;
             r.g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * sf.inv_pitch_f + sf.guard_extra;
             r.inv_len = 1.0f / (float)r.len;
@@ -525,7 +549,7 @@ __device__ __noinline__ uint2 rebin_flush(const Surface& sf, uint32_t* cells, in
         const int NE = sf.n_teeth * sf.E;
         const int s = ws.q_s[lane], m = ws.q_m[lane], idx = ws.q_idx[lane];
         const Vec9 v = load_vec9(sf.tool64, NE, idx);
-        const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, s - p * sf.steps_per_pass), path_y(sf, p), sf.z_ref);
+        const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, p, s - p * sf.steps_per_pass), path_y(sf, p), sf.z_ref);
         c.x = 1u;
         if (P.z < sf.stock) {
             const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tx * sf.tile_x;
@@ -617,7 +641,7 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
     const int lane = threadIdx.x & 31;
     const int hl = lane & 15, half = lane >> 4;
     const int S = sf.S;
-    const float fs32 = sf.fs_f;
+    const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
     const float inv_pitch = sf.inv_pitch_f;
     const float2* __restrict__ ph32 = sf.ph32;
     const int tile_x = sf.tile_x;
@@ -731,7 +755,7 @@ __device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<un
                 ++cnt.evaluated;
                 const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
                 if (!(z < stock)) continue;
-                const Pose64 P = pose64(v, cs, path_x(sf, s - s0), yc, zr);
+                const Pose64 P = pose64(v, cs, path_x(sf, p, s - s0), yc, zr);
                 const long long ig = bin64(P.x, x0, inv_pitch) - ib;
                 const long long kg = bin64(P.y, y0, inv_pitch) - kb;
                 if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
@@ -1180,18 +1204,28 @@ __global__ void __launch_bounds__(256) profiles_kernel(const RoughJob* __restric
         stride = (size_t)nx;
     }
     const T* h = reinterpret_cast<const T*>(jb.h);
+    // the profile is read from the map once, into shared memory when it fits
+    // (47 KB: 12032 floats or 6016 doubles); the passes below read it there
+    constexpr int kCache = 48128 / (int)sizeof(T);
+    __shared__ T pv[kCache];
+    const bool cached = L <= kCache;
+    if (cached) {
+        for (int a = threadIdx.x; a < L; a += blockDim.x) pv[a] = h[base + (size_t)a * stride];
+        __syncthreads();
+    }
+    auto value = [&](int a) -> double { return cached ? (double)pv[a] : (double)h[base + (size_t)a * stride]; };
     double s = 0.0;
-    for (int a = threadIdx.x; a < L; a += blockDim.x) s += (double)h[base + (size_t)a * stride];
+    for (int a = threadIdx.x; a < L; a += blockDim.x) s += value(a);
     const double mu = block_reduce<0>(s, sh) / (double)L;
     double w = 0.0;
-    for (int a = threadIdx.x; a < L; a += blockDim.x) w += fabs((double)h[base + (size_t)a * stride] - mu);
+    for (int a = threadIdx.x; a < L; a += blockDim.x) w += fabs(value(a) - mu);
     const double ra = block_reduce<0>(w, sh) / (double)L;
     double rz = 0.0;
     for (int seg = 0; seg < 5; ++seg) {  // Rz: max - min over 5 segments [floor(qL/5), floor((q+1)L/5))
         const int lo = (int)(((long long)seg * L) / 5), hi = (int)(((long long)(seg + 1) * L) / 5);
         double mx = -1e300, mn = 1e300;
         for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
-            const double z = (double)h[base + (size_t)a * stride];
+            const double z = value(a);
             mx = fmax(mx, z);
             mn = fmin(mn, z);
         }
@@ -1267,7 +1301,7 @@ __global__ void __launch_bounds__(256) traj_record_kernel(const Surface* __restr
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_steps; s += gridDim.x * blockDim.x) {
         const int p = s / spp;
         const int m = s % S;
-        const double xc = path_x(sf, s - p * spp), yc = path_y(sf, p);
+        const double xc = path_x(sf, p, s - p * spp), yc = path_y(sf, p);
         const double2 cs = __ldg(sf.ph64 + m);
         fsm_traj_point* o = out + (size_t)s * N;
         for (int K = 0; K < N; ++K) {

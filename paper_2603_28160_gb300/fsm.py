@@ -31,7 +31,8 @@ class ToolDesc(C.Structure):
                 ("diameter", C.c_double), ("helix_deg", C.c_double * MAX_TEETH),
                 ("tooth_deg", C.c_double * MAX_TEETH), ("runout_mm", C.c_double),
                 ("runout_phase_deg", C.c_double), ("insert_radius", C.c_double), ("rake_f_deg", C.c_double),
-                ("rake_p_deg", C.c_double), ("eps_r_mm", C.c_double), ("eps_a_mm", C.c_double)]
+                ("rake_p_deg", C.c_double), ("eps_r_mm", C.c_double), ("eps_a_mm", C.c_double),
+                ("corner_radius", C.c_double)]
 
 
 class ProcessDesc(C.Structure):
@@ -41,7 +42,7 @@ class ProcessDesc(C.Structure):
                 ("pass_x0", C.c_double), ("pass_y0", C.c_double), ("steps_per_pass", C.c_int64),
                 ("stock_z", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("pitch", C.c_double),
                 ("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32), ("surface", C.c_int32),
-                ("wall_y", C.c_double)]
+                ("wall_y", C.c_double), ("pass_mode", C.c_int32), ("reserved", C.c_int32)]
 
 
 class PredictOpts(C.Structure):
@@ -124,10 +125,10 @@ def lib() -> C.CDLL:
 
 def tool_desc(t: ToolSpec) -> ToolDesc:
     d = ToolDesc()
-    d.kind = {"flat": 0, "ball": 1, "insert": 2}[t.kind]
+    d.kind = {"flat": 0, "ball": 1, "insert": 2, "torus": 3}[t.kind]
     d.n_teeth = t.n_teeth
     d.n_edge = t.n_edge
-    d.n_end = t.n_end if t.kind == "flat" else 0
+    d.n_end = t.n_end if t.kind in ("flat", "torus") else 0
     d.diameter = t.diameter
     for k, (h, a) in enumerate(zip(t.helix(), t.teeth_angles())):
         d.helix_deg[k] = h
@@ -139,6 +140,7 @@ def tool_desc(t: ToolSpec) -> ToolDesc:
     d.rake_p_deg = t.rake_p_deg
     d.eps_r_mm = t.eps_r_mm
     d.eps_a_mm = t.eps_a_mm
+    d.corner_radius = t.corner_radius
     return d
 
 
@@ -151,6 +153,7 @@ def process_desc(p: ProcessSpec) -> ProcessDesc:
     d.precision = {"fp64": FSM_FP64, "fp32": FSM_FP32}[p.precision]
     d.surface = {"floor": 0, "wall": 1}[p.surface]
     d.wall_y = p.wall_y
+    d.pass_mode = {"one_way": 0, "zigzag": 1}[p.pass_mode]
     return d
 
 

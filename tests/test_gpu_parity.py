@@ -42,6 +42,20 @@ SMALL = {
                                                n_edge=60),
     "paper_case3_insert": lambda: W.paper_case(2, length=0.6, width=0.4, pitch=0.004, rot_step_deg=0.25,
                                                n_edge=60),
+    # bull-nose end mill and zig-zag raster passes
+    "torus_zigzag_lead": lambda: Workload("torus_zz", ToolSpec("torus", 8.0, 3, [30.0], n_edge=60, n_end=60,
+                                                               corner_radius=1.5, runout_mm=0.004),
+                                          ProcessSpec(fz=0.06, rpm=6000, rot_step_deg=0.5, ap=0.4, lead_deg=5.0,
+                                                      pass_x0=-4.6, pass_y0=-0.9, steps_per_pass=8000, n_passes=4,
+                                                      ae=0.6, x0=-0.3 + 0.31 * 0.004, y0=-0.3 + 0.37 * 0.004,
+                                                      pitch=0.004, nx=150, ny=151, pass_mode="zigzag")),
+    "ball_zigzag_tilt": lambda: Workload("ball_zz", ToolSpec("ball", 6.0, 2, [35.0], n_edge=70, runout_mm=0.006,
+                                                             runout_phase_deg=70.0),
+                                         ProcessSpec(fz=0.05, rpm=6000, rot_step_deg=0.5, ap=0.15, tilt_deg=8.0,
+                                                     lead_deg=-4.0, pass_x0=-3.5, pass_y0=-0.25, steps_per_pass=36000,
+                                                     n_passes=5, ae=0.12, x0=-0.25 + 0.31 * 0.003,
+                                                     y0=-0.25 + 0.37 * 0.003, pitch=0.003, nx=167, ny=163,
+                                                     pass_mode="zigzag", rot_sense=-1)),
     "flat_tilt_runout": lambda: Workload("flat_tilt", ToolSpec("flat", 3.0, 3, [35.0, 38.0, 41.0], n_edge=20,
                                                                n_end=80, runout_mm=0.008),
                                          ProcessSpec(fz=0.05, rpm=6000, rot_step_deg=1.0, ap=0.2, tilt_deg=4.0,

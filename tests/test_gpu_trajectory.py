@@ -38,6 +38,12 @@ CASES = {
     "slot_flat_d6": lambda: W.slot_flat_d6(),
     "insert_case2": lambda: W.paper_case(1, length=0.6, width=0.4, pitch=0.004, rot_step_deg=0.25, n_edge=61),
     "raster_ball_reduced": lambda: W.raster_ball_d10(precision="fp64", width=0.3, n_passes=2),
+    "torus_zigzag": lambda: Workload("torus_zz", ToolSpec("torus", 4.0, 3, [30.0], n_edge=21, n_end=15,
+                                                          corner_radius=0.7, runout_mm=0.003),
+                                     ProcessSpec(fz=0.05, rpm=1000, rot_step_deg=1.0, ap=0.3, lead_deg=6.0,
+                                                 pass_x0=-1.0, pass_y0=-0.1, steps_per_pass=700, n_passes=3,
+                                                 ae=0.1, x0=-0.1, y0=-0.1, pitch=0.005, nx=40, ny=40,
+                                                 pass_mode="zigzag")),
 }
 
 
