@@ -362,7 +362,8 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     if (opts && opts->sweep_events[0]) cudaEventRecord((cudaEvent_t)opts->sweep_events[0], st);
     // tiles are handed out by a device counter that the planning kernel zeroed
     e = launch_sweep_shaped(p.precision, d_s, 1, nullptr, tiles, s.tile_queue,
-                            opts ? (long long*)opts->d_counters : nullptr, grid, sh.threads, smem, st);
+                            opts ? (long long*)opts->d_counters : nullptr, grid, sh.threads, smem, st,
+                            phase_form_pays(t, p, sh.tile_x));
     if (opts && opts->sweep_events[1]) cudaEventRecord((cudaEvent_t)opts->sweep_events[1], st);
     cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");

@@ -297,13 +297,21 @@ __device__ __forceinline__ void warp_flush(Counters& c, long long* out) {
 
 // A run of one edge point with its iteration bookkeeping (see run_iter).
 struct RunRec {
-    int32_t m0, len, occ0, first_off, len0, total;
+    int32_t m0, len, occ0, first_off, len0;
+    int32_t k_last, len_last;  // last revolution of the window and its length
     float dxA;      // FP32 path: tile-local x of the pass at the run's first step
     float g_cells;  // FP32 path: bin ambiguity band of this run (cells)
-    float inv_len;  // 1 / len
 };
 
+__device__ __forceinline__ int32_t rec_total(const RunRec& r) {
+    return r.len0 + (r.k_last > 0 ? (r.k_last - 1) * r.len + r.len_last : 0);
+}
+
 constexpr int kRebinCap = 64;
+// Mean revolutions per run phase from which a task takes the phase form of
+// phase 2 (measured: the ball raster averages 1.7 and is fastest item by
+// item; floors and walls come back 4-20 times).
+constexpr int kPhaseFormRevs = 3;
 
 // One warp's scratch: runs of 32 edge points and the FP64 re-binning queue.
 struct WarpScratch {
@@ -374,7 +382,7 @@ __device__ __forceinline__ long long bin64(double coord, double origin, double i
 __device__ __forceinline__ void rec_item(const RunRec& r, int32_t S, float inv_len, int32_t t, int32_t* s,
                                          int32_t* m) {
     int32_t k, off;
-    if (r.total == r.len0) {  // a single occurrence: consecutive steps
+    if (r.k_last == 0) {  // a single occurrence: consecutive steps
         *s = r.occ0 + r.first_off + t;
         const int32_t mm = r.m0 + r.first_off + t;
         *m = mm >= S ? mm - S : mm;
@@ -504,13 +512,13 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
             r.occ0 = it.occ0;
             r.first_off = it.first_off;
             r.len0 = it.len0;
-            r.total = it.total;
+            r.k_last = it.k_last;
+            r.len_last = it.len_last;
             const int32_t sA = it.occ0 + it.first_off;
             const int32_t nA = f.reversed ? f.n_steps - 1 - (sA - f.s0) : sA - f.s0;
             r.dxA = df_affine(ts.dx_hi, ts.dx_lo, nA, sf.fs_hi, sf.fs_lo);
             const float span_mm = (float)(runs[a].s_hi - runs[a].s_lo) * sf.fs_f;
             r.g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * sf.inv_pitch_f + sf.guard_extra;
-            r.inv_len = 1.0f / (float)r.len;
         }
     }
     ws.n[lane] = nr;
@@ -604,23 +612,6 @@ __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint
     }
 }
 
-// Item t of a run, without branches (both halves of a warp may be on runs of
-// different shapes): first occurrence if t < len0, later ones otherwise.
-__device__ __forceinline__ void rec_item_sel(const RunRec& r, int32_t S, int32_t t, int32_t* s, int32_t* m) {
-    const int32_t tt = t - r.len0;
-    int32_t q = __float2int_rz((float)max(tt, 0) * r.inv_len);
-    q += ((q + 1) * r.len <= tt) ? 1 : 0;
-    q -= (q * r.len > tt) ? 1 : 0;
-    const bool first = tt < 0;
-    const int32_t k = first ? 0 : 1 + q;
-    const int32_t off = first ? r.first_off + t : tt - q * r.len;
-    *s = r.occ0 + k * S + off;
-    const int32_t mm = r.m0 + off;
-    *m = mm >= S ? mm - S : mm;
-}
-
-// The rare tail of an evaluation: an FP32 cell index near a boundary. True
-// if the point could lower one of its candidate cells in this tile.
 __device__ __noinline__ bool ambiguous_may_lower(const uint32_t* cells, int tile_x, int txc, int tyc, int i, int k,
                                                  float rx, float ry, float g, float z, float eps_z) {
     const int i0 = max(rx < g ? i - 1 : i, 0), i1 = min(rx > 1.f - g ? i + 1 : i, txc - 1);
@@ -632,10 +623,27 @@ __device__ __noinline__ bool ambiguous_may_lower(const uint32_t* cells, int tile
     return false;
 }
 
-// Phase 2 (FP32): the task's runs are taken two at a time, one per half-warp;
-// each lane evaluates two items of its half's run per iteration, written as
-// two interleaved, mostly predicated chains.
-__device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
+// Item t of a run, without branches (both halves of a warp may be on runs of
+// different shapes): first occurrence if t < len0, later ones otherwise.
+__device__ __forceinline__ void rec_item_sel(const RunRec& r, int32_t S, float inv_len, int32_t t, int32_t* s,
+                                             int32_t* m) {
+    const int32_t tt = t - r.len0;
+    int32_t q = __float2int_rz((float)max(tt, 0) * inv_len);
+    q += ((q + 1) * r.len <= tt) ? 1 : 0;
+    q -= (q * r.len > tt) ? 1 : 0;
+    const bool first = tt < 0;
+    const int32_t k = first ? 0 : 1 + q;
+    const int32_t off = first ? r.first_off + t : tt - q * r.len;
+    *s = r.occ0 + k * S + off;
+    const int32_t mm = r.m0 + off;
+    *m = mm >= S ? mm - S : mm;
+}
+
+// Phase 2 (FP32), item form for runs of few revolutions: the task's runs are
+// taken two at a time, one per half-warp; each lane evaluates two items of
+// its half's run per iteration, written as two interleaved, mostly
+// predicated chains.
+__device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
                                              int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
                                              Counters& cnt) {
     const int lane = threadIdx.x & 31;
@@ -657,16 +665,17 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
         const int o = code >> 2, a = code & 3;
         RunRec r = ws.run[o][a];
         if (!has) {  // a well-formed empty run: its (unused) item indices stay at phase 0
-            r.m0 = 0; r.len = 1; r.occ0 = 0; r.first_off = 0; r.len0 = 1; r.total = 0;
-            r.dxA = 0.f; r.g_cells = 0.f; r.inv_len = 1.f;
+            r.m0 = 0; r.len = 1; r.occ0 = 0; r.first_off = 0; r.len0 = 1; r.k_last = 0; r.len_last = 0;
+            r.dxA = 0.f; r.g_cells = 0.f;
         }
+        const float inv_len = 1.0f / (float)r.len;
         const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
         const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
         const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
         const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
         const int idx = K * sf.E + g * 32 + o;
-        const int tot = r.total;
+        const int tot = has ? rec_total(r) : 0;
         const int tmax = max(tot, __shfl_xor_sync(0xffffffffu, tot, 16));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
@@ -675,8 +684,8 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
             const int ta = base + hl, tb = base + 16 + hl;
             const bool va = ta < tot, vb = tb < tot;
             int32_t sa, ma, sb, mb;
-            rec_item_sel(r, S, va ? ta : 0, &sa, &ma);
-            rec_item_sel(r, S, vb ? tb : 0, &sb, &mb);
+            rec_item_sel(r, S, inv_len, va ? ta : 0, &sa, &ma);
+            rec_item_sel(r, S, inv_len, vb ? tb : 0, &sb, &mb);
             const float2 ca = __ldg(ph32 + ma);
             const float2 cb = __ldg(ph32 + mb);
             cnt.evaluated += (unsigned)va + (unsigned)vb;
@@ -724,6 +733,115 @@ __device__ __forceinline__ void sweep_task32(const Surface& sf, const TileCtx<ui
     if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
 }
 
+// Phase 2 (FP32), phase form for runs of many revolutions. The task's runs
+// are taken two at a time, one per half-warp, and every lane takes phase
+// offsets of its run. Height, y cell
+// and the point's x offset depend on the spindle phase alone, so they are
+// computed once per offset; the revolutions in which that phase lies inside
+// the run's step window differ only by a shift of S fs in x, and the ones
+// that can bring the point within a cell of the tile are found in closed
+// form and visited. Each visit evaluates exactly as a single item would
+// (the same FP32 pose, binning, guard band and FP64 re-binning).
+__device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
+                                               int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
+                                               Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const int hl = lane & 15, half = lane >> 4;
+    const int S = sf.S;
+    const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
+    const float inv_pitch = sf.inv_pitch_f;
+    const float pitch = 1.0f / inv_pitch;
+    const float2* __restrict__ ph32 = sf.ph32;
+    const int tile_x = sf.tile_x;
+    uint32_t* cells = tc.cells;
+    const int txc = tc.txc, tyc = tc.tyc;
+    const float x_hi = (float)txc * pitch + pitch;  // tile x range plus a cell each side, tile-local
+    const float x_lo = -pitch;
+    const float rev = (float)S * fs32;            // x shift per revolution
+    const float inv_rev = 1.0f / rev;
+    int R = ws.n[lane];
+    for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
+    int qn = 0;  // queued re-bins (warp-uniform)
+    for (int q = 0; q < R; q += 2) {
+        const int ri = q + half;
+        const bool has = ri < R;
+        const int code = has ? (int)ws.flat[ri] : 0;
+        const int o = code >> 2, a = code & 3;
+        RunRec r = ws.run[o][a];
+        if (!has) {  // a well-formed empty run (no offsets; its fields stay in range)
+            r.m0 = 0; r.len = 0; r.occ0 = 0; r.first_off = 0; r.len0 = 0; r.k_last = 0; r.len_last = 0;
+            r.dxA = 0.f; r.g_cells = 0.f;
+        }
+        const int len = r.len;
+        const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
+        const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
+        const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
+        const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
+        const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
+        const int idx = K * sf.E + g * 32 + o;
+        const int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 16));
+        const int32_t sA = r.occ0 + r.first_off;
+        const float gc = r.g_cells;
+        const float hg = 0.5f - gc;
+        const int f0 = r.first_off, f1 = r.first_off + r.len0;
+        for (int ob = 0; ob < lmax; ob += 16) {
+            const int off = ob + hl;
+            const bool vo = off < len;
+            const int offc = vo ? off : 0;
+            int32_t m = r.m0 + offc;
+            m = m >= S ? m - S : m;
+            const float2 c = __ldg(ph32 + m);
+            const float z = fmaf(c.x, uz, fmaf(c.y, vz, zb));
+            const float px = fmaf(c.x, ux, fmaf(c.y, vx, wx));
+            const float y = dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
+            const float fy = y * inv_pitch;
+            const float ly = floorf(fy);
+            const float ry = fy - ly;
+            const int ky = (int)ly;
+            // revolutions of this phase inside the window: the first only for
+            // offsets it covers, the last only below its length
+            const int kb = (offc >= f0 && offc < f1) ? 0 : 1;
+            const int ke = r.k_last == 0 ? 0 : (offc < r.len_last ? r.k_last : r.k_last - 1);
+            // ... and among them those whose x lies within a cell of the tile
+            const float x0 = fmaf((float)(r.occ0 + offc - sA), fs32, r.dxA) + px;
+            const float ka = (x_lo - x0) * inv_rev, kz = (x_hi - x0) * inv_rev;
+            const int k0 = max(kb, (int)floorf(fminf(ka, kz)) - 1);
+            const int k1 = min(ke, (int)ceilf(fmaxf(ka, kz)) + 1);
+            const bool row = vo && z < 0.f && ky >= -1 && ky <= tyc;
+            const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
+            int n_max = n_it;
+            for (int o2 = 16; o2 > 0; o2 >>= 1) n_max = max(n_max, __shfl_xor_sync(0xffffffffu, n_max, o2));
+            const uint32_t e = enc32(__float_as_uint(z));
+            const bool ky_in = (unsigned)ky < (unsigned)tyc;
+            const float dy = fabsf(ry - 0.5f);
+            for (int kk = 0; kk < n_max; ++kk) {
+                const bool v = kk < n_it;
+                const int32_t s = r.occ0 + (k0 + kk) * S + offc;
+                const float x = fmaf((float)(s - sA), fs32, r.dxA) + px;
+                const float fx = x * inv_pitch;
+                const float lx = floorf(fx);
+                const float rx = fx - lx;
+                const int ix = (int)lx;
+                cnt.evaluated += (unsigned)v;
+                const bool in = v && ky_in && (unsigned)ix < (unsigned)txc;
+                cnt.cutting += (unsigned)in;
+                const bool amb = fmaxf(fabsf(rx - 0.5f), dy) > hg;  // within gc of a cell boundary
+                const bool upd = in && !amb;
+                const int ci = ky * tile_x + ix;
+                const uint32_t cv = upd ? cells[ci] : 0u;
+                if (upd && e < cv) {
+                    atomicMin(cells + ci, e);
+                    ++cnt.atomics;
+                }
+                bool w = false;
+                if (v && amb) w = ambiguous_may_lower(cells, tile_x, txc, tyc, ix, ky, rx, ry, gc, z, eps_z);
+                if (__any_sync(0xffffffffu, w)) rebin_push(sf, tc, ws, p, w, s, m, idx, qn, cnt);
+            }
+        }
+    }
+    if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 path: all pose and binning arithmetic in FP64, global coordinates.
 // ---------------------------------------------------------------------------
@@ -748,9 +866,11 @@ __device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<un
         const Vec9 v = load_vec9(sf.tool64, NE, idx);
         for (int a = 0; a < nr; ++a) {
             const RunRec r = ws.run[o][a];
-            for (int t = lane; t < r.total; t += 32) {
+            const int32_t total = rec_total(r);
+            const float inv_len = 1.0f / (float)r.len;
+            for (int t = lane; t < total; t += 32) {
                 int32_t s, m;
-                rec_item(r, S, r.inv_len, t, &s, &m);
+                rec_item(r, S, inv_len, t, &s, &m);
                 const double2 cs = __ldg(ph64 + m);
                 ++cnt.evaluated;
                 const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
@@ -784,7 +904,7 @@ __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) 
 // (tile_base[s] = first tile of surface s); CTAs take tiles in a static
 // stride, or from *queue when it is not NULL. Inside a tile, warps take
 // (pass, tooth, 32-point group) tasks from a shared counter.
-template <bool FP64, bool kCount>
+template <bool FP64, bool kCount, bool kPhases>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
                                                        const int* __restrict__ tile_base, int total_tiles,
                                                        int* queue, long long* counters) {
@@ -853,7 +973,26 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             } else {
                 float yl2, yh2, dyp;
                 pass_band(sf, tc, ts, p, &yl2, &yh2, &dyp);
-                sweep_task32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
+                // runs that come back for many revolutions share their per-phase
+                // work (phase form); others are walked item by item
+                if constexpr (!kPhases) {
+                    sweep_items32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
+                    __syncwarp();
+                    continue;
+                }
+                int tot = 0, phases = 0;
+                for (int a = 0; a < ws.n[lane]; ++a) {
+                    tot += rec_total(ws.run[lane][a]);
+                    phases += ws.run[lane][a].len;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                    phases += __shfl_xor_sync(0xffffffffu, phases, o);
+                }
+                if (tot >= kPhaseFormRevs * phases)
+                    sweep_phases32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
+                else
+                    sweep_items32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
             }
             __syncwarp();
         }
@@ -1334,13 +1473,16 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
     Surface dummy;
     if (one) dummy = *one;
     else memset(&dummy, 0, sizeof dummy);
-    // a lone surface spreads its FP64 table work over many blocks
-    int parts = 1;
+    // A lone surface spreads its FP64 table work thinly over many SMs (small
+    // blocks): the FP64 transcendentals of the tables are bound by each SM's
+    // FP64 pipe, not by the thread count. A batch gives each surface a block.
+    int parts = 1, threads = 256;
     if (one) {
         const int work = one->n_teeth * one->E + one->S;
-        parts = max(1, min(kPlanParts, (work + 255) / 256));
+        threads = 64;
+        parts = max(1, min(kPlanParts, (work + threads - 1) / threads));
     }
-    plan_kernel<<<dim3(n, parts), 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
+    plan_kernel<<<dim3(n, parts), threads, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
     plan_finish_kernel<<<n, 256, 0, st>>>(d_surfs, n, parts);
     return cudaGetLastError();
 }
@@ -1353,22 +1495,30 @@ size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads) {
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,
-                                cudaStream_t st) {
-    // counting is a separate instantiation: without it the counters are dead code
+                                cudaStream_t st, bool phase_form) {
+    // counting and the FP32 phase form are separate instantiations: without
+    // them the counters are dead code and the item loop has the SM to itself
     if (precision == 0) {
         if (d_counters)
-            sweep_kernel<true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
-                                                                  d_queue, d_counters);
+            sweep_kernel<true, true, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                         d_queue, d_counters);
         else
-            sweep_kernel<true, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
-                                                                   d_queue, nullptr);
+            sweep_kernel<true, false, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                          total_tiles, d_queue, nullptr);
+    } else if (phase_form) {
+        if (d_counters)
+            sweep_kernel<false, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                         d_queue, d_counters);
+        else
+            sweep_kernel<false, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                          total_tiles, d_queue, nullptr);
     } else {
         if (d_counters)
-            sweep_kernel<false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
-                                                                   d_queue, d_counters);
+            sweep_kernel<false, true, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                          total_tiles, d_queue, d_counters);
         else
-            sweep_kernel<false, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
-                                                                    d_queue, nullptr);
+            sweep_kernel<false, false, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                           total_tiles, d_queue, nullptr);
     }
     return cudaGetLastError();
 }
@@ -1386,24 +1536,31 @@ static cudaError_t allow_dynamic_smem(K kernel, size_t max_bytes) {
 
 cudaError_t sweep_allow_smem(size_t max_bytes) {
     cudaError_t e;
-    if ((e = allow_dynamic_smem(sweep_kernel<true, true>, max_bytes)) != cudaSuccess) return e;
-    if ((e = allow_dynamic_smem(sweep_kernel<true, false>, max_bytes)) != cudaSuccess) return e;
-    if ((e = allow_dynamic_smem(sweep_kernel<false, true>, max_bytes)) != cudaSuccess) return e;
-    return allow_dynamic_smem(sweep_kernel<false, false>, max_bytes);
+    if ((e = allow_dynamic_smem(sweep_kernel<true, true, false>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, false, false>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<false, true, false>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<false, false, false>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<false, true, true>, max_bytes)) != cudaSuccess) return e;
+    return allow_dynamic_smem(sweep_kernel<false, false, true>, max_bytes);
 }
 
 // Resident CTAs per SM: the smaller of the counting and plain instantiations.
 int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
     int a = 0, b = 0;
     cudaError_t e1, e2;
+    int c = 1 << 20, d = 1 << 20;
+    cudaError_t e3 = cudaSuccess, e4 = cudaSuccess;
     if (precision == 0) {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<true, true>, threads, smem);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<true, false>, threads, smem);
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<true, true, false>, threads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<true, false, false>, threads, smem);
     } else {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<false, true>, threads, smem);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<false, false>, threads, smem);
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<false, true, false>, threads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<false, false, false>, threads, smem);
+        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, sweep_kernel<false, true, true>, threads, smem);
+        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, sweep_kernel<false, false, true>, threads, smem);
     }
-    return (e1 == cudaSuccess && e2 == cudaSuccess) ? min(a, b) : 0;
+    const bool ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess;
+    return ok ? min(min(a, b), min(c, d)) : 0;
 }
 
 __global__ void rough_setup_one_kernel(RoughJob jb, int chunks, RoughJob* d_job, int* d_base) {
