@@ -1473,16 +1473,14 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
     Surface dummy;
     if (one) dummy = *one;
     else memset(&dummy, 0, sizeof dummy);
-    // A lone surface spreads its FP64 table work thinly over many SMs (small
-    // blocks): the FP64 transcendentals of the tables are bound by each SM's
-    // FP64 pipe, not by the thread count. A batch gives each surface a block.
-    int parts = 1, threads = 256;
+    // a lone surface spreads its FP64 table work over many blocks; a batch
+    // gives each surface one block
+    int parts = 1;
     if (one) {
         const int work = one->n_teeth * one->E + one->S;
-        threads = 64;
-        parts = max(1, min(kPlanParts, (work + threads - 1) / threads));
+        parts = max(1, min(kPlanParts, (work + 255) / 256));
     }
-    plan_kernel<<<dim3(n, parts), threads, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
+    plan_kernel<<<dim3(n, parts), 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
     plan_finish_kernel<<<n, 256, 0, st>>>(d_surfs, n, parts);
     return cudaGetLastError();
 }
