@@ -278,6 +278,9 @@ def side_wall_leg(ctx, F, flush, steps=3):
     t, p = ctx.tool(w.tool), ctx.process(w.process)
     out = F.heights_tensor(w.process)
     rough = torch.zeros(F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+    # the library's autotuner picks the sweep shape for this workload; later
+    # calls with the same shape of problem use it
+    tuned = ctx.autotune(t, p, out)
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     ctx.predict_surface(t, p, out, counters=cnt)
     torch.cuda.synchronize()
@@ -290,7 +293,9 @@ def side_wall_leg(ctx, F, flush, steps=3):
                         % w.tool.n_edge,
             "cells": w.process.cells, "trajectory_points": w.trajectory_points, "cutting": cutting, "steps": steps,
             "ms_per_step": ms, "sweep_ms": sum(sweep_ms) / len(sweep_ms), "value": cutting / (ms / 1e3),
-            "unit": UNIT, "surfaces_per_s": 1e3 / ms}
+            "unit": UNIT, "surfaces_per_s": 1e3 / ms,
+            "sweep_shape": {"tile": list(tuned["tile"]), "threads": tuned["threads"],
+                            "ctas_per_sm": tuned["ctas_per_sm"]}}
 
 
 def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
