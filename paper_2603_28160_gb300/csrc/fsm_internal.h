@@ -36,8 +36,10 @@ cudaError_t launch_trajectory(const Surface* d_surf, int S, int n_teeth, long lo
 
 // Roughness of a set of maps of one precision. Map j is cut into
 // ceil(n/kChunk) chunks; d_chunk_base[j] is its first chunk (n_jobs+1
-// entries). d_part: 7 * total_chunks doubles of scratch. max_profiles = the
-// largest n_rows + n_cols of any job.
+// entries). d_part: 7 * total_chunks doubles of scratch; d_sync:
+// rough_sync_bytes(n_jobs) of scratch (8-byte aligned; cleared by the call).
+// max_profiles = the largest n_rows + n_cols of any job. One memset and two
+// launches.
 constexpr size_t kChunk = 32768;
 struct RoughJob {
     const void* h;
@@ -45,8 +47,10 @@ struct RoughJob {
     int nx, ny, n_rows, n_cols;
     fsm_roughness_out* out;
 };
+size_t rough_sync_bytes(int n_jobs);
 cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_jobs, const int* d_chunk_base,
-                                  int total_chunks, int max_profiles, double* d_part, cudaStream_t st);
+                                  int total_chunks, int max_profiles, double* d_part, void* d_sync,
+                                  cudaStream_t st);
 // One map; d_ws of roughness_one_ws_bytes(n) bytes (256-aligned).
 size_t roughness_one_ws_bytes(size_t n);
 cudaError_t launch_roughness_one(int precision, const RoughJob& jb, char* d_ws, cudaStream_t st);

@@ -1089,11 +1089,68 @@ __device__ __forceinline__ void chunk_range(const RoughJob& jb, int c, size_t* l
 }
 
 // Pass 1: per chunk sum, min, max -> part[b*3 + {0,1,2}]
+// Sync words of a set of roughness jobs: pass-1 and pass-2 completion
+// counters and the job means (zeroed before pass 1).
+struct RoughSync {
+    int* done1;
+    int* done2;
+    double* mean;
+};
+
+__device__ __forceinline__ RoughSync rough_sync(void* base, int n_jobs) {
+    RoughSync r;
+    r.done1 = (int*)base;
+    r.done2 = r.done1 + n_jobs;
+    r.mean = (double*)((char*)base + ((8 * (size_t)n_jobs + 7) & ~(size_t)7));
+    return r;
+}
+
+// Called by the whole block: true in the block that completes job j's last
+// chunk of this pass (its writes and every other block's are then visible).
+__device__ __forceinline__ bool last_chunk_block(int* done, int j, int n_chunks) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(done + j, 1) == n_chunks - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__device__ double job_mean(const double* part, int c0, int c1, size_t n, double* sh) {
+    double s = 0.0;
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) s += __ldcg(part + 3 * (size_t)c);
+    s = block_reduce<0>(s, sh);
+    return s / (double)n;
+}
+
+// End of pass 1: the block completing job j's last chunk stores its mean.
+__device__ __forceinline__ void job_mean_if_last(const RoughJob* __restrict__ jobs,
+                                                 const int* __restrict__ chunk_base, const double* part, int n_jobs,
+                                                 int j, void* sync, double* sh) {
+    const RoughSync rs = rough_sync(sync, n_jobs);
+    const int c0 = chunk_base[j], c1 = chunk_base[j + 1];
+    if (last_chunk_block(rs.done1, j, c1 - c0)) {
+        const double mu = job_mean(part, c0, c1, jobs[j].n, sh);
+        if (threadIdx.x == 0) rs.mean[j] = mu;
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) rough1_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
-                                                     const int* __restrict__ chunk_base, double* part) {
-    __shared__ double sh[32];
-    const int b = blockIdx.x;
+__device__ void profile_block(const RoughJob* __restrict__ jobs, int pb, int per_job, double* sh);
+__device__ void finalize_job(const RoughJob* __restrict__ jobs, const int* __restrict__ chunk_base,
+                             const double* part, const double* part2, int j, double mu, double* sh);
+
+template <typename T>
+__device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, int n_jobs,
+                                            const int* __restrict__ chunk_base, double* part, int total_chunks,
+                                            int per_job, void* sync, int b, double* sh) {
+    if (b >= total_chunks) {  // the profiles ride along after the chunks
+        profile_block<T>(jobs, b - total_chunks, per_job, sh);
+        return;
+    }
     const int j = find_job(chunk_base, n_jobs, b);
     const RoughJob jb = jobs[j];
     size_t lo, hi;
@@ -1115,182 +1172,24 @@ __global__ void __launch_bounds__(256) rough1_kernel(const RoughJob* __restrict_
         part[3 * (size_t)b + 1] = mn;
         part[3 * (size_t)b + 2] = mx;
     }
+    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, sh);
 }
 
 // Mean of job j from its chunk sums, in chunk order (identical in every block).
-__device__ double job_mean(const double* part, int c0, int c1, size_t n, double* sh) {
-    double s = 0.0;
-    for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) s += part[3 * (size_t)c];
-    s = block_reduce<0>(s, sh);
-    return s / (double)n;
-}
 
-// Pass 2: per chunk sums of |d|, d^2, d^3, d^4 about the job mean -> part2[b*4 + a]
-template <typename T>
-__global__ void __launch_bounds__(256) rough2_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
-                                                     const int* __restrict__ chunk_base, const double* part,
-                                                     double* part2) {
-    __shared__ double sh[32];
-    const int b = blockIdx.x;
-    const int j = find_job(chunk_base, n_jobs, b);
-    const RoughJob jb = jobs[j];
-    const double mu = job_mean(part, chunk_base[j], chunk_base[j + 1], jb.n, sh);
-    size_t lo, hi;
-    chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
-    const T* h = reinterpret_cast<const T*>(jb.h);
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-#pragma unroll 4
-    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double d = (double)h[i] - mu;
-        const double d2 = d * d;
-        v0 += fabs(d);
-        v1 += d2;
-        v2 += d2 * d;
-        v3 += d2 * d2;
-    }
-    v0 = block_reduce<0>(v0, sh);
-    v1 = block_reduce<0>(v1, sh);
-    v2 = block_reduce<0>(v2, sh);
-    v3 = block_reduce<0>(v3, sh);
-    if (threadIdx.x == 0) {
-        double* o = part2 + 4 * (size_t)b;
-        o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
-    }
-}
-
-// FP32 maps: the same two passes with 16-byte loads; per-cell terms in FP32,
-// summed in FP32 over 32 cells and then folded into the FP64 sums (relative
-// error of a leaf <= 32 u ~ 2e-6, far inside the FP32 path's 1e-4 target;
-// FP64 maps keep FP64 throughout). The mean is used as a float pair so the
-// deviations keep full FP32 precision.
-__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
-
-__global__ void __launch_bounds__(256) rough1_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
-                                                         const int* __restrict__ chunk_base, double* part) {
-    __shared__ double sh[32];
-    const int b = blockIdx.x;
-    const int j = find_job(chunk_base, n_jobs, b);
-    const RoughJob jb = jobs[j];
-    size_t lo, hi;
-    chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
-    const float* h = reinterpret_cast<const float*>(jb.h);
-    double s = 0.0;
-    float mn = 3.0e38f, mx = -3.0e38f;
-    if (aligned16(h)) {
-        const size_t v0 = lo >> 2, v1 = hi >> 2;  // lo is a multiple of 4
-        const float4* h4 = reinterpret_cast<const float4*>(h);
-        size_t v = v0 + threadIdx.x;
-        while (v < v1) {
-            float leaf = 0.f;
-#pragma unroll
-            for (int r = 0; r < 8; ++r, v += blockDim.x) {
-                if (v < v1) {
-                    const float4 q = __ldg(h4 + v);
-                    leaf += (q.x + q.y) + (q.z + q.w);
-                    mn = fminf(mn, fminf(fminf(q.x, q.y), fminf(q.z, q.w)));
-                    mx = fmaxf(mx, fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)));
-                }
-            }
-            s += (double)leaf;
-        }
-        for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
-            const float z = h[i];
-            s += (double)z;
-            mn = fminf(mn, z);
-            mx = fmaxf(mx, z);
-        }
-    } else {
-        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const float z = h[i];
-            s += (double)z;
-            mn = fminf(mn, z);
-            mx = fmaxf(mx, z);
-        }
-    }
-    s = block_reduce<0>(s, sh);
-    const double dmn = block_reduce<1>((double)mn, sh);
-    const double dmx = block_reduce<2>((double)mx, sh);
-    if (threadIdx.x == 0) {
-        part[3 * (size_t)b] = s;
-        part[3 * (size_t)b + 1] = dmn;
-        part[3 * (size_t)b + 2] = dmx;
-    }
-}
-
-__device__ __forceinline__ void dev_terms(float z, float mu_hi, float mu_lo, float* a) {
-    const float d = (z - mu_hi) - mu_lo;
-    const float d2 = d * d;
-    a[0] += fabsf(d);
-    a[1] += d2;
-    a[2] = fmaf(d2, d, a[2]);
-    a[3] = fmaf(d2, d2, a[3]);
-}
-
-__global__ void __launch_bounds__(256) rough2_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
-                                                         const int* __restrict__ chunk_base, const double* part,
-                                                         double* part2) {
-    __shared__ double sh[32];
-    const int b = blockIdx.x;
-    const int j = find_job(chunk_base, n_jobs, b);
-    const RoughJob jb = jobs[j];
-    const double mu = job_mean(part, chunk_base[j], chunk_base[j + 1], jb.n, sh);
-    const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
-    size_t lo, hi;
-    chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
-    const float* h = reinterpret_cast<const float*>(jb.h);
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (aligned16(h)) {
-        const size_t v0 = lo >> 2, v1 = hi >> 2;
-        const float4* h4 = reinterpret_cast<const float4*>(h);
-        size_t q = v0 + threadIdx.x;
-        while (q < v1) {
-            float a[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int r = 0; r < 8; ++r, q += blockDim.x) {
-                if (q < v1) {
-                    const float4 z = __ldg(h4 + q);
-                    dev_terms(z.x, mu_hi, mu_lo, a);
-                    dev_terms(z.y, mu_hi, mu_lo, a);
-                    dev_terms(z.z, mu_hi, mu_lo, a);
-                    dev_terms(z.w, mu_hi, mu_lo, a);
-                }
-            }
-            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
-        }
-        for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
-            float a[4] = {0.f, 0.f, 0.f, 0.f};
-            dev_terms(h[i], mu_hi, mu_lo, a);
-            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
-        }
-    } else {
-        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            float a[4] = {0.f, 0.f, 0.f, 0.f};
-            dev_terms(h[i], mu_hi, mu_lo, a);
-            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
-        }
-    }
-    for (int k = 0; k < 4; ++k) v[k] = block_reduce<0>(v[k], sh);
-    if (threadIdx.x == 0) {
-        double* o = part2 + 4 * (size_t)b;
-        o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
-    }
-}
-
-// Final: one block per job combines its chunks and writes the areal values.
-__global__ void __launch_bounds__(256) rough3_kernel(const RoughJob* __restrict__ jobs,
-                                                     const int* __restrict__ chunk_base, const double* part,
-                                                     const double* part2) {
-    __shared__ double sh[32];
-    const int j = blockIdx.x;
+// Final: the whole block combines job j's chunks (in chunk order) and writes
+// the areal values. Chunk partials written by other blocks of the running
+// launch are read past L1.
+__device__ void finalize_job(const RoughJob* __restrict__ jobs, const int* __restrict__ chunk_base,
+                             const double* part, const double* part2, int j, double mu, double* sh) {
     const RoughJob jb = jobs[j];
     const int c0 = chunk_base[j], c1 = chunk_base[j + 1];
-    const double mu = job_mean(part, c0, c1, jb.n, sh);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     double mn = 1e300, mx = -1e300;
     for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
-        for (int a = 0; a < 4; ++a) v[a] += part2[4 * (size_t)c + a];
-        mn = fmin(mn, part[3 * (size_t)c + 1]);
-        mx = fmax(mx, part[3 * (size_t)c + 2]);
+        for (int a = 0; a < 4; ++a) v[a] += __ldcg(part2 + 4 * (size_t)c + a);
+        mn = fmin(mn, __ldcg(part + 3 * (size_t)c + 1));
+        mx = fmax(mx, __ldcg(part + 3 * (size_t)c + 2));
     }
     for (int a = 0; a < 4; ++a) v[a] = block_reduce<0>(v[a], sh);
     mn = block_reduce<1>(mn, sh);
@@ -1320,11 +1219,11 @@ __global__ void __launch_bounds__(256) rough3_kernel(const RoughJob* __restrict_
     }
 }
 
-// Profiles: block (j, q) handles profile q of job j (rows first, then columns).
+// Profiles: block index pb handles profile q = pb mod per_job of job
+// j = pb / per_job (rows first, then columns).
 template <typename T>
-__global__ void __launch_bounds__(256) profiles_kernel(const RoughJob* __restrict__ jobs, int per_job) {
-    __shared__ double sh[32];
-    const int j = blockIdx.x / per_job, q = blockIdx.x - j * per_job;
+__device__ void profile_block(const RoughJob* __restrict__ jobs, int pb, int per_job, double* sh) {
+    const int j = pb / per_job, q = pb - j * per_job;
     const RoughJob jb = jobs[j];
     if (q >= jb.n_rows + jb.n_cols) return;
     const bool row = q < jb.n_rows;
@@ -1385,6 +1284,200 @@ __global__ void __launch_bounds__(256) profiles_kernel(const RoughJob* __restric
             out->Rz_col[r] = rzv;
         }
     }
+}
+
+
+// Pass 2: per chunk sums of |d|, d^2, d^3, d^4 about the job mean -> part2[b*4 + a]
+template <typename T>
+__device__ __forceinline__ void rough2_item(const RoughJob* __restrict__ jobs, int n_jobs,
+                                            const int* __restrict__ chunk_base, const double* part, double* part2,
+                                            void* sync, int b, double* sh) {
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    const RoughSync rs = rough_sync(sync, n_jobs);
+    const double mu = rs.mean[j];
+    size_t lo, hi;
+    chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
+    const T* h = reinterpret_cast<const T*>(jb.h);
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+#pragma unroll 4
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double d = (double)h[i] - mu;
+        const double d2 = d * d;
+        v0 += fabs(d);
+        v1 += d2;
+        v2 += d2 * d;
+        v3 += d2 * d2;
+    }
+    v0 = block_reduce<0>(v0, sh);
+    v1 = block_reduce<0>(v1, sh);
+    v2 = block_reduce<0>(v2, sh);
+    v3 = block_reduce<0>(v3, sh);
+    if (threadIdx.x == 0) {
+        double* o = part2 + 4 * (size_t)b;
+        o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
+    }
+    // the block that finishes a job's last chunk combines the job
+    if (last_chunk_block(rs.done2, j, chunk_base[j + 1] - chunk_base[j]))
+        finalize_job(jobs, chunk_base, part, part2, j, mu, sh);
+}
+
+// FP32 maps: the same two passes with 16-byte loads; per-cell terms in FP32,
+// summed in FP32 over 32 cells and then folded into the FP64 sums (relative
+// error of a leaf <= 32 u ~ 2e-6, far inside the FP32 path's 1e-4 target;
+// FP64 maps keep FP64 throughout). The mean is used as a float pair so the
+// deviations keep full FP32 precision.
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+__device__ __forceinline__ void rough1_f32_item(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                const int* __restrict__ chunk_base, double* part, int total_chunks,
+                                                int per_job, void* sync, int b, double* sh) {
+    if (b >= total_chunks) {  // the profiles ride along after the chunks
+        profile_block<float>(jobs, b - total_chunks, per_job, sh);
+        return;
+    }
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    size_t lo, hi;
+    chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
+    const float* h = reinterpret_cast<const float*>(jb.h);
+    double s = 0.0;
+    float mn = 3.0e38f, mx = -3.0e38f;
+    if (aligned16(h)) {
+        const size_t v0 = lo >> 2, v1 = hi >> 2;  // lo is a multiple of 4
+        const float4* h4 = reinterpret_cast<const float4*>(h);
+        size_t v = v0 + threadIdx.x;
+        while (v < v1) {
+            float leaf = 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r, v += blockDim.x) {
+                if (v < v1) {
+                    const float4 q = __ldg(h4 + v);
+                    leaf += (q.x + q.y) + (q.z + q.w);
+                    mn = fminf(mn, fminf(fminf(q.x, q.y), fminf(q.z, q.w)));
+                    mx = fmaxf(mx, fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)));
+                }
+            }
+            s += (double)leaf;
+        }
+        for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
+            const float z = h[i];
+            s += (double)z;
+            mn = fminf(mn, z);
+            mx = fmaxf(mx, z);
+        }
+    } else {
+        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const float z = h[i];
+            s += (double)z;
+            mn = fminf(mn, z);
+            mx = fmaxf(mx, z);
+        }
+    }
+    s = block_reduce<0>(s, sh);
+    const double dmn = block_reduce<1>((double)mn, sh);
+    const double dmx = block_reduce<2>((double)mx, sh);
+    if (threadIdx.x == 0) {
+        part[3 * (size_t)b] = s;
+        part[3 * (size_t)b + 1] = dmn;
+        part[3 * (size_t)b + 2] = dmx;
+    }
+    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, sh);
+}
+
+__device__ __forceinline__ void dev_terms(float z, float mu_hi, float mu_lo, float* a) {
+    const float d = (z - mu_hi) - mu_lo;
+    const float d2 = d * d;
+    a[0] += fabsf(d);
+    a[1] += d2;
+    a[2] = fmaf(d2, d, a[2]);
+    a[3] = fmaf(d2, d2, a[3]);
+}
+
+__device__ __forceinline__ void rough2_f32_item(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                const int* __restrict__ chunk_base, const double* part, double* part2,
+                                                void* sync, int b, double* sh) {
+    const int j = find_job(chunk_base, n_jobs, b);
+    const RoughJob jb = jobs[j];
+    const RoughSync rs = rough_sync(sync, n_jobs);
+    const double mu = rs.mean[j];
+    const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
+    size_t lo, hi;
+    chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
+    const float* h = reinterpret_cast<const float*>(jb.h);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (aligned16(h)) {
+        const size_t v0 = lo >> 2, v1 = hi >> 2;
+        const float4* h4 = reinterpret_cast<const float4*>(h);
+        size_t q = v0 + threadIdx.x;
+        while (q < v1) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int r = 0; r < 8; ++r, q += blockDim.x) {
+                if (q < v1) {
+                    const float4 z = __ldg(h4 + q);
+                    dev_terms(z.x, mu_hi, mu_lo, a);
+                    dev_terms(z.y, mu_hi, mu_lo, a);
+                    dev_terms(z.z, mu_hi, mu_lo, a);
+                    dev_terms(z.w, mu_hi, mu_lo, a);
+                }
+            }
+            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+        }
+        for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            dev_terms(h[i], mu_hi, mu_lo, a);
+            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+        }
+    } else {
+        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            dev_terms(h[i], mu_hi, mu_lo, a);
+            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+        }
+    }
+    for (int k = 0; k < 4; ++k) v[k] = block_reduce<0>(v[k], sh);
+    if (threadIdx.x == 0) {
+        double* o = part2 + 4 * (size_t)b;
+        o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
+    }
+    // the block that finishes a job's last chunk combines the job
+    if (last_chunk_block(rs.done2, j, chunk_base[j + 1] - chunk_base[j]))
+        finalize_job(jobs, chunk_base, part, part2, j, mu, sh);
+}
+
+// Persistent roughness passes: blocks walk the items (chunks, then profiles)
+// in a grid stride; partial results are stored per chunk, so the combine
+// order does not depend on which block took which chunk.
+template <typename T>
+__global__ void __launch_bounds__(256) rough1_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                     const int* __restrict__ chunk_base, double* part,
+                                                     int total_chunks, int per_job, void* sync, int n_items) {
+    __shared__ double sh[32];
+    for (int b = blockIdx.x; b < n_items; b += gridDim.x)
+        rough1_item<T>(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, b, sh);
+}
+__global__ void __launch_bounds__(256) rough1_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                         const int* __restrict__ chunk_base, double* part,
+                                                         int total_chunks, int per_job, void* sync, int n_items) {
+    __shared__ double sh[32];
+    for (int b = blockIdx.x; b < n_items; b += gridDim.x)
+        rough1_f32_item(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, b, sh);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) rough2_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                     const int* __restrict__ chunk_base, const double* part,
+                                                     double* part2, void* sync, int total_chunks) {
+    __shared__ double sh[32];
+    for (int b = blockIdx.x; b < total_chunks; b += gridDim.x)
+        rough2_item<T>(jobs, n_jobs, chunk_base, part, part2, sync, b, sh);
+}
+__global__ void __launch_bounds__(256) rough2_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+                                                         const int* __restrict__ chunk_base, const double* part,
+                                                         double* part2, void* sync, int total_chunks) {
+    __shared__ double sh[32];
+    for (int b = blockIdx.x; b < total_chunks; b += gridDim.x)
+        rough2_f32_item(jobs, n_jobs, chunk_base, part, part2, sync, b, sh);
 }
 
 // ===========================================================================
@@ -1573,9 +1666,10 @@ cudaError_t launch_roughness_one(int precision, const RoughJob& jb, char* d_ws, 
     const int chunks = (int)((jb.n + kChunk - 1) / kChunk);
     RoughJob* d_job = (RoughJob*)d_ws;
     int* d_base = (int*)(d_ws + 256);
+    void* d_sync = d_ws + 320;  // rough_sync_bytes(1) = 16
     double* d_part = (double*)(d_ws + 512);
     rough_setup_one_kernel<<<1, 32, 0, st>>>(jb, chunks, d_job, d_base);
-    return launch_roughness_jobs(precision, d_job, 1, d_base, chunks, jb.n_rows + jb.n_cols, d_part, st);
+    return launch_roughness_jobs(precision, d_job, 1, d_base, chunks, jb.n_rows + jb.n_cols, d_part, d_sync, st);
 }
 
 size_t roughness_one_ws_bytes(size_t n) {
@@ -1583,20 +1677,31 @@ size_t roughness_one_ws_bytes(size_t n) {
     return 512 + 7 * sizeof(double) * chunks;
 }
 
+size_t rough_sync_bytes(int n_jobs) { return ((8 * (size_t)n_jobs + 7) & ~(size_t)7) + 8 * (size_t)n_jobs; }
+
 cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_jobs, const int* d_chunk_base,
-                                  int total_chunks, int max_profiles, double* d_part, cudaStream_t st) {
+                                  int total_chunks, int max_profiles, double* d_part, void* d_sync,
+                                  cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
     double* part2 = d_part + 3 * (size_t)total_chunks;
+    cudaError_t e = cudaMemsetAsync(d_sync, 0, rough_sync_bytes(n_jobs), st);
+    if (e != cudaSuccess) return e;
+    // pass 1 (+ the profiles as extra blocks; each job's last block stores
+    // the mean), pass 2 (+ the final combine in each job's last block)
+    const int items1 = total_chunks + n_jobs * max_profiles;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int g1 = std::min(items1, 4 * sms), g2 = std::min(total_chunks, 8 * sms);
     if (precision == 0) {
-        rough1_kernel<double><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part);
-        rough2_kernel<double><<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
-        if (max_profiles > 0) profiles_kernel<double><<<n_jobs * max_profiles, 256, 0, st>>>(d_jobs, max_profiles);
+        rough1_kernel<double><<<g1, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, total_chunks, max_profiles,
+                                                 d_sync, items1);
+        rough2_kernel<double><<<g2, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2, d_sync, total_chunks);
     } else {
-        rough1_f32_kernel<<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part);
-        rough2_f32_kernel<<<total_chunks, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2);
-        if (max_profiles > 0) profiles_kernel<float><<<n_jobs * max_profiles, 256, 0, st>>>(d_jobs, max_profiles);
+        rough1_f32_kernel<<<g1, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, total_chunks, max_profiles,
+                                             d_sync, items1);
+        rough2_f32_kernel<<<g2, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2, d_sync, total_chunks);
     }
-    rough3_kernel<<<n_jobs, 256, 0, st>>>(d_jobs, d_chunk_base, d_part, part2);
     return cudaGetLastError();
 }
 
