@@ -165,7 +165,9 @@ typedef struct {
  *   block_threads     threads per CTA, a multiple of 32 in 64..512 (0 = default)
  *   ctas_per_sm       cap on resident CTAs per SM (0 = as many as fit)
  *   d_counters        NULL, or device int64_t[4] the sweep ADDS to:
- *                     [0] edge-point poses evaluated,
+ *                     [0] edge-point poses evaluated (the FP32 sweep's
+ *                         phase form skips revolutions that cannot reach a
+ *                         tile, so this count depends on the form used),
  *                     [1] cutting evaluations: inside the patch and below the
  *                         stock surface (the points the per-cell minimum runs
  *                         over); exact in FP64, within ~1e-5 relative in FP32
