@@ -29,7 +29,7 @@ struct BatchLayout {
     size_t off_surf = 0, off_tb64 = 0, off_tb32 = 0, off_queue = 0, off_jobs = 0, off_cb64 = 0,
            off_cb32 = 0, off_part64 = 0, off_part32 = 0, off_tables = 0, total = 0;
     bool rough = false;
-    bool phase_form32 = false;  // some FP32 surface's runs come back for many revolutions
+    bool phase_form32 = false, phase_form64 = false;  // some surface's runs come back for many revolutions
     long long* counters = nullptr;
     void* events[2] = {nullptr, nullptr};
     std::vector<char> blob;  // host image of [off_surf, off_tables)
@@ -59,9 +59,11 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     if (L->n64 && (rc = sweep_config(ctx, FSM_FP64, L->sh64, &L->smem64, &L->bps64)) != FSM_OK) return rc;
     if (L->n32 && (rc = sweep_config(ctx, FSM_FP32, L->sh32, &L->smem32, &L->bps32)) != FSM_OK) return rc;
     L->rough = d_rough != nullptr;
-    for (int i = 0; i < n; ++i)
-        if (procs[i]->precision == FSM_FP32 && phase_form_pays(*tools[i], *procs[i], L->sh32.tile_x))
-            L->phase_form32 = true;
+    for (int i = 0; i < n; ++i) {
+        const bool f64 = procs[i]->precision == FSM_FP64;
+        if (phase_form_pays(*tools[i], *procs[i], f64 ? L->sh64.tile_x : L->sh32.tile_x))
+            (f64 ? L->phase_form64 : L->phase_form32) = true;
+    }
     L->counters = opts ? (long long*)opts->d_counters : nullptr;
     if (opts) {
         L->events[0] = opts->sweep_events[0];
@@ -153,7 +155,7 @@ fsm_status run_batch(fsm_ctx* ctx, const BatchLayout& L, char* base, cudaStream_
     if (L.n64) {
         const int grid = std::min(L.tiles64, ctx->sm_count * L.bps64);
         e = launch_sweep_shaped(FSM_FP64, d_surf, L.n64, (const int*)(base + L.off_tb64), L.tiles64, q, L.counters,
-                                grid, L.sh64.threads, L.smem64, st, false);
+                                grid, L.sh64.threads, L.smem64, st, L.phase_form64);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel (FP64)");
     }
     if (L.n32) {

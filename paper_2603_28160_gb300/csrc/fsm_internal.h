@@ -16,17 +16,22 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
 size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads);
 int sweep_blocks_per_sm(int precision, int threads, size_t smem);
 cudaError_t sweep_allow_smem(size_t max_bytes);
-// phase_form: FP32 surfaces whose runs come back for many revolutions share
-// per-phase work (see phase_form_pays); the FP64 sweep ignores it.
+// phase_form: surfaces whose runs come back for many revolutions share
+// per-phase work (see phase_form_pays).
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,
                                 cudaStream_t st, bool phase_form);
 
-// True when a tile is at least three feeds per revolution wide: the runs of
-// one tile then come back for several revolutions.
+// True when a tile is several feeds per revolution wide, so that the runs of
+// one tile come back for several revolutions: three for the FP32 sweep, one
+// and a half for the FP64 sweep, whose per-item work is dearer (measured on
+// GB300: the ball raster, under one feed per tile, is faster item by item in
+// both; the side wall and the flat-end floor, at two to four, faster by phase:
+// FP64 wall 73.7 -> 15.5 ms, floor 257 -> 208 ms).
 inline bool phase_form_pays(const fsm_tool_desc& t, const fsm_process_desc& p, int tile_x) {
-    return (double)tile_x * p.pitch >= 3.0 * (double)t.n_teeth * p.fz;
+    const double feeds = (double)tile_x * p.pitch / ((double)t.n_teeth * p.fz);
+    return feeds >= (p.precision == FSM_FP64 ? 1.5 : 3.0);
 }
 
 // Trajectory map of one planned surface: argmin table d_jmin (S * n_teeth

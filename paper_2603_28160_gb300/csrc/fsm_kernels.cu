@@ -891,6 +891,71 @@ __device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<un
     }
 }
 
+// FP64 phase form: every lane takes a spindle phase of the run; height and
+// y cell are computed once per phase and only the revolutions whose x can be
+// within a cell of the tile are visited. Each visit computes the pose with
+// the same FP64 operations as the item form (x from the exact path position
+// of its step), so both forms give the same map.
+__device__ __forceinline__ void sweep_phases64(const Surface& sf, const TileCtx<unsigned long long>& tc, int K,
+                                               int g, int p, WarpScratch& ws, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const int E = sf.E, NE = sf.n_teeth * E;
+    const double yc = path_y(sf, p);
+    const double inv_pitch = sf.inv_pitch;
+    const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock;
+    const int S = sf.S;
+    const int s0 = p * sf.steps_per_pass;
+    const long long ib = (long long)tc.tx * sf.tile_x, kb_t = (long long)tc.ty * sf.tile_y;
+    const double2* __restrict__ ph64 = sf.ph64;
+    const int tile_x = sf.tile_x;
+    unsigned long long* cells = tc.cells;
+    const int txc = tc.txc, tyc = tc.tyc;
+    const double xlo = tc.X0 - sf.pitch, xhi = tc.X0 + (double)(txc + 1) * sf.pitch;
+    const double rev = (pass_reversed(sf, p) ? -(double)S : (double)S) * sf.fs;  // x shift per revolution
+    const double inv_rev = 1.0 / rev;
+    for (int o = 0; o < 32; ++o) {
+        const int nr = ws.n[o];
+        if (nr == 0) continue;
+        const int idx = K * E + g * 32 + o;
+        const Vec9 v = load_vec9(sf.tool64, NE, idx);
+        for (int a = 0; a < nr; ++a) {
+            const RunRec r = ws.run[o][a];
+            const int f0 = r.first_off, f1 = r.first_off + r.len0;
+            for (int off = lane; off < r.len; off += 32) {
+                int32_t m = r.m0 + off;
+                m = m >= S ? m - S : m;
+                const double2 cs = __ldg(ph64 + m);
+                const int kb = (off >= f0 && off < f1) ? 0 : 1;
+                const int ke = r.k_last == 0 ? 0 : (off < r.len_last ? r.k_last : r.k_last - 1);
+                const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
+                if (!(z < stock) || ke < kb) continue;
+                const double y = __dadd_rn(yc, __fma_rn(cs.x, v.uy, __fma_rn(cs.y, v.vy, v.wy)));
+                const long long kg = bin64(y, y0, inv_pitch) - kb_t;
+                if (kg < 0 || kg >= tyc) continue;
+                const double px = __fma_rn(cs.x, v.ux, __fma_rn(cs.y, v.vx, v.wx));
+                const double xk0 = path_x(sf, p, r.occ0 + off - s0) + px;  // approximate: only bounds k
+                const double ka = (xlo - xk0) * inv_rev, kz = (xhi - xk0) * inv_rev;
+                const int k0 = max(kb, (int)floor(fmin(ka, kz)) - 1);
+                const int k1 = min(ke, (int)ceil(fmax(ka, kz)) + 1);
+                const unsigned long long e = enc64((unsigned long long)__double_as_longlong(z));
+                unsigned long long* row = cells + (int)kg * tile_x;
+                for (int k = k0; k <= k1; ++k) {
+                    const int32_t s = r.occ0 + k * S + off;
+                    const double x = __dadd_rn(path_x(sf, p, s - s0), px);
+                    ++cnt.evaluated;
+                    const long long ig = bin64(x, x0, inv_pitch) - ib;
+                    if (ig < 0 || ig >= txc) continue;
+                    ++cnt.cutting;
+                    if (e < row[ig]) {
+                        atomicMin(row + ig, e);
+                        ++cnt.atomics;
+                    }
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -969,7 +1034,8 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             float2 pt;
             if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4, pt)) continue;
             if constexpr (FP64) {
-                sweep_task64(sf, tc, K, g, p, ws, cnt);
+                if constexpr (kPhases) sweep_phases64(sf, tc, K, g, p, ws, cnt);
+                else sweep_task64(sf, tc, K, g, p, ws, cnt);
             } else {
                 float yl2, yh2, dyp;
                 pass_band(sf, tc, ts, p, &yl2, &yh2, &dyp);
@@ -1589,7 +1655,14 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
                                 cudaStream_t st, bool phase_form) {
     // counting and the FP32 phase form are separate instantiations: without
     // them the counters are dead code and the item loop has the SM to itself
-    if (precision == 0) {
+    if (precision == 0 && phase_form) {
+        if (d_counters)
+            sweep_kernel<true, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
+                                                                        d_queue, d_counters);
+        else
+            sweep_kernel<true, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                         total_tiles, d_queue, nullptr);
+    } else if (precision == 0) {
         if (d_counters)
             sweep_kernel<true, true, false><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
                                                                          d_queue, d_counters);
@@ -1629,6 +1702,8 @@ cudaError_t sweep_allow_smem(size_t max_bytes) {
     cudaError_t e;
     if ((e = allow_dynamic_smem(sweep_kernel<true, true, false>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<true, false, false>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, true, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, false, true>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, true, false>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, false, false>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, true, true>, max_bytes)) != cudaSuccess) return e;
@@ -1644,6 +1719,8 @@ int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
     if (precision == 0) {
         e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<true, true, false>, threads, smem);
         e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<true, false, false>, threads, smem);
+        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, sweep_kernel<true, true, true>, threads, smem);
+        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, sweep_kernel<true, false, true>, threads, smem);
     } else {
         e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<false, true, false>, threads, smem);
         e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<false, false, false>, threads, smem);
