@@ -623,26 +623,25 @@ __device__ __noinline__ bool ambiguous_may_lower(const uint32_t* cells, int tile
     return false;
 }
 
-// Item t of a run, without branches (both halves of a warp may be on runs of
-// different shapes): first occurrence if t < len0, later ones otherwise.
-__device__ __forceinline__ void rec_item_sel(const RunRec& r, int32_t S, float inv_len, int32_t t, int32_t* s,
-                                             int32_t* m) {
-    const int32_t tt = t - r.len0;
-    int32_t q = __float2int_rz((float)max(tt, 0) * inv_len);
-    q += ((q + 1) * r.len <= tt) ? 1 : 0;
-    q -= (q * r.len > tt) ? 1 : 0;
-    const bool first = tt < 0;
-    const int32_t k = first ? 0 : 1 + q;
-    const int32_t off = first ? r.first_off + t : tt - q * r.len;
-    *s = r.occ0 + k * S + off;
-    const int32_t mm = r.m0 + off;
-    *m = mm >= S ? mm - S : mm;
+// q = v / len and r = v mod len for 0 <= v < 2^24, from a float reciprocal of
+// len with one correction step (the estimate is off by at most one).
+__device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_len, int32_t* q, int32_t* r) {
+    int32_t d = __float2int_rz((float)v * inv_len);
+    d += ((d + 1) * len <= v) ? 1 : 0;
+    d -= (d * len > v) ? 1 : 0;
+    *q = d;
+    *r = v - d * len;
 }
 
 // Phase 2 (FP32), item form for runs of few revolutions: the task's runs are
-// taken two at a time, one per half-warp; each lane evaluates two items of
-// its half's run per iteration, written as two interleaved, mostly
-// predicated chains.
+// taken two at a time, one per half-warp; each lane evaluates items hl and
+// hl + 16 of every 32 of its half's run, written as two interleaved, mostly
+// predicated chains. Counted from phase 0 of the first occurrence
+// (v = t + first_off; the first occurrence is complete up to the window's
+// end whenever there is a second one), item t lies in revolution q = v / len
+// at phase offset v mod len, q (S - len) + t steps after the run's first
+// item; the lane advances (q, offset) by 32 items per iteration without a
+// division.
 __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
                                              int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
                                              Counters& cnt) {
@@ -668,7 +667,6 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
             r.m0 = 0; r.len = 1; r.occ0 = 0; r.first_off = 0; r.len0 = 1; r.k_last = 0; r.len_last = 0;
             r.dxA = 0.f; r.g_cells = 0.f;
         }
-        const float inv_len = 1.0f / (float)r.len;
         const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
         const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
         const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
@@ -680,19 +678,31 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
         const float hg = 0.5f - gc;
+        const int32_t len = r.len, gap = S - len;
+        const float inv_len = 1.0f / (float)len;
+        int32_t d32, r32, d16, r16, qa, oa;  // 32 and 16 items in (revolutions, phases); item hl
+        divmod_small(32, len, inv_len, &d32, &r32);
+        divmod_small(16, len, inv_len, &d16, &r16);
+        divmod_small(hl + r.first_off, len, inv_len, &qa, &oa);
         for (int base = 0; base < tmax; base += 32) {
-            const int ta = base + hl, tb = base + 16 + hl;
+            const int ta = base + hl, tb = ta + 16;
             const bool va = ta < tot, vb = tb < tot;
-            int32_t sa, ma, sb, mb;
-            rec_item_sel(r, S, inv_len, va ? ta : 0, &sa, &ma);
-            rec_item_sel(r, S, inv_len, vb ? tb : 0, &sb, &mb);
+            int32_t ob = oa + r16, qb = qa + d16;
+            if (ob >= len) { ob -= len; ++qb; }
+            const int32_t dsa = ta + qa * gap, dsb = tb + qb * gap;  // steps after the run's first item
+            int32_t ma = r.m0 + oa, mb = r.m0 + ob;
+            ma = ma >= S ? ma - S : ma;
+            mb = mb >= S ? mb - S : mb;
+            oa += r32;
+            qa += d32;
+            if (oa >= len) { oa -= len; ++qa; }
             const float2 ca = __ldg(ph32 + ma);
             const float2 cb = __ldg(ph32 + mb);
             cnt.evaluated += (unsigned)va + (unsigned)vb;
             const float za = fmaf(ca.x, uz, fmaf(ca.y, vz, zb));
             const float zb2 = fmaf(cb.x, uz, fmaf(cb.y, vz, zb));
-            const float xa = fmaf((float)(sa - sA), fs32, r.dxA) + fmaf(ca.x, ux, fmaf(ca.y, vx, wx));
-            const float xb = fmaf((float)(sb - sA), fs32, r.dxA) + fmaf(cb.x, ux, fmaf(cb.y, vx, wx));
+            const float xa = fmaf((float)dsa, fs32, r.dxA) + fmaf(ca.x, ux, fmaf(ca.y, vx, wx));
+            const float xb = fmaf((float)dsb, fs32, r.dxA) + fmaf(cb.x, ux, fmaf(cb.y, vx, wx));
             const float ya = dyp + fmaf(ca.x, uy, fmaf(ca.y, vy, wy));
             const float yb = dyp + fmaf(cb.x, uy, fmaf(cb.y, vy, wy));
             const float fxa = xa * inv_pitch, fya = ya * inv_pitch, fxb = xb * inv_pitch, fyb = yb * inv_pitch;
@@ -725,8 +735,8 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
             if (cut_b && amb_b)
                 wb = ambiguous_may_lower(cells, tile_x, txc, tyc, ib, kb, rxb, ryb, gc, zb2, eps_z);
             if (__any_sync(0xffffffffu, wa || wb)) {
-                rebin_push(sf, tc, ws, p, wa, sa, ma, idx, qn, cnt);
-                rebin_push(sf, tc, ws, p, wb, sb, mb, idx, qn, cnt);
+                rebin_push(sf, tc, ws, p, wa, sA + dsa, ma, idx, qn, cnt);
+                rebin_push(sf, tc, ws, p, wb, sA + dsb, mb, idx, qn, cnt);
             }
         }
     }
