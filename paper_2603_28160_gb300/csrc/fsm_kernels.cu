@@ -634,19 +634,23 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
 }
 
 // Phase 2 (FP32), item form for runs of few revolutions: the task's runs are
-// taken two at a time, one per half-warp; each lane evaluates items hl and
-// hl + 16 of every 32 of its half's run, written as two interleaved, mostly
-// predicated chains. Counted from phase 0 of the first occurrence
+// taken four at a time, one per group of L = 8 lanes; each lane evaluates
+// items hl and hl + L of every 2L of its group's run, written as two
+// interleaved, mostly predicated chains (the runs average ~70 items, so
+// narrower groups waste fewer slots at run ends and share the per-run
+// shuffles among more runs). Counted from phase 0 of the first occurrence
 // (v = t + first_off; the first occurrence is complete up to the window's
 // end whenever there is a second one), item t lies in revolution q = v / len
 // at phase offset v mod len, q (S - len) + t steps after the run's first
-// item; the lane advances (q, offset) by 32 items per iteration without a
+// item; the lane advances (q, offset) by 2L items per iteration without a
 // division.
+constexpr int kItemLanes = 8;
 __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
                                              int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
                                              Counters& cnt) {
+    constexpr int L = kItemLanes;
     const int lane = threadIdx.x & 31;
-    const int hl = lane & 15, half = lane >> 4;
+    const int hl = lane & (L - 1), grp = lane / L;
     const int S = sf.S;
     const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
     const float inv_pitch = sf.inv_pitch_f;
@@ -657,8 +661,8 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
-    for (int q = 0; q < R; q += 2) {
-        const int ri = q + half;
+    for (int q = 0; q < R; q += 32 / L) {
+        const int ri = q + grp;
         const bool has = ri < R;
         const int code = has ? (int)ws.flat[ri] : 0;
         const int o = code >> 2, a = code & 3;
@@ -674,27 +678,28 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
         const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
         const int idx = K * sf.E + g * 32 + o;
         const int tot = has ? rec_total(r) : 0;
-        const int tmax = max(tot, __shfl_xor_sync(0xffffffffu, tot, 16));
+        int tmax = tot;
+        for (int o2 = L; o2 < 32; o2 <<= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o2));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
         const float hg = 0.5f - gc;
         const int32_t len = r.len, gap = S - len;
         const float inv_len = 1.0f / (float)len;
-        int32_t d32, r32, d16, r16, qa, oa;  // 32 and 16 items in (revolutions, phases); item hl
-        divmod_small(32, len, inv_len, &d32, &r32);
-        divmod_small(16, len, inv_len, &d16, &r16);
+        int32_t d2l, r2l, dl, rl, qa, oa;  // 2L and L items in (revolutions, phases); item hl
+        divmod_small(2 * L, len, inv_len, &d2l, &r2l);
+        divmod_small(L, len, inv_len, &dl, &rl);
         divmod_small(hl + r.first_off, len, inv_len, &qa, &oa);
-        for (int base = 0; base < tmax; base += 32) {
-            const int ta = base + hl, tb = ta + 16;
+        for (int base = 0; base < tmax; base += 2 * L) {
+            const int ta = base + hl, tb = ta + L;
             const bool va = ta < tot, vb = tb < tot;
-            int32_t ob = oa + r16, qb = qa + d16;
+            int32_t ob = oa + rl, qb = qa + dl;
             if (ob >= len) { ob -= len; ++qb; }
             const int32_t dsa = ta + qa * gap, dsb = tb + qb * gap;  // steps after the run's first item
             int32_t ma = r.m0 + oa, mb = r.m0 + ob;
             ma = ma >= S ? ma - S : ma;
             mb = mb >= S ? mb - S : mb;
-            oa += r32;
-            qa += d32;
+            oa += r2l;
+            qa += d2l;
             if (oa >= len) { oa -= len; ++qa; }
             const float2 ca = __ldg(ph32 + ma);
             const float2 cb = __ldg(ph32 + mb);
