@@ -749,8 +749,8 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
 }
 
 // Phase 2 (FP32), phase form for runs of many revolutions. The task's runs
-// are taken two at a time, one per half-warp, and every lane takes phase
-// offsets of its run. Height, y cell
+// are taken four at a time, one per group of L = 8 lanes, and every lane
+// takes phase offsets of its run. Height, y cell
 // and the point's x offset depend on the spindle phase alone, so they are
 // computed once per offset; the revolutions in which that phase lies inside
 // the run's step window differ only by a shift of S fs in x, and the ones
@@ -761,7 +761,8 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
                                                int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
                                                Counters& cnt) {
     const int lane = threadIdx.x & 31;
-    const int hl = lane & 15, half = lane >> 4;
+    constexpr int L = kItemLanes;
+    const int hl = lane & (L - 1), grp = lane / L;
     const int S = sf.S;
     const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
     const float inv_pitch = sf.inv_pitch_f;
@@ -777,8 +778,8 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
-    for (int q = 0; q < R; q += 2) {
-        const int ri = q + half;
+    for (int q = 0; q < R; q += 32 / L) {
+        const int ri = q + grp;
         const bool has = ri < R;
         const int code = has ? (int)ws.flat[ri] : 0;
         const int o = code >> 2, a = code & 3;
@@ -794,12 +795,13 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
         const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
         const int idx = K * sf.E + g * 32 + o;
-        const int lmax = max(len, __shfl_xor_sync(0xffffffffu, len, 16));
+        int lmax = len;
+        for (int o2 = L; o2 < 32; o2 <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
         const float hg = 0.5f - gc;
         const int f0 = r.first_off, f1 = r.first_off + r.len0;
-        for (int ob = 0; ob < lmax; ob += 16) {
+        for (int ob = 0; ob < lmax; ob += L) {
             const int off = ob + hl;
             const bool vo = off < len;
             const int offc = vo ? off : 0;
