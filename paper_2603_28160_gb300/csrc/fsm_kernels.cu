@@ -612,15 +612,97 @@ __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint
     }
 }
 
-__device__ __noinline__ bool ambiguous_may_lower(const uint32_t* cells, int tile_x, int txc, int tyc, int i, int k,
-                                                 float rx, float ry, float g, float z, float eps_z) {
-    const int i0 = max(rx < g ? i - 1 : i, 0), i1 = min(rx > 1.f - g ? i + 1 : i, txc - 1);
-    const int k0 = max(ry < g ? k - 1 : k, 0), k1 = min(ry > 1.f - g ? k + 1 : k, tyc - 1);
-    const uint32_t elo = enc32(__float_as_uint(z - eps_z));
-    for (int kk = k0; kk <= k1; ++kk)
-        for (int ii = i0; ii <= i1; ++ii)
-            if (elo < cells[kk * tile_x + ii]) return true;
-    return false;
+// Ambiguous FP32 points (within the guard band of a cell boundary) wait in a
+// per-warp queue and are checked 32 at a time against the cells they may
+// belong to: their own and the neighbours across the near boundaries,
+// clamped to the tile. Those whose height, lowered by the FP32 error bound,
+// is below one of them go on to FP64 re-binning. Cell values only decrease,
+// so a check made later than the point's evaluation skips no point that
+// could still lower a cell.
+constexpr int kAmbCap = 64;
+struct AmbQueue {
+    uint32_t ik[kAmbCap];   // (i + 1) | (k + 1) << 16: tile-local cell of the FP32 pose
+    uint32_t mdd[kAmbCap];  // phase index | (dx + 1) << 28 | (dy + 1) << 30: the near boundaries
+    uint32_t elo[kAmbCap];  // encoding of z - eps_z
+    int32_t s[kAmbCap], idx[kAmbCap];
+};
+
+// Queue this lane's point if `want` (warp-cooperative; i in [-1, txc] and
+// k in [-1, tyc], the cells that can have a neighbour in the tile).
+__device__ __forceinline__ void amb_push(AmbQueue& aq, bool want, int i, int k, float rx, float ry, float g,
+                                         float z, float eps_z, int32_t s, int32_t m, int idx, int& an) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (want) {
+        const int pos = an + __popc(bal & ((1u << lane) - 1u));
+        const int dx = rx < g ? -1 : (rx > 1.f - g ? 1 : 0);
+        const int dy = ry < g ? -1 : (ry > 1.f - g ? 1 : 0);
+        aq.ik[pos] = (uint32_t)(i + 1) | ((uint32_t)(k + 1) << 16);
+        aq.mdd[pos] = (uint32_t)m | ((uint32_t)(dx + 1) << 28) | ((uint32_t)(dy + 1) << 30);
+        aq.elo[pos] = enc32(__float_as_uint(z - eps_z));
+        aq.s[pos] = s;
+        aq.idx[pos] = idx;
+    }
+    an += __popc(bal);
+    __syncwarp();
+}
+
+// Check the first min(count, 32) queued points (one per lane), move the rest
+// down, and queue the ones that may lower a cell for FP64 re-binning.
+__device__ __forceinline__ void amb_flush(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws,
+                                          AmbQueue& aq, int p, int count, int& qn, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    bool w = false;
+    int32_t s = 0, m = 0, idx = 0;
+    if (lane < count) {
+        const uint32_t ik = aq.ik[lane], mdd = aq.mdd[lane], elo = aq.elo[lane];
+        s = aq.s[lane];
+        idx = aq.idx[lane];
+        m = (int32_t)(mdd & 0x0FFFFFFFu);
+        const int i = (int)(ik & 0xFFFFu) - 1, k = (int)(ik >> 16) - 1;
+        const int dx = (int)((mdd >> 28) & 3u) - 1, dy = (int)(mdd >> 30) - 1;
+        const int i0 = max(min(i, i + dx), 0), i1 = min(max(i, i + dx), tc.txc - 1);
+        const int k0 = max(min(k, k + dy), 0), k1 = min(max(k, k + dy), tc.tyc - 1);
+        for (int kk = k0; kk <= k1; ++kk)
+            for (int ii = i0; ii <= i1; ++ii) w |= elo < tc.cells[kk * sf.tile_x + ii];
+    }
+    __syncwarp();
+    const int rest = count > 32 ? count - 32 : 0;
+    uint32_t t_ik = 0, t_mdd = 0, t_elo = 0;
+    int32_t t_s = 0, t_idx = 0;
+    if (lane < rest) {
+        t_ik = aq.ik[32 + lane];
+        t_mdd = aq.mdd[32 + lane];
+        t_elo = aq.elo[32 + lane];
+        t_s = aq.s[32 + lane];
+        t_idx = aq.idx[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+        aq.ik[lane] = t_ik;
+        aq.mdd[lane] = t_mdd;
+        aq.elo[lane] = t_elo;
+        aq.s[lane] = t_s;
+        aq.idx[lane] = t_idx;
+    }
+    __syncwarp();
+    rebin_push(sf, tc, ws, p, w, s, m, idx, qn, cnt);
+}
+
+// Per-warp scratch in front of the tile cells (precision 0 = FP64, else FP32).
+__host__ __device__ constexpr size_t sweep_scratch_bytes(int precision, int threads) {
+    return (sizeof(WarpScratch) + (precision == 0 ? 0 : sizeof(AmbQueue))) * (size_t)(threads / 32);
+}
+
+// Drain both queues at the end of a task.
+__device__ __forceinline__ void amb_drain(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws,
+                                          AmbQueue& aq, int p, int an, int& qn, Counters& cnt) {
+    while (an > 0) {
+        amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
+        an = an > 32 ? an - 32 : 0;
+    }
+    if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
+    qn = 0;
 }
 
 // q = v / len and r = v mod len for 0 <= v < 2^24, from a float reciprocal of
@@ -646,8 +728,8 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
 // division.
 constexpr int kItemLanes = 8;
 __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
-                                             int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
-                                             Counters& cnt) {
+                                             int g, int p, WarpScratch& ws, AmbQueue& aq, const float4 (&t4)[3],
+                                             float2 pt, Counters& cnt) {
     constexpr int L = kItemLanes;
     const int lane = threadIdx.x & 31;
     const int hl = lane & (L - 1), grp = lane / L;
@@ -661,6 +743,7 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
+    int an = 0;  // queued ambiguous points (warp-uniform)
     for (int q = 0; q < R; q += 32 / L) {
         const int ri = q + grp;
         const bool has = ri < R;
@@ -734,18 +817,23 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
                 atomicMin(cells + cib, eb);
                 ++cnt.atomics;
             }
-            bool wa = false, wb = false;
-            if (cut_a && amb_a)
-                wa = ambiguous_may_lower(cells, tile_x, txc, tyc, ia, ka, rxa, rya, gc, za, eps_z);
-            if (cut_b && amb_b)
-                wb = ambiguous_may_lower(cells, tile_x, txc, tyc, ib, kb, rxb, ryb, gc, zb2, eps_z);
-            if (__any_sync(0xffffffffu, wa || wb)) {
-                rebin_push(sf, tc, ws, p, wa, sA + dsa, ma, idx, qn, cnt);
-                rebin_push(sf, tc, ws, p, wb, sA + dsb, mb, idx, qn, cnt);
+            const bool pa = cut_a && amb_a && ia >= -1 && ia <= txc && ka >= -1 && ka <= tyc;
+            const bool pb = cut_b && amb_b && ib >= -1 && ib <= txc && kb >= -1 && kb <= tyc;
+            if (__any_sync(0xffffffffu, pa || pb)) {
+                amb_push(aq, pa, ia, ka, rxa, rya, gc, za, eps_z, sA + dsa, ma, idx, an);
+                if (an >= 32) {
+                    amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
+                    an -= 32;
+                }
+                amb_push(aq, pb, ib, kb, rxb, ryb, gc, zb2, eps_z, sA + dsb, mb, idx, an);
+                if (an >= 32) {
+                    amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
+                    an -= 32;
+                }
             }
         }
     }
-    if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
+    amb_drain(sf, tc, ws, aq, p, an, qn, cnt);
 }
 
 // Phase 2 (FP32), phase form for runs of many revolutions. The task's runs
@@ -758,8 +846,8 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
 // form and visited. Each visit evaluates exactly as a single item would
 // (the same FP32 pose, binning, guard band and FP64 re-binning).
 __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
-                                               int g, int p, WarpScratch& ws, const float4 (&t4)[3], float2 pt,
-                                               Counters& cnt) {
+                                               int g, int p, WarpScratch& ws, AmbQueue& aq,
+                                               const float4 (&t4)[3], float2 pt, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     constexpr int L = kItemLanes;
     const int hl = lane & (L - 1), grp = lane / L;
@@ -778,6 +866,7 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
+    int an = 0;  // queued ambiguous points (warp-uniform)
     for (int q = 0; q < R; q += 32 / L) {
         const int ri = q + grp;
         const bool has = ri < R;
@@ -850,13 +939,18 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
                     atomicMin(cells + ci, e);
                     ++cnt.atomics;
                 }
-                bool w = false;
-                if (v && amb) w = ambiguous_may_lower(cells, tile_x, txc, tyc, ix, ky, rx, ry, gc, z, eps_z);
-                if (__any_sync(0xffffffffu, w)) rebin_push(sf, tc, ws, p, w, s, m, idx, qn, cnt);
+                const bool pw = v && amb && ix >= -1 && ix <= txc;  // (v: ky in [-1, tyc])
+                if (__any_sync(0xffffffffu, pw)) {
+                    amb_push(aq, pw, ix, ky, rx, ry, gc, z, eps_z, s, m, idx, an);
+                    if (an >= 32) {
+                        amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
+                        an -= 32;
+                    }
+                }
             }
         }
     }
-    if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
+    amb_drain(sf, tc, ws, aq, p, an, qn, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -996,8 +1090,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
     __shared__ TileShared ts;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
+    // [WarpScratch x warps][AmbQueue x warps, FP32 only][tile cells]
     WarpScratch* wscr = reinterpret_cast<WarpScratch*>(smem);
-    Cell* cells = reinterpret_cast<Cell*>(smem + sizeof(WarpScratch) * nwarps);
+    AmbQueue* aqs = reinterpret_cast<AmbQueue*>(smem + sizeof(WarpScratch) * nwarps);
+    Cell* cells = reinterpret_cast<Cell*>(smem + sweep_scratch_bytes(FP64 ? 0 : 1, nwarps * 32));
     WarpScratch& ws = wscr[warp];
     Counters cnt = {0, 0, 0, 0};
 
@@ -1059,7 +1155,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                 // runs that come back for many revolutions share their per-phase
                 // work (phase form); others are walked item by item
                 if constexpr (!kPhases) {
-                    sweep_items32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
+                    sweep_items32(sf, tc, dyp, K, g, p, ws, aqs[warp], t4, pt, cnt);
                     __syncwarp();
                     continue;
                 }
@@ -1073,9 +1169,9 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                     phases += __shfl_xor_sync(0xffffffffu, phases, o);
                 }
                 if (tot >= kPhaseFormRevs * phases)
-                    sweep_phases32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
+                    sweep_phases32(sf, tc, dyp, K, g, p, ws, aqs[warp], t4, pt, cnt);
                 else
-                    sweep_items32(sf, tc, dyp, K, g, p, ws, t4, pt, cnt);
+                    sweep_items32(sf, tc, dyp, K, g, p, ws, aqs[warp], t4, pt, cnt);
             }
             __syncwarp();
         }
@@ -1663,7 +1759,7 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_
 
 size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads) {
     const size_t cell = precision == 0 ? 8 : 4;
-    return sizeof(WarpScratch) * (size_t)(threads / 32) + cell * (size_t)tile_x * (size_t)tile_y;
+    return sweep_scratch_bytes(precision, threads) + cell * (size_t)tile_x * (size_t)tile_y;
 }
 
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
