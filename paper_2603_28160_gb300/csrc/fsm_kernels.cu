@@ -425,7 +425,8 @@ __device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCt
 }
 
 // y band of pass p relative to the pass line, and the pass line relative to the tile
-__device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<uint32_t>& tc, const TileShared& ts,
+template <typename Cell>
+__device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<Cell>& tc, const TileShared& ts,
                                           int p, float* ylo, float* yhi, float* dy) {
     if (p < kPassCache) {
         *ylo = ts.ylo[p];
@@ -436,19 +437,6 @@ __device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<uint3
         *ylo = (float)(tc.Y0 - yc) - kMarginMm;
         *yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
         *dy = (float)(yc - tc.Y0);
-    }
-}
-
-template <typename Cell>
-__device__ __forceinline__ void pass_band_any(const Surface& sf, const TileCtx<Cell>& tc, const TileShared& ts,
-                                              int p, float* ylo, float* yhi) {
-    if (p < kPassCache) {
-        *ylo = ts.ylo[p];
-        *yhi = ts.yhi[p];
-    } else {
-        const double yc = path_y(sf, p);
-        *ylo = (float)(tc.Y0 - yc) - kMarginMm;
-        *yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
     }
 }
 
@@ -534,25 +522,37 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
 }
 
 // ---------------------------------------------------------------------------
-// FP32 path: tile-local FP32 poses; points whose FP32 cell is ambiguous and
-// that could lower a cell are re-binned in FP64, 32 at a time.
+// Phase 2: tile-local FP32 poses decide the cell of every point whose FP32
+// position lies farther than the guard band from a cell boundary (the band
+// bounds the FP32 error, so that cell is the one the FP64 pose gives).
+// Ambiguous points are re-binned with the FP64 pose, 32 at a time. FP32 maps
+// take the FP32 height; FP64 maps take the FP64 height, computed with the
+// same operations as the FP64 pose, so an FP64 map equals the one an
+// all-FP64 sweep gives while only the height runs on the FP64 pipe.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool update32(uint32_t* cells, int idx, float zrel) {
-    const uint32_t e = enc32(__float_as_uint(zrel));
-    if (e < cells[idx]) {
-        atomicMin(cells + idx, e);
-        return true;
-    }
-    return false;
+template <bool F64>
+using CellOf = typename std::conditional<F64, unsigned long long, uint32_t>::type;
+
+__device__ __forceinline__ uint32_t cell_key(float zrel) { return enc32(__float_as_uint(zrel)); }
+__device__ __forceinline__ unsigned long long cell_key(double z) {
+    return enc64((unsigned long long)__double_as_longlong(z));
+}
+
+// FP64 height of edge point (u, v, w) at phase (cos, sin): the z row of the
+// FP64 pose.
+__device__ __forceinline__ double height64(double2 cs, double uz, double vz, double wz, double zr) {
+    return __dadd_rn(zr, __fma_rn(cs.x, uz, __fma_rn(cs.y, vz, wz)));
 }
 
 // Re-bin queued points in FP64 (lanes < count take one entry each). Takes
-// the tile by value and returns this lane's (re-binned, atomics) counts, so
-// the caller's counters stay in registers.
-__device__ __noinline__ uint2 rebin_flush(const Surface& sf, uint32_t* cells, int tx, int ty, int txc, int tyc,
+// the tile by value and returns this lane's (re-binned, atomics, cutting)
+// counts, so the caller's counters stay in registers; cutting is counted
+// here for FP64 maps only (FP32 maps count it from the FP32 pose).
+template <bool F64>
+__device__ __noinline__ uint4 rebin_flush(const Surface& sf, CellOf<F64>* cells, int tx, int ty, int txc, int tyc,
                                           WarpScratch& ws, int p, int count) {
     const int lane = threadIdx.x & 31;
-    uint2 c = make_uint2(0u, 0u);
+    uint4 c = make_uint4(0u, 0u, 0u, 0u);
     if (lane < count) {
         const int NE = sf.n_teeth * sf.E;
         const int s = ws.q_s[lane], m = ws.q_m[lane], idx = ws.q_idx[lane];
@@ -562,8 +562,15 @@ __device__ __noinline__ uint2 rebin_flush(const Surface& sf, uint32_t* cells, in
         if (P.z < sf.stock) {
             const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tx * sf.tile_x;
             const long long kg = bin64(P.y, sf.y0, sf.inv_pitch) - (long long)ty * sf.tile_y;
-            if (ig >= 0 && ig < txc && kg >= 0 && kg < tyc)
-                c.y = update32(cells, (int)kg * sf.tile_x + (int)ig, (float)(P.z - sf.stock)) ? 1u : 0u;
+            if (ig >= 0 && ig < txc && kg >= 0 && kg < tyc) {
+                CellOf<F64>* cell = cells + (int)kg * sf.tile_x + (int)ig;
+                const auto e = F64 ? (CellOf<F64>)cell_key(P.z) : (CellOf<F64>)cell_key((float)(P.z - sf.stock));
+                if (e < *cell) {
+                    atomicMin(cell, e);
+                    c.y = 1u;
+                }
+                c.z = F64 ? 1u : 0u;
+            }
         }
     }
     __syncwarp();
@@ -585,16 +592,19 @@ __device__ __noinline__ uint2 rebin_flush(const Surface& sf, uint32_t* cells, in
     return c;
 }
 
-__device__ __forceinline__ void rebin_flush_count(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws,
-                                                  int p, int count, Counters& cnt) {
-    const uint2 c = rebin_flush(sf, tc.cells, tc.tx, tc.ty, tc.txc, tc.tyc, ws, p, count);
+template <bool F64>
+__device__ __forceinline__ void rebin_flush_count(const Surface& sf, const TileCtx<CellOf<F64>>& tc,
+                                                  WarpScratch& ws, int p, int count, Counters& cnt) {
+    const uint4 c = rebin_flush<F64>(sf, tc.cells, tc.tx, tc.ty, tc.txc, tc.tyc, ws, p, count);
     cnt.rebinned += c.x;
     cnt.atomics += c.y;
+    cnt.cutting += c.z;
 }
 
 // Queue this iteration's re-bins (warp-cooperative) and flush full batches.
-__device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws, int p,
-                                           bool want, int32_t s, int32_t m, int idx, int& qn, Counters& cnt) {
+template <bool F64>
+__device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<CellOf<F64>>& tc, WarpScratch& ws,
+                                           int p, bool want, int32_t s, int32_t m, int idx, int& qn, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const unsigned bal = __ballot_sync(0xffffffffu, want);
     if (!bal) return;
@@ -607,18 +617,19 @@ __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<uint
     qn += __popc(bal);
     __syncwarp();
     if (qn >= 32) {
-        rebin_flush_count(sf, tc, ws, p, qn, cnt);
+        rebin_flush_count<F64>(sf, tc, ws, p, qn, cnt);
         qn -= 32;
     }
 }
 
-// Ambiguous FP32 points (within the guard band of a cell boundary) wait in a
-// per-warp queue and are checked 32 at a time against the cells they may
-// belong to: their own and the neighbours across the near boundaries,
-// clamped to the tile. Those whose height, lowered by the FP32 error bound,
-// is below one of them go on to FP64 re-binning. Cell values only decrease,
-// so a check made later than the point's evaluation skips no point that
-// could still lower a cell.
+// Ambiguous points of FP32 maps (within the guard band of a cell boundary)
+// wait in a per-warp queue and are checked 32 at a time against the cells
+// they may belong to: their own and the neighbours across the near
+// boundaries, clamped to the tile. Those whose height, lowered by the FP32
+// error bound, is below one of them go on to FP64 re-binning. Cell values
+// only decrease, so a check made later than the point's evaluation skips no
+// point that could still lower a cell. (FP64 maps re-bin every ambiguous
+// point: their cells hold FP64 heights.)
 constexpr int kAmbCap = 64;
 struct AmbQueue {
     uint32_t ik[kAmbCap];   // (i + 1) | (k + 1) << 16: tile-local cell of the FP32 pose
@@ -686,7 +697,7 @@ __device__ __forceinline__ void amb_flush(const Surface& sf, const TileCtx<uint3
         aq.idx[lane] = t_idx;
     }
     __syncwarp();
-    rebin_push(sf, tc, ws, p, w, s, m, idx, qn, cnt);
+    rebin_push<false>(sf, tc, ws, p, w, s, m, idx, qn, cnt);
 }
 
 // Per-warp scratch in front of the tile cells (precision 0 = FP64, else FP32).
@@ -694,14 +705,35 @@ __host__ __device__ constexpr size_t sweep_scratch_bytes(int precision, int thre
     return (sizeof(WarpScratch) + (precision == 0 ? 0 : sizeof(AmbQueue))) * (size_t)(threads / 32);
 }
 
-// Drain both queues at the end of a task.
-__device__ __forceinline__ void amb_drain(const Surface& sf, const TileCtx<uint32_t>& tc, WarpScratch& ws,
-                                          AmbQueue& aq, int p, int an, int& qn, Counters& cnt) {
-    while (an > 0) {
-        amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
-        an = an > 32 ? an - 32 : 0;
+// An ambiguous point: FP32 maps queue it for the cell check, FP64 maps for
+// re-binning. `an` counts the check queue.
+template <bool F64>
+__device__ __forceinline__ void push_ambiguous(const Surface& sf, const TileCtx<CellOf<F64>>& tc, WarpScratch& ws,
+                                               AmbQueue* aq, int p, bool want, int i, int k, float rx, float ry,
+                                               float g, float z, float eps_z, int32_t s, int32_t m, int idx,
+                                               int& an, int& qn, Counters& cnt) {
+    if constexpr (F64) {
+        rebin_push<true>(sf, tc, ws, p, want, s, m, idx, qn, cnt);
+    } else {
+        amb_push(*aq, want, i, k, rx, ry, g, z, eps_z, s, m, idx, an);
+        if (an >= 32) {
+            amb_flush(sf, tc, ws, *aq, p, an, qn, cnt);
+            an -= 32;
+        }
     }
-    if (qn > 0) rebin_flush_count(sf, tc, ws, p, qn, cnt);
+}
+
+// Drain the queues at the end of a task.
+template <bool F64>
+__device__ __forceinline__ void drain_queues(const Surface& sf, const TileCtx<CellOf<F64>>& tc, WarpScratch& ws,
+                                             AmbQueue* aq, int p, int an, int& qn, Counters& cnt) {
+    if constexpr (!F64) {
+        while (an > 0) {
+            amb_flush(sf, tc, ws, *aq, p, an, qn, cnt);
+            an = an > 32 ? an - 32 : 0;
+        }
+    }
+    if (qn > 0) rebin_flush_count<F64>(sf, tc, ws, p, qn, cnt);
     qn = 0;
 }
 
@@ -715,7 +747,7 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
     *r = v - d * len;
 }
 
-// Phase 2 (FP32), item form for runs of few revolutions: the task's runs are
+// Item form of phase 2, for runs of few revolutions: the task's runs are
 // taken four at a time, one per group of L = 8 lanes; each lane evaluates
 // items hl and hl + L of every 2L of its group's run, written as two
 // interleaved, mostly predicated chains (the runs average ~70 items, so
@@ -727,9 +759,11 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
 // item; the lane advances (q, offset) by 2L items per iteration without a
 // division.
 constexpr int kItemLanes = 8;
-__device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
-                                             int g, int p, WarpScratch& ws, AmbQueue& aq, const float4 (&t4)[3],
-                                             float2 pt, Counters& cnt) {
+template <bool F64>
+__device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
+                                            int g, int p, WarpScratch& ws, AmbQueue* aq, const float4 (&t4)[3],
+                                            float2 pt, Counters& cnt) {
+    using Cell = CellOf<F64>;
     constexpr int L = kItemLanes;
     const int lane = threadIdx.x & 31;
     const int hl = lane & (L - 1), grp = lane / L;
@@ -737,8 +771,11 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
     const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
     const float inv_pitch = sf.inv_pitch_f;
     const float2* __restrict__ ph32 = sf.ph32;
+    const double2* __restrict__ ph64 = sf.ph64;
+    const int NE = sf.n_teeth * sf.E;
+    const double zr = sf.z_ref, stock = sf.stock;
     const int tile_x = sf.tile_x;
-    uint32_t* cells = tc.cells;
+    Cell* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
@@ -760,6 +797,12 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
         const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
         const int idx = K * sf.E + g * 32 + o;
+        double uz64 = 0.0, vz64 = 0.0, wz64 = 0.0;
+        if constexpr (F64) {
+            uz64 = __ldg(sf.tool64 + 2 * NE + idx);
+            vz64 = __ldg(sf.tool64 + 5 * NE + idx);
+            wz64 = __ldg(sf.tool64 + 8 * NE + idx);
+        }
         const int tot = has ? rec_total(r) : 0;
         int tmax = tot;
         for (int o2 = L; o2 < 32; o2 <<= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o2));
@@ -797,18 +840,32 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
             const float lxa = floorf(fxa), lya = floorf(fya), lxb = floorf(fxb), lyb = floorf(fyb);
             const float rxa = fxa - lxa, rya = fya - lya, rxb = fxb - lxb, ryb = fyb - lyb;
             const int ia = (int)lxa, ka = (int)lya, ib = (int)lxb, kb = (int)lyb;
-            const bool cut_a = va && za < 0.f, cut_b = vb && zb2 < 0.f;
+            Cell ea, eb;
+            bool cut_a, cut_b;
+            if constexpr (F64) {  // below the stock by the FP64 height
+                const double za64 = height64(__ldg(ph64 + ma), uz64, vz64, wz64, zr);
+                const double zb64 = height64(__ldg(ph64 + mb), uz64, vz64, wz64, zr);
+                cut_a = va && za64 < stock;
+                cut_b = vb && zb64 < stock;
+                ea = cell_key(za64);
+                eb = cell_key(zb64);
+            } else {
+                cut_a = va && za < 0.f;
+                cut_b = vb && zb2 < 0.f;
+                ea = cell_key(za);
+                eb = cell_key(zb2);
+            }
             const bool in_a = cut_a && (unsigned)ia < (unsigned)txc && (unsigned)ka < (unsigned)tyc;
             const bool in_b = cut_b && (unsigned)ib < (unsigned)txc && (unsigned)kb < (unsigned)tyc;
-            cnt.cutting += (unsigned)in_a + (unsigned)in_b;
             // within gc of a cell boundary: |r - 1/2| > 1/2 - gc on either axis
             const bool amb_a = fmaxf(fabsf(rxa - 0.5f), fabsf(rya - 0.5f)) > hg;
             const bool amb_b = fmaxf(fabsf(rxb - 0.5f), fabsf(ryb - 0.5f)) > hg;
             const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
+            // FP32 maps count the FP32 cell; FP64 maps count ambiguous points when re-binned
+            cnt.cutting += F64 ? (unsigned)upd_a + (unsigned)upd_b : (unsigned)in_a + (unsigned)in_b;
             const int cia = ka * tile_x + ia, cib = kb * tile_x + ib;
-            const uint32_t ea = enc32(__float_as_uint(za)), eb = enc32(__float_as_uint(zb2));
-            const uint32_t cva = upd_a ? cells[cia] : 0u;
-            const uint32_t cvb = upd_b ? cells[cib] : 0u;
+            const Cell cva = upd_a ? cells[cia] : (Cell)0;
+            const Cell cvb = upd_b ? cells[cib] : (Cell)0;
             if (upd_a && ea < cva) {
                 atomicMin(cells + cia, ea);
                 ++cnt.atomics;
@@ -820,34 +877,30 @@ __device__ __forceinline__ void sweep_items32(const Surface& sf, const TileCtx<u
             const bool pa = cut_a && amb_a && ia >= -1 && ia <= txc && ka >= -1 && ka <= tyc;
             const bool pb = cut_b && amb_b && ib >= -1 && ib <= txc && kb >= -1 && kb <= tyc;
             if (__any_sync(0xffffffffu, pa || pb)) {
-                amb_push(aq, pa, ia, ka, rxa, rya, gc, za, eps_z, sA + dsa, ma, idx, an);
-                if (an >= 32) {
-                    amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
-                    an -= 32;
-                }
-                amb_push(aq, pb, ib, kb, rxb, ryb, gc, zb2, eps_z, sA + dsb, mb, idx, an);
-                if (an >= 32) {
-                    amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
-                    an -= 32;
-                }
+                push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ka, rxa, rya, gc, za, eps_z, sA + dsa, ma, idx, an,
+                                    qn, cnt);
+                push_ambiguous<F64>(sf, tc, ws, aq, p, pb, ib, kb, rxb, ryb, gc, zb2, eps_z, sA + dsb, mb, idx, an,
+                                    qn, cnt);
             }
         }
     }
-    amb_drain(sf, tc, ws, aq, p, an, qn, cnt);
+    drain_queues<F64>(sf, tc, ws, aq, p, an, qn, cnt);
 }
 
-// Phase 2 (FP32), phase form for runs of many revolutions. The task's runs
-// are taken four at a time, one per group of L = 8 lanes, and every lane
-// takes phase offsets of its run. Height, y cell
-// and the point's x offset depend on the spindle phase alone, so they are
-// computed once per offset; the revolutions in which that phase lies inside
-// the run's step window differ only by a shift of S fs in x, and the ones
-// that can bring the point within a cell of the tile are found in closed
-// form and visited. Each visit evaluates exactly as a single item would
-// (the same FP32 pose, binning, guard band and FP64 re-binning).
-__device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<uint32_t>& tc, float dyp, int K,
-                                               int g, int p, WarpScratch& ws, AmbQueue& aq,
-                                               const float4 (&t4)[3], float2 pt, Counters& cnt) {
+// Phase form of phase 2, for runs of many revolutions. The task's runs are
+// taken four at a time, one per group of L = 8 lanes, and every lane takes
+// phase offsets of its run. Height, y cell and the point's x offset depend
+// on the spindle phase alone, so they are computed once per offset; the
+// revolutions in which that phase lies inside the run's step window differ
+// only by a shift of S fs in x, and the ones that can bring the point within
+// a cell of the tile are found in closed form and visited. Each visit
+// evaluates exactly as a single item would (the same FP32 pose, binning,
+// guard band and FP64 re-binning).
+template <bool F64>
+__device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
+                                             int g, int p, WarpScratch& ws, AmbQueue* aq, const float4 (&t4)[3],
+                                             float2 pt, Counters& cnt) {
+    using Cell = CellOf<F64>;
     const int lane = threadIdx.x & 31;
     constexpr int L = kItemLanes;
     const int hl = lane & (L - 1), grp = lane / L;
@@ -856,8 +909,11 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
     const float inv_pitch = sf.inv_pitch_f;
     const float pitch = 1.0f / inv_pitch;
     const float2* __restrict__ ph32 = sf.ph32;
+    const double2* __restrict__ ph64 = sf.ph64;
+    const int NE = sf.n_teeth * sf.E;
+    const double zr = sf.z_ref, stock = sf.stock;
     const int tile_x = sf.tile_x;
-    uint32_t* cells = tc.cells;
+    Cell* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
     const float x_hi = (float)txc * pitch + pitch;  // tile x range plus a cell each side, tile-local
     const float x_lo = -pitch;
@@ -884,6 +940,12 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
         const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
         const int idx = K * sf.E + g * 32 + o;
+        double uz64 = 0.0, vz64 = 0.0, wz64 = 0.0;
+        if constexpr (F64) {
+            uz64 = __ldg(sf.tool64 + 2 * NE + idx);
+            vz64 = __ldg(sf.tool64 + 5 * NE + idx);
+            wz64 = __ldg(sf.tool64 + 8 * NE + idx);
+        }
         int lmax = len;
         for (int o2 = L; o2 < 32; o2 <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
         const int32_t sA = r.occ0 + r.first_off;
@@ -913,11 +975,20 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
             const float ka = (x_lo - x0) * inv_rev, kz = (x_hi - x0) * inv_rev;
             const int k0 = max(kb, (int)floorf(fminf(ka, kz)) - 1);
             const int k1 = min(ke, (int)ceilf(fmaxf(ka, kz)) + 1);
-            const bool row = vo && z < 0.f && ky >= -1 && ky <= tyc;
+            Cell e;
+            bool below;
+            if constexpr (F64) {  // below the stock by the FP64 height
+                const double z64 = height64(__ldg(ph64 + m), uz64, vz64, wz64, zr);
+                below = z64 < stock;
+                e = cell_key(z64);
+            } else {
+                below = z < 0.f;
+                e = cell_key(z);
+            }
+            const bool row = vo && below && ky >= -1 && ky <= tyc;
             const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
             int n_max = n_it;
             for (int o2 = 16; o2 > 0; o2 >>= 1) n_max = max(n_max, __shfl_xor_sync(0xffffffffu, n_max, o2));
-            const uint32_t e = enc32(__float_as_uint(z));
             const bool ky_in = (unsigned)ky < (unsigned)tyc;
             const float dy = fabsf(ry - 0.5f);
             for (int kk = 0; kk < n_max; ++kk) {
@@ -930,141 +1001,22 @@ __device__ __forceinline__ void sweep_phases32(const Surface& sf, const TileCtx<
                 const int ix = (int)lx;
                 cnt.evaluated += (unsigned)v;
                 const bool in = v && ky_in && (unsigned)ix < (unsigned)txc;
-                cnt.cutting += (unsigned)in;
                 const bool amb = fmaxf(fabsf(rx - 0.5f), dy) > hg;  // within gc of a cell boundary
                 const bool upd = in && !amb;
+                cnt.cutting += F64 ? (unsigned)upd : (unsigned)in;
                 const int ci = ky * tile_x + ix;
-                const uint32_t cv = upd ? cells[ci] : 0u;
+                const Cell cv = upd ? cells[ci] : (Cell)0;
                 if (upd && e < cv) {
                     atomicMin(cells + ci, e);
                     ++cnt.atomics;
                 }
                 const bool pw = v && amb && ix >= -1 && ix <= txc;  // (v: ky in [-1, tyc])
-                if (__any_sync(0xffffffffu, pw)) {
-                    amb_push(aq, pw, ix, ky, rx, ry, gc, z, eps_z, s, m, idx, an);
-                    if (an >= 32) {
-                        amb_flush(sf, tc, ws, aq, p, an, qn, cnt);
-                        an -= 32;
-                    }
-                }
+                if (__any_sync(0xffffffffu, pw))
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pw, ix, ky, rx, ry, gc, z, eps_z, s, m, idx, an, qn, cnt);
             }
         }
     }
-    amb_drain(sf, tc, ws, aq, p, an, qn, cnt);
-}
-
-// ---------------------------------------------------------------------------
-// FP64 path: all pose and binning arithmetic in FP64, global coordinates.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void sweep_task64(const Surface& sf, const TileCtx<unsigned long long>& tc, int K, int g,
-                                             int p, WarpScratch& ws, Counters& cnt) {
-    const int lane = threadIdx.x & 31;
-    const int E = sf.E, NE = sf.n_teeth * E;
-    const double yc = path_y(sf, p);
-    const double inv_pitch = sf.inv_pitch;
-    const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock;
-    const int S = sf.S;
-    const int s0 = p * sf.steps_per_pass;
-    const long long ib = (long long)tc.tx * sf.tile_x, kb = (long long)tc.ty * sf.tile_y;
-    const double2* __restrict__ ph64 = sf.ph64;
-    const int tile_x = sf.tile_x;
-    unsigned long long* cells = tc.cells;
-    const int txc = tc.txc, tyc = tc.tyc;
-    for (int o = 0; o < 32; ++o) {
-        const int nr = ws.n[o];
-        if (nr == 0) continue;
-        const int idx = K * E + g * 32 + o;
-        const Vec9 v = load_vec9(sf.tool64, NE, idx);
-        for (int a = 0; a < nr; ++a) {
-            const RunRec r = ws.run[o][a];
-            const int32_t total = rec_total(r);
-            const float inv_len = 1.0f / (float)r.len;
-            for (int t = lane; t < total; t += 32) {
-                int32_t s, m;
-                rec_item(r, S, inv_len, t, &s, &m);
-                const double2 cs = __ldg(ph64 + m);
-                ++cnt.evaluated;
-                const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
-                if (!(z < stock)) continue;
-                const Pose64 P = pose64(v, cs, path_x(sf, p, s - s0), yc, zr);
-                const long long ig = bin64(P.x, x0, inv_pitch) - ib;
-                const long long kg = bin64(P.y, y0, inv_pitch) - kb;
-                if (ig < 0 || ig >= txc || kg < 0 || kg >= tyc) continue;
-                ++cnt.cutting;
-                const unsigned long long e = enc64((unsigned long long)__double_as_longlong(P.z));
-                unsigned long long* cell = cells + (int)kg * tile_x + (int)ig;
-                if (e < *cell) {
-                    atomicMin(cell, e);
-                    ++cnt.atomics;
-                }
-            }
-        }
-    }
-}
-
-// FP64 phase form: every lane takes a spindle phase of the run; height and
-// y cell are computed once per phase and only the revolutions whose x can be
-// within a cell of the tile are visited. Each visit computes the pose with
-// the same FP64 operations as the item form (x from the exact path position
-// of its step), so both forms give the same map.
-__device__ __forceinline__ void sweep_phases64(const Surface& sf, const TileCtx<unsigned long long>& tc, int K,
-                                               int g, int p, WarpScratch& ws, Counters& cnt) {
-    const int lane = threadIdx.x & 31;
-    const int E = sf.E, NE = sf.n_teeth * E;
-    const double yc = path_y(sf, p);
-    const double inv_pitch = sf.inv_pitch;
-    const double x0 = sf.x0, y0 = sf.y0, zr = sf.z_ref, stock = sf.stock;
-    const int S = sf.S;
-    const int s0 = p * sf.steps_per_pass;
-    const long long ib = (long long)tc.tx * sf.tile_x, kb_t = (long long)tc.ty * sf.tile_y;
-    const double2* __restrict__ ph64 = sf.ph64;
-    const int tile_x = sf.tile_x;
-    unsigned long long* cells = tc.cells;
-    const int txc = tc.txc, tyc = tc.tyc;
-    const double xlo = tc.X0 - sf.pitch, xhi = tc.X0 + (double)(txc + 1) * sf.pitch;
-    const double rev = (pass_reversed(sf, p) ? -(double)S : (double)S) * sf.fs;  // x shift per revolution
-    const double inv_rev = 1.0 / rev;
-    for (int o = 0; o < 32; ++o) {
-        const int nr = ws.n[o];
-        if (nr == 0) continue;
-        const int idx = K * E + g * 32 + o;
-        const Vec9 v = load_vec9(sf.tool64, NE, idx);
-        for (int a = 0; a < nr; ++a) {
-            const RunRec r = ws.run[o][a];
-            const int f0 = r.first_off, f1 = r.first_off + r.len0;
-            for (int off = lane; off < r.len; off += 32) {
-                int32_t m = r.m0 + off;
-                m = m >= S ? m - S : m;
-                const double2 cs = __ldg(ph64 + m);
-                const int kb = (off >= f0 && off < f1) ? 0 : 1;
-                const int ke = r.k_last == 0 ? 0 : (off < r.len_last ? r.k_last : r.k_last - 1);
-                const double z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
-                if (!(z < stock) || ke < kb) continue;
-                const double y = __dadd_rn(yc, __fma_rn(cs.x, v.uy, __fma_rn(cs.y, v.vy, v.wy)));
-                const long long kg = bin64(y, y0, inv_pitch) - kb_t;
-                if (kg < 0 || kg >= tyc) continue;
-                const double px = __fma_rn(cs.x, v.ux, __fma_rn(cs.y, v.vx, v.wx));
-                const double xk0 = path_x(sf, p, r.occ0 + off - s0) + px;  // approximate: only bounds k
-                const double ka = (xlo - xk0) * inv_rev, kz = (xhi - xk0) * inv_rev;
-                const int k0 = max(kb, (int)floor(fmin(ka, kz)) - 1);
-                const int k1 = min(ke, (int)ceil(fmax(ka, kz)) + 1);
-                const unsigned long long e = enc64((unsigned long long)__double_as_longlong(z));
-                unsigned long long* row = cells + (int)kg * tile_x;
-                for (int k = k0; k <= k1; ++k) {
-                    const int32_t s = r.occ0 + k * S + off;
-                    const double x = __dadd_rn(path_x(sf, p, s - s0), px);
-                    ++cnt.evaluated;
-                    const long long ig = bin64(x, x0, inv_pitch) - ib;
-                    if (ig < 0 || ig >= txc) continue;
-                    ++cnt.cutting;
-                    if (e < row[ig]) {
-                        atomicMin(row + ig, e);
-                        ++cnt.atomics;
-                    }
-                }
-            }
-        }
-    }
+    drain_queues<F64>(sf, tc, ws, aq, p, an, qn, cnt);
 }
 
 __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) {
@@ -1139,40 +1091,34 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             const int p = task / (sf.n_teeth * G);
             const int rem = task - p * sf.n_teeth * G;
             const int K = rem / G, g = rem - K * G;
-            float ylo, yhi;
-            pass_band_any(sf, tc, ts, p, &ylo, &yhi);
+            float ylo, yhi, dyp;
+            pass_band(sf, tc, ts, p, &ylo, &yhi, &dyp);
             const float4 gb = sf.groups[K * G + g];
             if (gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi) continue;  // warp-uniform
             float4 t4[3];
             float2 pt;
             if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4, pt)) continue;
-            if constexpr (FP64) {
-                if constexpr (kPhases) sweep_phases64(sf, tc, K, g, p, ws, cnt);
-                else sweep_task64(sf, tc, K, g, p, ws, cnt);
-            } else {
-                float yl2, yh2, dyp;
-                pass_band(sf, tc, ts, p, &yl2, &yh2, &dyp);
-                // runs that come back for many revolutions share their per-phase
-                // work (phase form); others are walked item by item
-                if constexpr (!kPhases) {
-                    sweep_items32(sf, tc, dyp, K, g, p, ws, aqs[warp], t4, pt, cnt);
-                    __syncwarp();
-                    continue;
-                }
-                int tot = 0, phases = 0;
-                for (int a = 0; a < ws.n[lane]; ++a) {
-                    tot += rec_total(ws.run[lane][a]);
-                    phases += ws.run[lane][a].len;
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                    phases += __shfl_xor_sync(0xffffffffu, phases, o);
-                }
-                if (tot >= kPhaseFormRevs * phases)
-                    sweep_phases32(sf, tc, dyp, K, g, p, ws, aqs[warp], t4, pt, cnt);
-                else
-                    sweep_items32(sf, tc, dyp, K, g, p, ws, aqs[warp], t4, pt, cnt);
+            AmbQueue* aq = FP64 ? nullptr : aqs + warp;
+            // runs that come back for many revolutions share their per-phase
+            // work (phase form); others are walked item by item
+            if constexpr (!kPhases) {
+                sweep_items<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
+                __syncwarp();
+                continue;
             }
+            int tot = 0, phases = 0;
+            for (int a = 0; a < ws.n[lane]; ++a) {
+                tot += rec_total(ws.run[lane][a]);
+                phases += ws.run[lane][a].len;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                phases += __shfl_xor_sync(0xffffffffu, phases, o);
+            }
+            if (tot >= kPhaseFormRevs * phases)
+                sweep_phases<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
+            else
+                sweep_items<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
             __syncwarp();
         }
         __syncthreads();
