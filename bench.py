@@ -30,6 +30,8 @@ sys.path.insert(0, ROOT)
 METRIC = "edge-point evals/s and surfaces/s at <=5 nm height error; p50/p99 latency"
 UNIT = "cutting edge-point evaluations/s"
 FP32_FLOPS_PER_EVAL = 16  # 6 FMA pose (12) + 2 tile offsets + 2 bin scalings
+FP64_HEIGHT_FLOPS = 5     # FP64 maps: the height row of the pose (2 FMA + 1 add) per evaluation
+FP64_PEAK_TFLOPS = 1.25   # nominal FP64 rate of GB300
 TRAJ_FP64_FLOPS = 15      # one FP64 pose: 3 x (2 FMA + 1 add)
 L2_FLUSH_BYTES = 256 << 20
 
@@ -237,6 +239,28 @@ def reference_arm(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def fp32_alu_peak(torch, device, sm_max_mhz=None):
+    """FP32 FMA peak of the GPU in TFLOP/s: SMs x 128 lanes x 2 flop x max SM clock."""
+    props = torch.cuda.get_device_properties(device)
+    sm_max = sm_max_mhz or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    return peak, "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (props.multi_processor_count, sm_max)
+
+
+def fp64_roofline(cutting, sweep_ms, fp32_peak):
+    """Roofline of an FP64-map sweep: its binning is FP32 arithmetic (against
+    the FP32 peak, as for FP32 maps); its heights run on the FP64 pipe, at
+    most one 5-flop height per evaluation (the phase form shares one among
+    the revolutions of a phase)."""
+    a32 = cutting * FP32_FLOPS_PER_EVAL / (sweep_ms / 1e3) / 1e12
+    a64 = cutting * FP64_HEIGHT_FLOPS / (sweep_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": a32, "peak": fp32_peak, "unit": "TFLOP/s", "frac": a32 / fp32_peak,
+            "flops_per_cutting_eval": FP32_FLOPS_PER_EVAL,
+            "fp64_heights": {"achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                             "frac": a64 / FP64_PEAK_TFLOPS, "flops_per_cutting_eval": FP64_HEIGHT_FLOPS,
+                             "note": "upper bound on the heights computed"}}
 
 
 def time_steps(ctx, F, tool, proc, out, rough, K, flush, precision, events_sweep=True):
@@ -505,7 +529,8 @@ def trajectory_leg(ctx, F, flush, steps=5):
     # one FP64 pose per record (15 flops) against GB300's FP64 rate binds
     # before the 32 B record write does
     return {"records": n, "bytes": n * F.TRAJ_BYTES, "ms": mean, "records_per_s": n / (mean / 1e3),
-            "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s (FP64)", "frac": tf / 1.25,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                         "frac": tf / FP64_PEAK_TFLOPS,
                          "peak_source": "nominal FP64",
                          "note": "algorithmic work = 15 FP64 flops (one pose) per (step, tooth) record; call "
                                  "time includes planning and the per-phase argmin table",
@@ -685,11 +710,10 @@ def gb300_arm(args):
         k64 = max(3, args.steps // 10)
         s64, sw64 = time_steps(ctx, F, t64, p64, out64, rough, k64, flush, "fp64")
         ms64 = max_over_ranks(sum(s64) / len(s64), ws)
+        sw64_mean = sum(sw64) / len(sw64)
         fp64 = {"value": ws * cut64 / (ms64 / 1e3), "ms_per_step": ms64, "steps": k64,
-                "sweep_ms": sum(sw64) / len(sw64), "cutting": cut64,
-                "roofline": {"bound": "alu", "achieved": cut64 * FP32_FLOPS_PER_EVAL / (sum(sw64) / len(sw64)) / 1e9,
-                             "peak": 1.25, "unit": "TFLOP/s (FP64)"}}
-        fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / 1.25
+                "sweep_ms": sw64_mean, "cutting": cut64,
+                "roofline": fp64_roofline(cut64, sw64_mean, fp32_alu_peak(torch, local)[0])}
         del out64
 
     large = None
@@ -724,14 +748,9 @@ def gb300_arm(args):
 
     # roofline of the dominant kernel (the FP32 sweep): algorithmic FP32 flops
     # per cutting evaluation / live event time of the sweep launch
-    props = torch.cuda.get_device_properties(local)
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    if args.precision == "fp32":
-        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-        peak_note = "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (props.multi_processor_count, sm_max)
-    else:
-        peak = 1.25
-        peak_note = "nominal FP64"
+    # (FP64 maps bin with the same FP32 arithmetic; their FP64 heights are
+    # reported beside it against the FP64 rate)
+    peak, peak_note = fp32_alu_peak(torch, local, clk.get("sm_max_mhz"))
     achieved = cutting * FP32_FLOPS_PER_EVAL / (sweep_mean / 1e3) / 1e12
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sweep_%s_raster_ball_d10.json" % args.precision)

@@ -61,7 +61,7 @@ struct Surface {
     double* tool64;   // [9][N*E]: ux uy uz vx vy vz wx wy wz
     float2* ph32;     // [S] (cos, sin) of Theta_m
     double2* ph64;    // [S]
-    float4* groups;   // [N * ceil(E/32)]: (min P_y, max P_y, min P_z, 0) over 32 points
+    float4* groups;   // [N * ceil(E/32)]: (min P_y, max P_y while below the stock, min P_z, 0) over 32 points
     double* plan_part;  // [kPlanParts][4]: per planning block, lowest z, x and y reach
     int* tile_queue;    // next-tile counter of a single-surface sweep (zeroed by planning)
     void* heights;    // output map

@@ -23,15 +23,20 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
                                 long long* d_counters, int grid, int threads, size_t smem,
                                 cudaStream_t st, bool phase_form);
 
-// True when a tile is several feeds per revolution wide, so that the runs of
-// one tile come back for several revolutions: three for the FP32 sweep, one
-// and a half for the FP64 sweep, whose per-item work is dearer (measured on
-// GB300: the ball raster, under one feed per tile, is faster item by item in
-// both; the side wall and the flat-end floor, at two to four, faster by phase:
-// FP64 wall 73.7 -> 15.5 ms, floor 257 -> 208 ms).
+// Whether the sweep is launched in the instantiation that chooses between
+// the item and the phase form per task (otherwise every task takes the item
+// form). FP32 maps: when a tile is three or more feeds per revolution wide,
+// so that the runs of one tile come back for several revolutions (measured
+// on GB300: the ball raster, under one feed per tile, is faster item by
+// item; the side wall and the flat-end floor, at two to four, by phase).
+// FP64 maps always: their FP64 height is computed once per phase in the
+// phase form, and the per-task choice keeps runs of few revolutions item by
+// item (ball raster FP64 4.55 -> 3.57 ms with 512x32 tiles, 8 mm floor
+// 79.6 -> 55.0 ms).
 inline bool phase_form_pays(const fsm_tool_desc& t, const fsm_process_desc& p, int tile_x) {
+    if (p.precision == FSM_FP64) return true;
     const double feeds = (double)tile_x * p.pitch / ((double)t.n_teeth * p.fz);
-    return feeds >= (p.precision == FSM_FP64 ? 1.5 : 3.0);
+    return feeds >= 3.0;
 }
 
 // Trajectory map of one planned surface: argmin table d_jmin (S * n_teeth

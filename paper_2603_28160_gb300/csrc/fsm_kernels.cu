@@ -216,26 +216,6 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
     Surface* sf = surfs + sidx;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int N = sf->n_teeth, E = sf->E, S = sf->S;
-    // per 32-point group bounds for the warp-level quick reject (warp per group)
-    const int G = (E + 31) / 32;
-    for (int gi = warp; gi < N * G; gi += nw) {
-        const int K = gi / G, g = gi - K * G;
-        const int j = g * 32 + lane;
-        float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
-        if (j < E) {
-            const float4* t4 = sf->tool32 + 4 * (size_t)(K * E + j);
-            const float wy = t4[1].z, ay = t4[2].y, wz = t4[2].x, az = t4[2].w;
-            ymin = wy - ay;
-            ymax = wy + ay;
-            zmin = wz - az;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
-            ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
-            zmin = fminf(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
-        }
-        if (lane == 0) sf->groups[gi] = make_float4(ymin, ymax, zmin, 0.f);
-    }
     if (tid == 0) {
         if (sf->tile_queue) *sf->tile_queue = 0;
         double zlo = 1e300, rx = 0.0, ry = 0.0;
@@ -275,6 +255,38 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         const double u24 = 5.9604644775390625e-8;
         sf->guard_extra = (float)(3.0 * u24 * (double)max(sf->tile_x, sf->tile_y) + 1e-6);
     }
+    // per 32-point group bounds for the warp-level quick reject (warp per
+    // group): the y range of the points over the phases in which they are
+    // below the stock (the tile-independent z limit of the enumeration), and
+    // their lowest z. A group outside a tile's y band has no runs there.
+    __syncthreads();
+    const int G = (E + 31) / 32;
+    const float zhi = (float)(sf->stock - sf->z_ref) + kMarginMm;
+    const float fS = (float)S;
+    for (int gi = warp; gi < N * G; gi += nw) {
+        const int K = gi / G, g = gi - K * G;
+        const int j = g * 32 + lane;
+        float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
+        if (j < E) {
+            const PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j));
+            zmin = geo.wz - geo.amp_z;
+            ArcF za;
+            ArcI ia[kMaxArcs];
+            if (below_arc(geo.wz, geo.amp_z, geo.mph_z, zhi, sf->inv_dth_f, fS, &za) > 0 &&
+                to_int_arcs(&za, 1, S, ia) > 0) {
+                sinus_range(geo.wy, geo.amp_y, geo.mph_y, ia[0], sf->dth_f, S, &ymin, &ymax);
+                const float slack = 1e-5f * geo.amp_y + kMarginMm;
+                ymin -= slack;
+                ymax += slack;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+            ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+            zmin = fminf(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+        }
+        if (lane == 0) sf->groups[gi] = make_float4(ymin, ymax, zmin, 0.f);
+    }
 }
 
 // ===========================================================================
@@ -309,9 +321,14 @@ __device__ __forceinline__ int32_t rec_total(const RunRec& r) {
 
 constexpr int kRebinCap = 64;
 // Mean revolutions per run phase from which a task takes the phase form of
-// phase 2 (measured: the ball raster averages 1.7 and is fastest item by
-// item; floors and walls come back 4-20 times).
-constexpr int kPhaseFormRevs = 3;
+// phase 2, as a fraction num/den: 3 for FP32 maps (measured: the ball raster
+// averages 1.7 and is fastest item by item; floors and walls come back 4-20
+// times); 1.2 for FP64 maps, where the phase form also computes the FP64
+// height once per phase instead of once per item.
+template <bool F64>
+__device__ __forceinline__ bool phase_form_task(int items, int phases) {
+    return F64 ? 5 * items >= 6 * phases : items >= 3 * phases;
+}
 
 // One warp's scratch: runs of 32 edge points and the FP64 re-binning queue.
 struct WarpScratch {
@@ -1115,7 +1132,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                 tot += __shfl_xor_sync(0xffffffffu, tot, o);
                 phases += __shfl_xor_sync(0xffffffffu, phases, o);
             }
-            if (tot >= kPhaseFormRevs * phases)
+            if (phase_form_task<FP64>(tot, phases))
                 sweep_phases<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
             else
                 sweep_items<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
