@@ -115,9 +115,12 @@ typedef struct {
  *   passes. The tool reference height is chosen so the lowest position any
  *   edge point reaches in a revolution is stock_z - ap.
  *   lead_deg leans the tool axis toward +X_W, tilt_deg toward +Y_W.
- *   precision FSM_FP64 (double heights, all arithmetic FP64) or FSM_FP32
- *   (float heights; edge poses in FP32 tile-local coordinates, FP64 for the
- *   spindle phase, the path position and near-boundary re-binning).
+ *   precision FSM_FP64 (double heights: the FP64 height of every point and
+ *   the cell its FP64 pose falls in, i.e. the map of an all-FP64 sweep; the
+ *   cell is decided from FP32 tile-local coordinates where an error bound
+ *   proves it, else from the FP64 pose) or FSM_FP32 (float heights; edge
+ *   poses in FP32 tile-local coordinates, FP64 for the spindle phase, the
+ *   path position and near-boundary re-binning).
  *   surface FSM_SURFACE_FLOOR: the map covers x (columns) and y (rows) from
  *   (x0, y0), height z, un-machined at stock_z. FSM_SURFACE_WALL (an
  *   extension; the paper maps floors only): the side wall the flank leaves
