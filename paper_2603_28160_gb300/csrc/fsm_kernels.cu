@@ -1214,6 +1214,54 @@ __device__ __forceinline__ double block_reduce(double v, double* sh /*[32]*/) {
     return x;
 }
 
+// Min (kind 1) or max (2) of a float over the block (exact); every thread
+// gets the result.
+template <int KIND>
+__device__ __forceinline__ float block_minmax_f(float v, double* sh /*[32]*/) {
+    float* sf = reinterpret_cast<float*>(sh);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = KIND == 1 ? fminf(v, w) : fmaxf(v, w);
+    }
+    __syncthreads();
+    if (lane == 0) sf[warp] = v;
+    __syncthreads();
+    float x = lane < nw ? sf[lane] : (KIND == 1 ? 3.0e38f : -3.0e38f);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, x, o);
+        x = KIND == 1 ? fminf(x, w) : fmaxf(x, w);
+    }
+    return x;
+}
+
+// Double-float sums for FP32 maps, on the FP32 pipes (GB300 runs FP64 at
+// 1/64 of the FP32 rate): unevaluated pairs (hi, lo) added with Knuth's
+// two-sum on the high parts (exact and symmetric in its operands, so every
+// lane of a butterfly ends with the same pair).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float t, e;
+    two_sum(a.x, b.x, &t, &e);
+    e += a.y + b.y;
+    const float hi = t + e;
+    return make_float2(hi, e - (hi - t));
+}
+
+// Block sum of double-float values in a fixed tree; every thread gets it.
+__device__ __forceinline__ double block_sum_df(float2 v, double* sh /*[32]*/) {
+    float2* s2 = reinterpret_cast<float2*>(sh);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    __syncthreads();
+    if (lane == 0) s2[warp] = v;
+    __syncthreads();
+    float2 x = lane < nw ? s2[lane] : make_float2(0.f, 0.f);
+    for (int o = 16; o > 0; o >>= 1)
+        x = df_add(x, make_float2(__shfl_xor_sync(0xffffffffu, x.x, o), __shfl_xor_sync(0xffffffffu, x.y, o)));
+    return (double)x.x + (double)x.y;
+}
+
 __device__ __forceinline__ int find_job(const int* base, int n, int b) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1261,21 +1309,23 @@ __device__ __forceinline__ bool last_chunk_block(int* done, int j, int n_chunks)
     return last;
 }
 
-__device__ double job_mean(const double* part, int c0, int c1, size_t n, double* sh) {
+// Chunk sums of FP32 maps are taken about a reference height (the map's
+// first cell), so their FP32 leaves carry deviations only; FP64 maps use 0.
+__device__ double job_mean(const double* part, int c0, int c1, size_t n, double ref, double* sh) {
     double s = 0.0;
     for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) s += __ldcg(part + 3 * (size_t)c);
     s = block_reduce<0>(s, sh);
-    return s / (double)n;
+    return ref + s / (double)n;
 }
 
 // End of pass 1: the block completing job j's last chunk stores its mean.
 __device__ __forceinline__ void job_mean_if_last(const RoughJob* __restrict__ jobs,
                                                  const int* __restrict__ chunk_base, const double* part, int n_jobs,
-                                                 int j, void* sync, double* sh) {
+                                                 int j, void* sync, double ref, double* sh) {
     const RoughSync rs = rough_sync(sync, n_jobs);
     const int c0 = chunk_base[j], c1 = chunk_base[j + 1];
     if (last_chunk_block(rs.done1, j, c1 - c0)) {
-        const double mu = job_mean(part, c0, c1, jobs[j].n, sh);
+        const double mu = job_mean(part, c0, c1, jobs[j].n, ref, sh);
         if (threadIdx.x == 0) rs.mean[j] = mu;
     }
 }
@@ -1289,7 +1339,7 @@ template <typename T>
 __device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, int n_jobs,
                                             const int* __restrict__ chunk_base, double* part, int total_chunks,
                                             int per_job, void* sync, int b, double* sh) {
-    if (b >= total_chunks) {  // the profiles ride along after the chunks
+    if (b >= total_chunks) {  // items past the chunks are profiles
         profile_block<T>(jobs, b - total_chunks, per_job, sh);
         return;
     }
@@ -1314,7 +1364,7 @@ __device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, i
         part[3 * (size_t)b + 1] = mn;
         part[3 * (size_t)b + 2] = mx;
     }
-    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, sh);
+    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, 0.0, sh);
 }
 
 // Mean of job j from its chunk sums, in chunk order (identical in every block).
@@ -1394,23 +1444,54 @@ __device__ void profile_block(const RoughJob* __restrict__ jobs, int pb, int per
         __syncthreads();
     }
     auto value = [&](int a) -> double { return cached ? (double)pv[a] : (double)h[base + (size_t)a * stride]; };
-    double s = 0.0;
-    for (int a = threadIdx.x; a < L; a += blockDim.x) s += value(a);
-    const double mu = block_reduce<0>(s, sh) / (double)L;
-    double w = 0.0;
-    for (int a = threadIdx.x; a < L; a += blockDim.x) w += fabs(value(a) - mu);
-    const double ra = block_reduce<0>(w, sh) / (double)L;
+    double mu, ra;
+    if (sizeof(T) == 4 && cached) {
+        // FP32 maps: mean and mean |z - mu| in double-float on the FP32 pipes
+        // (each deviation formed exactly: two-sum of z and -mu_hi, less mu_lo)
+        float2 acc = make_float2(0.f, 0.f);
+        for (int a = threadIdx.x; a < L; a += blockDim.x) acc = df_add(acc, make_float2((float)pv[a], 0.f));
+        mu = block_sum_df(acc, sh) / (double)L;
+        const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
+        float2 w = make_float2(0.f, 0.f);
+        for (int a = threadIdx.x; a < L; a += blockDim.x) {
+            float d, e, dh, dl;
+            two_sum((float)pv[a], -mu_hi, &d, &e);
+            two_sum(d, e - mu_lo, &dh, &dl);  // z - mu as a normalised pair: its sign is dh's
+            w = df_add(w, dh < 0.f ? make_float2(-dh, -dl) : make_float2(dh, dl));
+        }
+        ra = block_sum_df(w, sh) / (double)L;
+    } else {
+        double s = 0.0;
+        for (int a = threadIdx.x; a < L; a += blockDim.x) s += value(a);
+        mu = block_reduce<0>(s, sh) / (double)L;
+        double w = 0.0;
+        for (int a = threadIdx.x; a < L; a += blockDim.x) w += fabs(value(a) - mu);
+        ra = block_reduce<0>(w, sh) / (double)L;
+    }
     double rz = 0.0;
     for (int seg = 0; seg < 5; ++seg) {  // Rz: max - min over 5 segments [floor(qL/5), floor((q+1)L/5))
         const int lo = (int)(((long long)seg * L) / 5), hi = (int)(((long long)(seg + 1) * L) / 5);
-        double mx = -1e300, mn = 1e300;
-        for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
-            const double z = value(a);
-            mx = fmax(mx, z);
-            mn = fmin(mn, z);
+        double mx, mn;
+        if constexpr (sizeof(T) == 4) {  // exact in the map's own precision
+            float fx = -3.0e38f, fn = 3.0e38f;
+            for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
+                const float z = cached ? (float)pv[a] : (float)h[base + (size_t)a * stride];
+                fx = fmaxf(fx, z);
+                fn = fminf(fn, z);
+            }
+            mx = (double)block_minmax_f<2>(fx, sh);
+            mn = (double)block_minmax_f<1>(fn, sh);
+        } else {
+            mx = -1e300;
+            mn = 1e300;
+            for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
+                const double z = value(a);
+                mx = fmax(mx, z);
+                mn = fmin(mn, z);
+            }
+            mx = block_reduce<2>(mx, sh);
+            mn = block_reduce<1>(mn, sh);
         }
-        mx = block_reduce<2>(mx, sh);
-        mn = block_reduce<1>(mn, sh);
         rz += mx - mn;
     }
     if (threadIdx.x == 0) {
@@ -1464,17 +1545,20 @@ __device__ __forceinline__ void rough2_item(const RoughJob* __restrict__ jobs, i
         finalize_job(jobs, chunk_base, part, part2, j, mu, sh);
 }
 
-// FP32 maps: the same two passes with 16-byte loads; per-cell terms in FP32,
-// summed in FP32 over 32 cells and then folded into the FP64 sums (relative
-// error of a leaf <= 32 u ~ 2e-6, far inside the FP32 path's 1e-4 target;
-// FP64 maps keep FP64 throughout). The mean is used as a float pair so the
-// deviations keep full FP32 precision.
+// FP32 maps: the same two passes with 16-byte loads and no FP64 arithmetic
+// per cell or per chunk: per-cell terms in FP32, summed in FP32 over 32
+// cells (relative error of a leaf <= 32 u ~ 2e-6, far inside the FP32 path's
+// 1e-4 target), the leaves and the block sums kept as double-float pairs.
+// Pass 1 sums z - ref about the map's first cell, so its leaves carry
+// deviations only; min and max are exact in FP32. The mean is used as a
+// float pair so the deviations keep full FP32 precision. FP64 maps keep FP64
+// throughout.
 __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 __device__ __forceinline__ void rough1_f32_item(const RoughJob* __restrict__ jobs, int n_jobs,
                                                 const int* __restrict__ chunk_base, double* part, int total_chunks,
                                                 int per_job, void* sync, int b, double* sh) {
-    if (b >= total_chunks) {  // the profiles ride along after the chunks
+    if (b >= total_chunks) {  // items past the chunks are profiles
         profile_block<float>(jobs, b - total_chunks, per_job, sh);
         return;
     }
@@ -1483,7 +1567,8 @@ __device__ __forceinline__ void rough1_f32_item(const RoughJob* __restrict__ job
     size_t lo, hi;
     chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
     const float* h = reinterpret_cast<const float*>(jb.h);
-    double s = 0.0;
+    const float ref = __ldg(h);
+    float2 s = make_float2(0.f, 0.f);  // sum of z - ref
     float mn = 3.0e38f, mx = -3.0e38f;
     if (aligned16(h)) {
         const size_t v0 = lo >> 2, v1 = hi >> 2;  // lo is a multiple of 4
@@ -1495,36 +1580,36 @@ __device__ __forceinline__ void rough1_f32_item(const RoughJob* __restrict__ job
             for (int r = 0; r < 8; ++r, v += blockDim.x) {
                 if (v < v1) {
                     const float4 q = __ldg(h4 + v);
-                    leaf += (q.x + q.y) + (q.z + q.w);
+                    leaf += ((q.x - ref) + (q.y - ref)) + ((q.z - ref) + (q.w - ref));
                     mn = fminf(mn, fminf(fminf(q.x, q.y), fminf(q.z, q.w)));
                     mx = fmaxf(mx, fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w)));
                 }
             }
-            s += (double)leaf;
+            s = df_add(s, make_float2(leaf, 0.f));
         }
         for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
             const float z = h[i];
-            s += (double)z;
+            s = df_add(s, make_float2(z - ref, 0.f));
             mn = fminf(mn, z);
             mx = fmaxf(mx, z);
         }
     } else {
         for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const float z = h[i];
-            s += (double)z;
+            s = df_add(s, make_float2(z - ref, 0.f));
             mn = fminf(mn, z);
             mx = fmaxf(mx, z);
         }
     }
-    s = block_reduce<0>(s, sh);
-    const double dmn = block_reduce<1>((double)mn, sh);
-    const double dmx = block_reduce<2>((double)mx, sh);
+    const double sum = block_sum_df(s, sh);
+    mn = block_minmax_f<1>(mn, sh);
+    mx = block_minmax_f<2>(mx, sh);
     if (threadIdx.x == 0) {
-        part[3 * (size_t)b] = s;
-        part[3 * (size_t)b + 1] = dmn;
-        part[3 * (size_t)b + 2] = dmx;
+        part[3 * (size_t)b] = sum;
+        part[3 * (size_t)b + 1] = (double)mn;
+        part[3 * (size_t)b + 2] = (double)mx;
     }
-    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, sh);
+    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, (double)ref, sh);
 }
 
 __device__ __forceinline__ void dev_terms(float z, float mu_hi, float mu_lo, float* a) {
@@ -1547,7 +1632,7 @@ __device__ __forceinline__ void rough2_f32_item(const RoughJob* __restrict__ job
     size_t lo, hi;
     chunk_range<float>(jb, b - chunk_base[j], &lo, &hi);
     const float* h = reinterpret_cast<const float*>(jb.h);
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    float2 v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     if (aligned16(h)) {
         const size_t v0 = lo >> 2, v1 = hi >> 2;
         const float4* h4 = reinterpret_cast<const float4*>(h);
@@ -1564,31 +1649,32 @@ __device__ __forceinline__ void rough2_f32_item(const RoughJob* __restrict__ job
                     dev_terms(z.w, mu_hi, mu_lo, a);
                 }
             }
-            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+            for (int k = 0; k < 4; ++k) v[k] = df_add(v[k], make_float2(a[k], 0.f));
         }
         for (size_t i = (v1 << 2) + threadIdx.x; i < hi; i += blockDim.x) {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
             dev_terms(h[i], mu_hi, mu_lo, a);
-            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+            for (int k = 0; k < 4; ++k) v[k] = df_add(v[k], make_float2(a[k], 0.f));
         }
     } else {
         for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
             dev_terms(h[i], mu_hi, mu_lo, a);
-            for (int k = 0; k < 4; ++k) v[k] += (double)a[k];
+            for (int k = 0; k < 4; ++k) v[k] = df_add(v[k], make_float2(a[k], 0.f));
         }
     }
-    for (int k = 0; k < 4; ++k) v[k] = block_reduce<0>(v[k], sh);
+    double vs[4];
+    for (int k = 0; k < 4; ++k) vs[k] = block_sum_df(v[k], sh);
     if (threadIdx.x == 0) {
         double* o = part2 + 4 * (size_t)b;
-        o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
+        o[0] = vs[0]; o[1] = vs[1]; o[2] = vs[2]; o[3] = vs[3];
     }
     // the block that finishes a job's last chunk combines the job
     if (last_chunk_block(rs.done2, j, chunk_base[j + 1] - chunk_base[j]))
         finalize_job(jobs, chunk_base, part, part2, j, mu, sh);
 }
 
-// Persistent roughness passes: blocks walk the items (chunks, then profiles)
+// Persistent roughness passes: blocks walk the items (pass 1: profiles, then chunks)
 // in a grid stride; partial results are stored per chunk, so the combine
 // order does not depend on which block took which chunk.
 template <typename T>
@@ -1596,15 +1682,21 @@ __global__ void __launch_bounds__(256) rough1_kernel(const RoughJob* __restrict_
                                                      const int* __restrict__ chunk_base, double* part,
                                                      int total_chunks, int per_job, void* sync, int n_items) {
     __shared__ double sh[32];
-    for (int b = blockIdx.x; b < n_items; b += gridDim.x)
-        rough1_item<T>(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, b, sh);
+    const int n_prof = n_items - total_chunks;  // profiles first: they are the longest items
+    for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
+        const int item = b < n_prof ? total_chunks + b : b - n_prof;
+        rough1_item<T>(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, item, sh);
+    }
 }
 __global__ void __launch_bounds__(256) rough1_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
                                                          const int* __restrict__ chunk_base, double* part,
                                                          int total_chunks, int per_job, void* sync, int n_items) {
     __shared__ double sh[32];
-    for (int b = blockIdx.x; b < n_items; b += gridDim.x)
-        rough1_f32_item(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, b, sh);
+    const int n_prof = n_items - total_chunks;  // profiles first: they are the longest items
+    for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
+        const int item = b < n_prof ? total_chunks + b : b - n_prof;
+        rough1_f32_item(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, item, sh);
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(256) rough2_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
