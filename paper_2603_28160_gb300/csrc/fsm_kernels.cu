@@ -555,6 +555,14 @@ __device__ __forceinline__ unsigned long long cell_key(double z) {
     return enc64((unsigned long long)__double_as_longlong(z));
 }
 
+// Key below which a height is below the stock: z < stock exactly when
+// cell_key(z) < stock_key(stock) (both zeros take the key of -0, the lowest
+// of the two, so that -0 is not below +0). Compares integers on the ALU
+// instead of a double on GB300's 1/64-rate FP64 pipe.
+__device__ __forceinline__ unsigned long long stock_key(double stock) {
+    return cell_key(stock == 0.0 ? -0.0 : stock);
+}
+
 // FP64 height of edge point (u, v, w) at phase (cos, sin): the z row of the
 // FP64 pose.
 __device__ __forceinline__ double height64(double2 cs, double uz, double vz, double wz, double zr) {
@@ -790,7 +798,8 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
     const float2* __restrict__ ph32 = sf.ph32;
     const double2* __restrict__ ph64 = sf.ph64;
     const int NE = sf.n_teeth * sf.E;
-    const double zr = sf.z_ref, stock = sf.stock;
+    const double zr = sf.z_ref;
+    const unsigned long long below_key = stock_key(sf.stock);
     const int tile_x = sf.tile_x;
     Cell* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
@@ -860,12 +869,10 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
             Cell ea, eb;
             bool cut_a, cut_b;
             if constexpr (F64) {  // below the stock by the FP64 height
-                const double za64 = height64(__ldg(ph64 + ma), uz64, vz64, wz64, zr);
-                const double zb64 = height64(__ldg(ph64 + mb), uz64, vz64, wz64, zr);
-                cut_a = va && za64 < stock;
-                cut_b = vb && zb64 < stock;
-                ea = cell_key(za64);
-                eb = cell_key(zb64);
+                ea = cell_key(height64(__ldg(ph64 + ma), uz64, vz64, wz64, zr));
+                eb = cell_key(height64(__ldg(ph64 + mb), uz64, vz64, wz64, zr));
+                cut_a = va && ea < below_key;
+                cut_b = vb && eb < below_key;
             } else {
                 cut_a = va && za < 0.f;
                 cut_b = vb && zb2 < 0.f;
@@ -928,7 +935,8 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
     const float2* __restrict__ ph32 = sf.ph32;
     const double2* __restrict__ ph64 = sf.ph64;
     const int NE = sf.n_teeth * sf.E;
-    const double zr = sf.z_ref, stock = sf.stock;
+    const double zr = sf.z_ref;
+    const unsigned long long below_key = stock_key(sf.stock);
     const int tile_x = sf.tile_x;
     Cell* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
@@ -995,9 +1003,8 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             Cell e;
             bool below;
             if constexpr (F64) {  // below the stock by the FP64 height
-                const double z64 = height64(__ldg(ph64 + m), uz64, vz64, wz64, zr);
-                below = z64 < stock;
-                e = cell_key(z64);
+                e = cell_key(height64(__ldg(ph64 + m), uz64, vz64, wz64, zr));
+                below = e < below_key;
             } else {
                 below = z < 0.f;
                 e = cell_key(z);
