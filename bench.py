@@ -429,8 +429,9 @@ PAPER_DT_S = 2e-7
 def paper_case2_leg(ctx, F, flush, steps=3):
     """The paper's own performance workload: the round-insert face mill of
     Case 2 over 10 x 5 mm at 5 um, zero runout, the nine (vc, fz, ap)
-    conditions of Section 4.3. FP64 one surface at a time, and FP32 as one
-    prepared batch of nine, each with roughness."""
+    conditions of Section 4.3, in FP64 and FP32, each as one prepared batch
+    of nine and one surface at a time (host enqueue included), each surface
+    with its roughness."""
     import torch
     from paper_2603_28160_gb300 import workloads as W
     out = {}
@@ -450,36 +451,40 @@ def paper_case2_leg(ctx, F, flush, steps=3):
         torch.cuda.synchronize()
         cutting = int(cnt[1].item())
         code = F.FSM_FP64 if prec == "fp64" else F.FSM_FP32
-        b = ctx.batch(tools, procs, outs, rough_buf=rough, tile=tuned["tile"],
-                      threads=tuned["threads"]) if prec == "fp32" else None
+        b = ctx.batch(tools, procs, outs, rough_buf=rough, tile=tuned["tile"], threads=tuned["threads"])
 
-        def one_step():
-            if b is not None:
+        def one_step(batched):
+            if batched:
                 b.run()
             else:
                 for t_, p_, o_ in zip(tools, procs, outs):
                     ctx.predict_surface(t_, p_, o_)
                     ctx.roughness_async(o_, code, rough)
-        for _ in range(3):
-            one_step()
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            one_step()
-            e1.record()
+
+        def timed(batched):
+            for _ in range(3):
+                one_step(batched)
             torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        mean = sum(ms) / len(ms)
-        if b is not None:
-            b.close()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                one_step(batched)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return sum(ms) / len(ms)
+        mean = timed(True)
+        single = timed(False)
+        b.close()
         out[prec] = {"ms_per_9_surfaces": mean, "ms_per_surface": mean / len(ws),
                      "sweep_shape": {"tile": list(tuned["tile"]), "threads": tuned["threads"]},
                      "surfaces_per_s": len(ws) / (mean / 1e3), "cutting": cutting,
-                     "value": cutting / (mean / 1e3), "unit": UNIT,
-                     "launch": "prepared batch of 9" if prec == "fp32" else "one surface at a time"}
+                     "value": cutting / (mean / 1e3), "unit": UNIT, "launch": "prepared batch of 9",
+                     "one_at_a_time": {"ms_per_surface": single / len(ws),
+                                       "launch": "fsm_predict_surface + fsm_roughness per surface, "
+                                                 "host enqueue included"}}
         del outs
     torch.cuda.empty_cache()
     grid = W.paper_grid(dt_s=PAPER_DT_S)

@@ -52,7 +52,8 @@ static fsm_status check_tool(const fsm_tool_desc* t) {
         !(t->corner_radius > 0.0 && t->corner_radius <= 0.5 * t->diameter && finite(t->corner_radius)))
         return fail(FSM_E_INVALID, "corner_radius must be in (0, D/2]");
     if (t->kind == FSM_TOOL_INSERT) {
-        if (!(t->insert_radius > 0.0) || !finite(t->insert_radius)) return fail(FSM_E_INVALID, "insert_radius must be > 0");
+        if (!(t->insert_radius > 0.0) || !finite(t->insert_radius))
+            return fail(FSM_E_INVALID, "insert_radius must be > 0");
         const double v[] = {t->rake_f_deg, t->rake_p_deg, t->eps_r_mm, t->eps_a_mm};
         for (double x : v)
             if (!finite(x)) return fail(FSM_E_INVALID, "non-finite insert parameter");
@@ -303,7 +304,21 @@ fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* sm
     if (sh.tile_x < 4 || sh.tile_y < 1 || (sh.tile_x & 3)) return fail(FSM_E_INVALID, "tile_x must be a multiple of 4");
     *smem = sweep_smem_bytes(precision, sh.tile_x, sh.tile_y, sh.threads);
     if (*smem + 1024 > ctx->smem_optin) return fail(FSM_E_INVALID, "tile does not fit in shared memory");
-    int b = sweep_blocks_per_sm(precision, sh.threads, *smem);
+    // the occupancy queries cost host time on every call: cached per context
+    const std::array<long long, 3> key = {precision, sh.threads, (long long)*smem};
+    int b = -1;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->occupancy.find(key);
+        if (it != ctx->occupancy.end()) b = it->second;
+    }
+    if (b < 0) {
+        b = sweep_blocks_per_sm(precision, sh.threads, *smem);
+        if (b > 0) {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->occupancy[key] = b;
+        }
+    }
     if (b <= 0) {
         cudaGetLastError();
         return fail(FSM_E_CUDA, "sweep kernel cannot be resident with this configuration");
@@ -352,7 +367,7 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     fill_surface(t, p, sh, &s, (char*)ws + surf_bytes);
     s.heights = d_heights;
     Surface* d_s = (Surface*)ws;
-    if ((e = launch_plan(d_s, 1, &s, st)) != cudaSuccess) {
+    if ((e = launch_plan(d_s, 1, &s, 0, ctx->sm_count, st)) != cudaSuccess) {
         cudaFreeAsync(ws, st);
         return cuda_fail(e, "plan kernel");
     }
@@ -371,7 +386,7 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     return FSM_OK;
 }
 
-fsm_status trajectory_one(fsm_ctx*, const fsm_tool_desc& t, const fsm_process_desc& p, fsm_traj_point* d_out,
+fsm_status trajectory_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, fsm_traj_point* d_out,
                           int64_t capacity, cudaStream_t st) {
     const long long n_rec = (long long)p.n_passes * p.steps_per_pass * t.n_teeth;
     if (capacity < n_rec) return fail(FSM_E_INVALID, "trajectory buffer holds fewer records than the tool path");
@@ -387,7 +402,7 @@ fsm_status trajectory_one(fsm_ctx*, const fsm_tool_desc& t, const fsm_process_de
     fill_surface(t, p, sh, &s, (char*)ws + surf_bytes);
     s.heights = nullptr;
     Surface* d_s = (Surface*)ws;
-    if ((e = launch_plan(d_s, 1, &s, st)) == cudaSuccess)
+    if ((e = launch_plan(d_s, 1, &s, 0, ctx->sm_count, st)) == cudaSuccess)
         e = launch_trajectory(d_s, s.S, t.n_teeth, n_rec, (int32_t*)((char*)ws + surf_bytes + table_bytes), d_out,
                               st);
     cudaError_t e2 = cudaFreeAsync(ws, st);

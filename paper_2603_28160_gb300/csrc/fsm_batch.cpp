@@ -30,6 +30,7 @@ struct BatchLayout {
            off_cb32 = 0, off_part64 = 0, off_part32 = 0, off_tables = 0, total = 0;
     bool rough = false;
     bool phase_form32 = false, phase_form64 = false;  // some surface's runs come back for many revolutions
+    int plan_work = 0;  // largest (edge points + phases) of a surface, for the planning grid
     long long* counters = nullptr;
     void* events[2] = {nullptr, nullptr};
     std::vector<char> blob;  // host image of [off_surf, off_tables)
@@ -83,6 +84,7 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
         const Shape& sh = procs[i]->precision == FSM_FP64 ? L->sh64 : L->sh32;
         toff[k] = tables;
         tables += fill_surface(*tools[i], *procs[i], sh, &hs[k], nullptr);
+        L->plan_work = std::max(L->plan_work, hs[k].n_teeth * hs[k].E + hs[k].S);
     }
     std::vector<int> tb64(L->n64 + 1, 0), tb32(L->n32 + 1, 0), cb64(L->n64 + 1, 0), cb32(L->n32 + 1, 0);
     for (int k = 0; k < n; ++k) {
@@ -149,7 +151,8 @@ fsm_status run_batch(fsm_ctx* ctx, const BatchLayout& L, char* base, cudaStream_
     cudaError_t e = cudaMemsetAsync(base + L.off_queue, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queues)");
     Surface* d_surf = (Surface*)(base + L.off_surf);
-    if ((e = launch_plan(d_surf, L.n, nullptr, st)) != cudaSuccess) return cuda_fail(e, "plan kernel");
+    if ((e = launch_plan(d_surf, L.n, nullptr, L.plan_work, ctx->sm_count, st)) != cudaSuccess)
+        return cuda_fail(e, "plan kernel");
     int* q = (int*)(base + L.off_queue);
     if (L.events[0]) cudaEventRecord((cudaEvent_t)L.events[0], st);
     if (L.n64) {

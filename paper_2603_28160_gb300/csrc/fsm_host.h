@@ -30,6 +30,8 @@ struct fsm_ctx {
     fsm::Server* server = nullptr;
     // autotuned sweep shapes: workload signature -> (tile_x, tile_y, ctas_per_sm, threads)
     std::map<std::string, std::array<int, 4>> tuned;
+    // resident sweep CTAs per SM: (precision, threads, shared bytes) -> count
+    std::map<std::array<long long, 3>, int> occupancy;
 };
 
 namespace fsm {

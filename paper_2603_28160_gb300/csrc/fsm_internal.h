@@ -11,7 +11,11 @@ namespace fsm {
 
 // Build tables and derived values of n surfaces (one block each). If `one`
 // is not NULL it is copied into d_surfs[0] first (n must be 1).
-cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_t st);
+// Planning of n surfaces (one: a single surface passed by value). Each
+// surface gets up to kPlanParts blocks, as many as its largest
+// (edge points + phases) work calls for while n x blocks stays within a few
+// waves of the GPU's sm_count SMs; max_work is taken from `one` when given.
+cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, int max_work, int sm_count, cudaStream_t st);
 
 size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads);
 int sweep_blocks_per_sm(int precision, int threads, size_t smem);

@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
     if (use_one && blockIdx.y == 0 && threadIdx.x == 0) surfs[sidx] = one;
     __shared__ double A[9];
     __shared__ double kap[2];
+    __shared__ double run_c[2];                  // runout offset (x, y)
+    __shared__ double tooth_t[kMaxTeeth][2];     // per tooth: tan(helix), reference angle
     __shared__ double shd[32];
     __shared__ float shf[32];
     const int tid = threadIdx.x;
@@ -67,6 +69,32 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
     const double R = 0.5 * sf.diameter;
     const double sigma = (double)sf.rot_sense;
     const double dth = deg2rad(sf.rot_step_deg);
+    // per-surface and per-tooth terms, once per block (blocks of at least 64 threads)
+    if (tid < N) {
+        tooth_t[tid][0] = tan(deg2rad(sf.helix_deg[tid]));
+        tooth_t[tid][1] = -deg2rad(sf.tooth_deg[tid]);
+    }
+    __shared__ double ins[5];  // round insert: cos, sin of the radial rake; sin, cos of the axial rake; dL
+    if (tid == 32) {
+        const double lam = deg2rad(sf.runout_phase_deg);
+        run_c[0] = sf.runout_mm * cos(lam);
+        run_c[1] = sf.runout_mm * sin(lam);
+    }
+    if (tid == 33 && sf.kind == 2) {
+        const double Ri = sf.insert_radius;
+        const double gf = deg2rad(sf.rake_f_deg), gp = deg2rad(sf.rake_p_deg);
+        // unfused products: R^2 - l^2 must be exactly 0 at l = +-R (an fma
+        // would leave its rounding error there, possibly negative)
+        const double rr = __dmul_rn(Ri, Ri);
+        const double imm = Ri - sf.ap;
+        const double dl_ap = sf.ap >= Ri ? Ri : sqrt(fmax(__dsub_rn(rr, __dmul_rn(imm, imm)), 0.0));
+        const double dl_fz = sf.fz / (2.0 * cos(gf));
+        ins[0] = cos(gf);
+        ins[1] = sin(gf);
+        ins[2] = sin(gp);
+        ins[3] = cos(gp);
+        ins[4] = fmin(fmax(dl_ap, dl_fz), Ri);
+    }
     if (tid == 0) {
         double L = deg2rad(sf.lead_deg), T = deg2rad(sf.tilt_deg);
         double cL = cos(L), sL = sin(L), cT = cos(T), sT = sin(T);
@@ -97,24 +125,17 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         double qx, qy, qz;
         if (sf.kind == 2) {  // round insert: lower semicircle, rake, per-insert runout, tooth angle
             const double Ri = sf.insert_radius;
-            const double gf = deg2rad(sf.rake_f_deg), gp = deg2rad(sf.rake_p_deg);
-            // unfused products: R^2 - l^2 must be exactly 0 at l = +-R (an fma
-            // would leave its rounding error there, possibly negative)
             const double rr = __dmul_rn(Ri, Ri);
-            const double imm = Ri - sf.ap;
-            const double dl_ap = sf.ap >= Ri ? Ri : sqrt(fmax(__dsub_rn(rr, __dmul_rn(imm, imm)), 0.0));
-            const double dl_fz = sf.fz / (2.0 * cos(gf));
-            const double dL = fmin(fmax(dl_ap, dl_fz), Ri);
+            const double cgf = ins[0], sgf = ins[1], sgp = ins[2], cgp = ins[3], dL = ins[4];
             const double l = -dL + 2.0 * dL * ((double)j / (double)(E - 1));
             const double zc = Ri - sqrt(fmax(__dsub_rn(rr, __dmul_rn(l, l)), 0.0));
             // insert frame -> tool frame (x along the radius at the tooth's reference)
-            const double xt = cos(gf) * l + sin(gf) * sin(gp) * zc + R + (double)K * sf.eps_r_mm;
-            const double yt = -sin(gf) * l + cos(gf) * sin(gp) * zc;
-            const double zt = cos(gp) * zc + (double)K * sf.eps_a_mm;
-            const double ta = -deg2rad(sf.tooth_deg[K]);
-            const double lam = deg2rad(sf.runout_phase_deg);
-            qx = cos(ta) * xt - sin(ta) * yt + sf.runout_mm * cos(lam);
-            qy = sin(ta) * xt + cos(ta) * yt + sf.runout_mm * sin(lam);
+            const double xt = cgf * l + sgf * sgp * zc + R + (double)K * sf.eps_r_mm;
+            const double yt = -sgf * l + cgf * sgp * zc;
+            const double zt = cgp * zc + (double)K * sf.eps_a_mm;
+            const double ta = tooth_t[K][1];
+            qx = cos(ta) * xt - sin(ta) * yt + run_c[0];
+            qy = sin(ta) * xt + cos(ta) * yt + run_c[1];
             qz = zt;
         } else {
             double r, h;
@@ -150,11 +171,12 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
                 r = R * sin(kappa);
                 h = R * (1.0 - cos(kappa));
             }
-            double psi = h * tan(deg2rad(sf.helix_deg[K])) / R;   // helix lag
-            double alpha = -deg2rad(sf.tooth_deg[K]) - sigma * psi;
-            double lam = deg2rad(sf.runout_phase_deg);
-            qx = r * cos(alpha) + sf.runout_mm * cos(lam);
-            qy = r * sin(alpha) + sf.runout_mm * sin(lam);
+            const double psi = h * tooth_t[K][0] / R;  // helix lag
+            const double alpha = tooth_t[K][1] - sigma * psi;
+            double sa, ca;
+            sincos(alpha, &sa, &ca);
+            qx = r * ca + run_c[0];
+            qy = r * sa + run_c[1];
             qz = h;
         }
         double u[3], v[3], w[3];
@@ -168,8 +190,10 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         t64[3 * NE + idx] = v[0]; t64[4 * NE + idx] = v[1]; t64[5 * NE + idx] = v[2];
         t64[6 * NE + idx] = w[0]; t64[7 * NE + idx] = w[1]; t64[8 * NE + idx] = w[2];
         float amp[3], mph[3];
+        double a64[3];
         for (int d = 0; d < 3; ++d) {
-            double a = sqrt(u[d] * u[d] + v[d] * v[d]);
+            const double a = sqrt(u[d] * u[d] + v[d] * v[d]);
+            a64[d] = a;
             double delta = atan2(v[d], u[d]);
             // Theta_m - delta = sense*dth*(m - mph)
             double m = sigma * (delta - deg2rad(sf.phase0_deg)) / dth;
@@ -186,9 +210,9 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         // lowest workpiece z of the point over a turn (exact FP64; min is
         // order-free): the map height on a floor, the map y on a wall
         const int dz = sf.surface == 1 ? 1 : 2;
-        zlo = fmin(zlo, w[dz] - sqrt(u[dz] * u[dz] + v[dz] * v[dz]));
-        rx = fmaxf(rx, (float)(fabs(w[0]) + sqrt(u[0] * u[0] + v[0] * v[0])));
-        ry = fmaxf(ry, (float)(fabs(w[1]) + sqrt(u[1] * u[1] + v[1] * v[1])));
+        zlo = fmin(zlo, w[dz] - a64[dz]);
+        rx = fmaxf(rx, (float)(fabs(w[0]) + a64[0]));
+        ry = fmaxf(ry, (float)(fabs(w[1]) + a64[1]));
     }
     // phase table
     for (int m = first; m < S; m += stride) {
@@ -1803,17 +1827,18 @@ cudaError_t launch_trajectory(const Surface* d_surf, int S, int n_teeth, long lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, cudaStream_t st) {
+cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, int max_work, int sm_count, cudaStream_t st) {
     Surface dummy;
     if (one) dummy = *one;
     else memset(&dummy, 0, sizeof dummy);
-    // a lone surface spreads its FP64 table work over many blocks; a batch
-    // gives each surface one block
-    int parts = 1;
-    if (one) {
-        const int work = one->n_teeth * one->E + one->S;
-        parts = max(1, min(kPlanParts, (work + 255) / 256));
-    }
+    // the FP64 tables (edge points and the phase table: tens of thousands of
+    // phases at fine time steps) are spread over several blocks per surface
+    // as long as the grid stays within ~8 blocks per SM; large batches give
+    // each surface one block
+    if (one) max_work = one->n_teeth * one->E + one->S;
+    const int want = max(1, min(kPlanParts, (max_work + 255) / 256));
+    const int fit = max(1, 8 * max(sm_count, 1) / max(n, 1));
+    const int parts = one ? want : min(want, fit);
     plan_kernel<<<dim3(n, parts), 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
     plan_finish_kernel<<<n, 256, 0, st>>>(d_surfs, n, parts);
     return cudaGetLastError();
