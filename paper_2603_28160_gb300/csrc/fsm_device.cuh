@@ -369,21 +369,4 @@ FSM_HD RunIter run_iter(const Run& r, int32_t S) {
     return it;
 }
 
-// Item t (0 <= t < total) of a run -> global step s and phase index m.
-FSM_HD void run_item(const Run& r, const RunIter& it, int32_t S, int32_t t, int32_t* s, int32_t* m) {
-    int32_t k, off;
-    if (t < it.len0) {
-        k = 0;
-        off = it.first_off + t;
-    } else {
-        int32_t tt = t - it.len0;
-        int32_t q = tt / r.len;
-        k = 1 + q;
-        off = tt - q * r.len;
-    }
-    *s = it.occ0 + k * S + off;
-    int32_t mm = r.m0 + off;
-    *m = mm >= S ? mm - S : mm;
-}
-
 }  // namespace fsm

@@ -419,32 +419,6 @@ __device__ __forceinline__ long long bin64(double coord, double origin, double i
     return (long long)floor(__dmul_rn(__dsub_rn(coord, origin), inv_pitch));
 }
 
-// Item t of a run without an integer division per item (t < 2^24).
-__device__ __forceinline__ void rec_item(const RunRec& r, int32_t S, float inv_len, int32_t t, int32_t* s,
-                                         int32_t* m) {
-    int32_t k, off;
-    if (r.k_last == 0) {  // a single occurrence: consecutive steps
-        *s = r.occ0 + r.first_off + t;
-        const int32_t mm = r.m0 + r.first_off + t;
-        *m = mm >= S ? mm - S : mm;
-        return;
-    }
-    if (t < r.len0) {
-        k = 0;
-        off = r.first_off + t;
-    } else {
-        const int32_t tt = t - r.len0;
-        int32_t q = __float2int_rz((float)tt * inv_len);
-        if ((q + 1) * r.len <= tt) ++q;
-        else if (q * r.len > tt) --q;
-        k = 1 + q;
-        off = tt - q * r.len;
-    }
-    *s = r.occ0 + k * S + off;
-    const int32_t mm = r.m0 + off;
-    *m = mm >= S ? mm - S : mm;
-}
-
 template <typename Cell>
 __device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCtx<Cell>& tc, TileShared& ts) {
     const int np = min(sf.n_passes, kPassCache);
@@ -1379,15 +1353,21 @@ __device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, i
     size_t lo, hi;
     chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
     const T* h = reinterpret_cast<const T*>(jb.h);
-    double s = 0.0, mn = 1e300, mx = -1e300;
+    // min and max on the order-preserving keys (exact, on the integer ALU),
+    // leaving the sum as the one FP64 operation per cell
+    double s = 0.0;
+    unsigned long long kmn = ~0ull, kmx = 0ull;
 #pragma unroll 4
     for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double z = (double)h[i];
         s += z;
-        mn = fmin(mn, z);
-        mx = fmax(mx, z);
+        const unsigned long long k = enc64((unsigned long long)__double_as_longlong(z));
+        kmn = k < kmn ? k : kmn;
+        kmx = k > kmx ? k : kmx;
     }
     s = block_reduce<0>(s, sh);
+    double mn = kmn == ~0ull ? 1e300 : __longlong_as_double((long long)dec64(kmn));
+    double mx = kmx == 0ull ? -1e300 : __longlong_as_double((long long)dec64(kmx));
     mn = block_reduce<1>(mn, sh);
     mx = block_reduce<2>(mx, sh);
     if (threadIdx.x == 0) {
