@@ -110,13 +110,15 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
                  int n_group, int sm_count) {
     // Default ladder, measured on GB300: 16 warps sharing one large, wide
     // tile amortise the per-tile enumeration best (5x5 mm, 1 um ball raster:
-    // FP32 512x48 1.62 ms vs 256x48 with 8 warps 2.19 ms; FP64 512x32 3.57 ms
-    // vs 256x64 4.55 ms), while wide, short tiles keep per-arc x ranges
-    // tight. A step down is taken while the surfaces have fewer tiles than
+    // FP32 512x56 1.38 ms vs 512x48 1.43 ms and, earlier, 512x48 1.62 ms vs
+    // 256x48 with 8 warps 2.19 ms; FP64 512x32 3.57 ms vs 256x64 4.55 ms;
+    // 8 mm flat-end floor FP32 512x56 30.8 ms vs 512x48 32.5 ms), while wide,
+    // short tiles keep per-arc x ranges tight. 512x56 FP32 cells (112 KB) are
+    // the largest that fit beside the 16 warps' scratch. A step down is taken while the surfaces have fewer tiles than
     // there are resident CTAs (small maps: the 2 Mcell face-milled patch runs
     // 0.33 ms at 128x32 against 0.99 ms at 512x48).
     struct Level { int tx, ty, threads, ctas; };
-    static const Level l32[] = {{512, 48, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
+    static const Level l32[] = {{512, 56, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
     static const Level l64[] = {{512, 32, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
     const Level* lv = p.precision == FSM_FP64 ? l64 : l32;
     int pick = 0;
@@ -481,10 +483,10 @@ extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm
     cudaStream_t st = (cudaStream_t)stream;
     // candidates (tile_x, tile_y, threads): wide, short tiles shared by many
     // warps first (they amortise the enumeration and keep x ranges tight)
-    static const int c32[][3] = {{512, 48, 512}, {448, 48, 512}, {512, 40, 512}, {512, 24, 256}, {256, 96, 512},
-                                 {384, 64, 512}, {768, 32, 512}, {512, 56, 512}, {256, 48, 256}, {256, 64, 256},
+    static const int c32[][3] = {{512, 56, 512}, {640, 44, 512}, {512, 48, 512}, {576, 48, 512}, {512, 24, 256},
+                                 {384, 64, 512}, {768, 32, 512}, {256, 96, 512}, {256, 48, 256}, {256, 64, 256},
                                  {128, 48, 256}, {128, 32, 256}, {64, 32, 256}};
-    static const int c64[][3] = {{512, 32, 512}, {384, 40, 512}, {256, 64, 512}, {512, 24, 384}, {256, 48, 512},
+    static const int c64[][3] = {{512, 32, 512}, {640, 27, 512}, {576, 30, 512}, {256, 64, 512}, {512, 24, 384},
                                  {256, 32, 256}, {128, 64, 256}, {128, 32, 256}, {64, 64, 256}, {64, 32, 256}};
     const bool f64 = proc->d.precision == FSM_FP64;
     const int nshape = f64 ? 10 : 13;
