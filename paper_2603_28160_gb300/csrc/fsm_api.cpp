@@ -111,15 +111,17 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
     // Default ladder, measured on GB300: 16 warps sharing one large, wide
     // tile amortise the per-tile enumeration best (5x5 mm, 1 um ball raster:
     // FP32 512x56 1.38 ms vs 512x48 1.43 ms and, earlier, 512x48 1.62 ms vs
-    // 256x48 with 8 warps 2.19 ms; FP64 512x32 3.57 ms vs 256x64 4.55 ms;
-    // 8 mm flat-end floor FP32 512x56 30.8 ms vs 512x48 32.5 ms), while wide,
-    // short tiles keep per-arc x ranges tight. 512x56 FP32 cells (112 KB) are
-    // the largest that fit beside the 16 warps' scratch. A step down is taken while the surfaces have fewer tiles than
+    // 256x48 with 8 warps 2.19 ms; FP64 640x27 3.07 ms vs 512x32 3.34 ms vs
+    // 256x64 4.55 ms; 8 mm flat-end floor FP32 512x56 30.8 ms vs 512x48
+    // 32.5 ms, FP64 640x27 37.1 ms vs 512x32 37.7 ms; FP64 side wall 640x27
+    // 2.89 ms vs 512x32 3.53 ms), while wide, short tiles keep per-arc x
+    // ranges tight. 512x56 FP32 cells (112 KB) and 640x27 FP64 cells (135 KB)
+    // nearly fill the shared memory beside the 16 warps' scratch. A step down is taken while the surfaces have fewer tiles than
     // there are resident CTAs (small maps: the 2 Mcell face-milled patch runs
     // 0.33 ms at 128x32 against 0.99 ms at 512x48).
     struct Level { int tx, ty, threads, ctas; };
     static const Level l32[] = {{512, 56, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
-    static const Level l64[] = {{512, 32, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
+    static const Level l64[] = {{640, 27, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
     const Level* lv = p.precision == FSM_FP64 ? l64 : l32;
     int pick = 0;
     if (group && n_group > 0 && sm_count > 0) {
