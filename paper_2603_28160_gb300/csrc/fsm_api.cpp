@@ -116,9 +116,10 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
     // 32.5 ms, FP64 640x27 37.1 ms vs 512x32 37.7 ms; FP64 side wall 640x27
     // 2.89 ms vs 512x32 3.53 ms), while wide, short tiles keep per-arc x
     // ranges tight. 512x56 FP32 cells (112 KB) and 640x27 FP64 cells (135 KB)
-    // nearly fill the shared memory beside the 16 warps' scratch. A step down is taken while the surfaces have fewer tiles than
-    // there are resident CTAs (small maps: the 2 Mcell face-milled patch runs
-    // 0.33 ms at 128x32 against 0.99 ms at 512x48).
+    // nearly fill the shared memory beside the 16 warps' scratch. A step
+    // down is taken while the surfaces have fewer tiles than there are
+    // resident CTAs (small maps: the 2 Mcell face-milled patch runs 0.33 ms
+    // at 128x32 against 0.99 ms at 512x48).
     struct Level { int tx, ty, threads, ctas; };
     static const Level l32[] = {{512, 56, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
     static const Level l64[] = {{640, 27, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
@@ -340,6 +341,30 @@ std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
     return buf;
 }
 
+// FP32 maps decide a point's cell from FP32 tile-local coordinates unless it
+// lies within a guard band (the FP32 error bound, in cells) of a boundary;
+// the check of an ambiguous point looks one cell to each side, so the band
+// must stay below half a cell. This bounds the band of every run of the
+// workload from the tool's size, the tile and the whole pass length (the
+// device takes each run's own, smaller, figures) and rejects FP32 maps whose
+// pitch is too fine for it -- about 20 nm and below for a 10 mm tool -- for
+// which FP64 maps are the choice.
+fsm_status check_fp32_band(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh) {
+    if (p.precision != FSM_FP32) return FSM_OK;
+    const double u24 = 5.9604644775390625e-8;
+    const double r_max = 0.5 * t.diameter + t.insert_radius +
+                         (double)t.n_teeth * (fabs(t.eps_r_mm) + fabs(t.eps_a_mm)) + t.runout_mm;
+    const double w_sum = 3.0 * (t.diameter + p.ap + t.insert_radius + (double)t.n_teeth * fabs(t.eps_a_mm));
+    const double tile = (double)std::max(sh.tile_x, sh.tile_y);
+    const double span = (double)p.steps_per_pass * (double)t.n_teeth * p.fz * p.rot_step_deg / 360.0;
+    const double band = 1.5 * u24 * (6.0 * r_max + 3.0 * w_sum + 3.0 * tile * p.pitch + 2.0 * span) / p.pitch +
+                        3.0 * u24 * tile + 1e-6;
+    if (band >= 0.45)
+        return fail(FSM_E_INVALID, "pitch too fine for an FP32 map of this tool and pass (FP32 guard band of " +
+                                       std::to_string(band) + " cells); use FSM_FP64");
+    return FSM_OK;
+}
+
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st) {
     const fsm_process_desc* self = &p;
@@ -360,7 +385,9 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     }
     size_t smem = 0;
     int bps = 0;
-    fsm_status rc = sweep_config(ctx, p.precision, sh, &smem, &bps);
+    fsm_status rc = check_fp32_band(t, p, sh);
+    if (rc != FSM_OK) return rc;
+    rc = sweep_config(ctx, p.precision, sh, &smem, &bps);
     if (rc != FSM_OK) return rc;
     Surface s;
     const size_t surf_bytes = align256(sizeof(Surface));

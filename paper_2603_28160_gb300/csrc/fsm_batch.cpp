@@ -82,6 +82,7 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         const Shape& sh = procs[i]->precision == FSM_FP64 ? L->sh64 : L->sh32;
+        if ((rc = check_fp32_band(*tools[i], *procs[i], sh)) != FSM_OK) return rc;
         toff[k] = tables;
         tables += fill_surface(*tools[i], *procs[i], sh, &hs[k], nullptr);
         L->plan_work = std::max(L->plan_work, hs[k].n_teeth * hs[k].E + hs[k].S);

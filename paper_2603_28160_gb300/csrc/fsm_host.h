@@ -88,6 +88,7 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
 fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* smem, int* blocks_per_sm);
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st);
+fsm_status check_fp32_band(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh);
 fsm_status trajectory_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, fsm_traj_point* d_out,
                           int64_t capacity, cudaStream_t st);
 fsm_status roughness_one(fsm_ctx* ctx, const void* d_h, int precision, int nx, int ny, int n_rows, int n_cols,

@@ -102,3 +102,25 @@ def test_rejects_bad_tool(tool):
     ctx = F.Context(0)
     with pytest.raises((F.FsmError, IndexError, ValueError)):
         ctx.tool(tool)
+
+
+def test_fp32_rejects_pitch_below_its_guard_band(oracle_mod):
+    """A 10 mm ball end over a map at 1 nm pitch: the FP32 error bound of the
+    tile-local poses spans several cells, more than the FP32 path's check of
+    ambiguous points covers, so an FP32 map is refused; the FP64 map (whose
+    ambiguous points are all re-binned in FP64) runs and equals the oracle."""
+    import torch
+    from paper_2603_28160_gb300 import fsm as F
+    ctx = F.Context(0)
+    tool = ToolSpec("ball", 10.0, 2, [30.0], n_edge=40)
+    fine = dict(pitch=1e-6, nx=64, ny=64, x0=0.2, y0=-32e-6, pass_x0=-0.4, steps_per_pass=2000)
+    w32 = Workload("fine32", tool, proc(precision="fp32", **fine))
+    t = ctx.tool(w32.tool)
+    out = F.heights_tensor(w32.process)
+    with pytest.raises(F.FsmError):
+        ctx.predict_surface(t, ctx.process(w32.process), out)
+    w64 = Workload("fine64", tool, proc(precision="fp64", **fine))
+    ref = oracle_mod.fsm(w64, n_threads=4)
+    H = gpu_map(ctx, F, w64)
+    torch.cuda.synchronize()
+    compare_maps(H, ref, "fp64")
