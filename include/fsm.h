@@ -241,6 +241,10 @@ fsm_status fsm_destroy_process(fsm_ctx* ctx, fsm_process* proc);
  *              alignment works, slower). Every cell is written; cells no edge
  *              point reaches keep stock_z.
  *   opts       NULL for defaults.
+ * FSM_E_INVALID for an FP32 map whose pitch is too fine for FP32 tile-local
+ * binning with this tool and pass (worst-case FP32 error bound of 0.45 cell
+ * or more: about 20 nm and below for a 10 mm tool); FP64 maps have no such
+ * limit. The same holds for every FP32 surface of a batch.
  * Scratch: stream-ordered device allocations (cudaMallocAsync) freed on the
  * same stream. Asynchronous; errors of the enqueue are returned, kernel
  * faults surface at the next synchronisation. */
