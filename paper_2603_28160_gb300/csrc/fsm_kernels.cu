@@ -832,7 +832,12 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         for (int o2 = L; o2 < 32; o2 <<= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o2));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
-        const float hg = 0.5f - gc;
+        // Cells of a point whose FP32 cell is ambiguous lie within M cells of
+        // it: M = 1 while the band is under a cell (the host keeps FP32 maps'
+        // bands under half a cell); FP64 maps at very fine pitch widen it, and
+        // from a band of half a cell every point is ambiguous (FP64 re-binned).
+        const float hg = gc >= 0.5f ? -1.0f : 0.5f - gc;
+        const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
         const int32_t len = r.len, gap = S - len;
         const float inv_len = 1.0f / (float)len;
         int32_t d2l, r2l, dl, rl, qa, oa;  // 2L and L items in (revolutions, phases); item hl
@@ -896,8 +901,8 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
                 atomicMin(cells + cib, eb);
                 ++cnt.atomics;
             }
-            const bool pa = cut_a && amb_a && ia >= -1 && ia <= txc && ka >= -1 && ka <= tyc;
-            const bool pb = cut_b && amb_b && ib >= -1 && ib <= txc && kb >= -1 && kb <= tyc;
+            const bool pa = cut_a && amb_a && ia >= -M && ia <= txc - 1 + M && ka >= -M && ka <= tyc - 1 + M;
+            const bool pb = cut_b && amb_b && ib >= -M && ib <= txc - 1 + M && kb >= -M && kb <= tyc - 1 + M;
             if (__any_sync(0xffffffffu, pa || pb)) {
                 push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ka, rxa, rya, gc, za, eps_z, sA + dsa, ma, idx, an,
                                     qn, cnt);
@@ -938,8 +943,6 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
     const int tile_x = sf.tile_x;
     Cell* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
-    const float x_hi = (float)txc * pitch + pitch;  // tile x range plus a cell each side, tile-local
-    const float x_lo = -pitch;
     const float rev = (float)S * fs32;            // x shift per revolution
     const float inv_rev = 1.0f / rev;
     int R = ws.n[lane];
@@ -973,7 +976,12 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         for (int o2 = L; o2 < 32; o2 <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
-        const float hg = 0.5f - gc;
+        // the cells a point may belong to lie within M cells of its FP32 cell
+        // (see the item form)
+        const float hg = gc >= 0.5f ? -1.0f : 0.5f - gc;
+        const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
+        const float x_hi = (float)(txc + M) * pitch;  // tile x range plus M cells each side, tile-local
+        const float x_lo = -(float)M * pitch;
         const int f0 = r.first_off, f1 = r.first_off + r.len0;
         for (int ob = 0; ob < lmax; ob += L) {
             const int off = ob + hl;
@@ -1007,7 +1015,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
                 below = z < 0.f;
                 e = cell_key(z);
             }
-            const bool row = vo && below && ky >= -1 && ky <= tyc;
+            const bool row = vo && below && ky >= -M && ky <= tyc - 1 + M;
             const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
             int n_max = n_it;
             for (int o2 = 16; o2 > 0; o2 >>= 1) n_max = max(n_max, __shfl_xor_sync(0xffffffffu, n_max, o2));
@@ -1032,7 +1040,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
                     atomicMin(cells + ci, e);
                     ++cnt.atomics;
                 }
-                const bool pw = v && amb && ix >= -1 && ix <= txc;  // (v: ky in [-1, tyc])
+                const bool pw = v && amb && ix >= -M && ix <= txc - 1 + M;  // (v: ky in [-M, tyc - 1 + M])
                 if (__any_sync(0xffffffffu, pw))
                     push_ambiguous<F64>(sf, tc, ws, aq, p, pw, ix, ky, rx, ry, gc, z, eps_z, s, m, idx, an, qn, cnt);
             }

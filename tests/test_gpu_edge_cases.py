@@ -104,23 +104,26 @@ def test_rejects_bad_tool(tool):
         ctx.tool(tool)
 
 
-def test_fp32_rejects_pitch_below_its_guard_band(oracle_mod):
-    """A 10 mm ball end over a map at 1 nm pitch: the FP32 error bound of the
-    tile-local poses spans several cells, more than the FP32 path's check of
-    ambiguous points covers, so an FP32 map is refused; the FP64 map (whose
-    ambiguous points are all re-binned in FP64) runs and equals the oracle."""
+def test_pitch_below_the_fp32_guard_band(oracle_mod):
+    """A 1 mm flat end at 1 nm pitch (a 2 x 2 um patch of 4 Mcells, crossed by
+    the bottom edge as the tool turns): the FP32 error bound of the
+    tile-local poses reaches a cell, more than the FP32 path's check of
+    ambiguous points covers, so an FP32 map is refused; the FP64 map, whose
+    ambiguous points are re-binned in FP64 from as many cells around the tile
+    as the bound spans, equals the oracle cell by cell."""
     import torch
     from paper_2603_28160_gb300 import fsm as F
     ctx = F.Context(0)
-    tool = ToolSpec("ball", 10.0, 2, [30.0], n_edge=40)
-    fine = dict(pitch=1e-6, nx=64, ny=64, x0=0.2, y0=-32e-6, pass_x0=-0.4, steps_per_pass=2000)
+    tool = ToolSpec("flat", 1.0, 2, [30.0], n_edge=5, n_end=200)
+    fine = dict(fz=0.001, rot_step_deg=0.1, ap=0.1, pitch=1e-6, nx=2000, ny=2000, x0=0.0, y0=0.0,
+                pass_x0=-0.2, pass_y0=0.001, steps_per_pass=20000)
     w32 = Workload("fine32", tool, proc(precision="fp32", **fine))
-    t = ctx.tool(w32.tool)
-    out = F.heights_tensor(w32.process)
     with pytest.raises(F.FsmError):
-        ctx.predict_surface(t, ctx.process(w32.process), out)
+        ctx.predict_surface(ctx.tool(w32.tool), ctx.process(w32.process), F.heights_tensor(w32.process))
     w64 = Workload("fine64", tool, proc(precision="fp64", **fine))
-    ref = oracle_mod.fsm(w64, n_threads=4)
-    H = gpu_map(ctx, F, w64)
-    torch.cuda.synchronize()
+    ref = oracle_mod.fsm(w64, n_threads=8)
+    assert ref.stats["cutting"] > 0
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    H = gpu_map(ctx, F, w64, counters=cnt)
     compare_maps(H, ref, "fp64")
+    assert int(cnt[1].item()) == ref.stats["cutting"]
