@@ -396,9 +396,9 @@ __device__ __forceinline__ Vec9 load_vec9(const double* t64, int NE, int idx) {
     return v;
 }
 
-// Every FP64 pose of the library goes through these functions, with each
-// rounding step spelled out, so the FP64 path and the FP32 path's re-binning
-// assign a point to the same cell.
+// Every FP64 pose of the library (re-binning in the sweep, trajectory
+// records) goes through these functions, with each rounding step spelled
+// out, so a point is assigned to the same cell wherever it is re-binned.
 __device__ __forceinline__ bool pass_reversed(const Surface& sf, int p) { return sf.pass_mode == 1 && (p & 1); }
 // tool reference x at local step n of pass p (a zig-zag return pass runs back)
 __device__ __forceinline__ double path_x(const Surface& sf, int p, int32_t n) {
