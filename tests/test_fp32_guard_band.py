@@ -1,0 +1,93 @@
+"""The FP32 binning's guard band bounds its FP32 error (CPU, no GPU).
+
+FP32 maps and the binning of FP64 maps place an edge point in a cell from
+FP32 tile-local coordinates; a point within the guard band of a cell
+boundary is re-binned with the FP64 pose. The maps equal the FP64 binning
+only if the band bounds the FP32 error of every point. This test models the
+sweep's FP32 arithmetic for the tile-local x and y of a pose -- the run
+anchor from a float pair of the pass offset and of the feed per step
+(double-float affine step), fused multiply-adds of the rounded phase table
+and tool vectors, the bin scaling -- with each fused multiply-add rounded
+once (float32 products are exact in float64), against the same pose in
+float64, over random tools, phases, tiles, pitches, feeds and run spans, and
+checks the error in cells against the band the kernel computes for the run:
+1.5 u (6 max(amp_x, amp_y) + 3 (|w_x| + |w_y| + |w_z|) + 3 tile pitch
++ 2 span) / pitch + 3 u tile + 1e-6, u = 2^-24."""
+import numpy as np
+
+U24 = 2.0 ** -24
+f32 = np.float32
+
+
+def fma32(a, b, c):
+    """fmaf: a*b is exact in float64 for float32 a, b; one rounding to float32
+    (the float64 sum's own rounding is far below float32's)."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(f32)
+
+
+def two_sum(a, b):
+    s = (a + b).astype(f32)
+    bb = (s - a).astype(f32)
+    e = ((a - (s - bb)) + (b - bb)).astype(f32)
+    return s, e
+
+
+def df_affine(d_hi, d_lo, n, f_hi, f_lo):
+    """(d_hi + d_lo) + n (f_hi + f_lo) to float, the kernel's run anchor."""
+    nf = n.astype(f32)
+    p = (nf * f_hi).astype(f32)
+    pe = fma32(nf, f_hi, -p)
+    s, e = two_sum(d_hi, p)
+    e = (e + ((d_lo + pe).astype(f32) + (nf * f_lo).astype(f32)).astype(f32)).astype(f32)
+    return (s + e).astype(f32)
+
+
+def test_guard_band_bounds_fp32_binning_error():
+    rng = np.random.default_rng(20260328)
+    worst = 0.0
+    for pitch in (5e-4, 1e-3, 2e-3, 5e-3, 1e-2):
+        for tile_x, tile_y in ((512, 56), (640, 27), (128, 32), (1024, 8)):
+            n = 200_000
+            amp = rng.uniform(0.0, 10.0, n)
+            ax, ay = amp * rng.uniform(0.0, 1.0, n), amp * rng.uniform(0.0, 1.0, n)
+            phx, phy = rng.uniform(0, 2 * np.pi, n), rng.uniform(0, 2 * np.pi, n)
+            ux, vx, uy, vy = ax * np.cos(phx), ax * np.sin(phx), ay * np.cos(phy), ay * np.sin(phy)
+            wx, wy, wz = rng.uniform(-10.0, 10.0, (3, n))
+            th = rng.uniform(0.0, 2 * np.pi, n)
+            c, s = np.cos(th), np.sin(th)
+            fs = 10.0 ** rng.uniform(-5.0, -2.0, n)
+            span = np.floor(rng.uniform(0.0, 1.0, n) * np.minimum(1e6, 20.0 / fs))  # steps of the run
+            ds = np.floor(rng.uniform(0.0, 1.0, n) * (span + 1))                     # item's steps after the run start
+            n_a = np.floor(rng.uniform(0.0, 1e6, n)).astype(np.int64)                 # pass step of the run start
+            # tile-local targets near the tile, and the pass offset that puts the point there
+            X = rng.uniform(-1.0, tile_x + 1.0, n) * pitch
+            Y = rng.uniform(-1.0, tile_y + 1.0, n) * pitch
+            px = c * ux + s * vx + wx
+            d = X - ds * fs - px - n_a * fs          # pass_x0 - tile origin
+            dyp = Y - (c * uy + s * vy + wy)         # pass line - tile origin (y)
+            # FP32 inputs as the planner stores them
+            c32, s32 = c.astype(f32), s.astype(f32)
+            ux32, vx32, wx32 = ux.astype(f32), vx.astype(f32), wx.astype(f32)
+            uy32, vy32, wy32 = uy.astype(f32), vy.astype(f32), wy.astype(f32)
+            d_hi = d.astype(f32)
+            d_lo = (d - d_hi.astype(np.float64)).astype(f32)
+            fs_hi = fs.astype(f32)
+            fs_lo = (fs - fs_hi.astype(np.float64)).astype(f32)
+            inv_pitch = f32(1.0 / pitch)
+            # the kernel's FP32 arithmetic
+            dxa = df_affine(d_hi, d_lo, n_a, fs_hi, fs_lo)
+            x32 = (fma32(ds.astype(f32), fs_hi, dxa) + fma32(c32, ux32, fma32(s32, vx32, wx32))).astype(f32)
+            y32 = (dyp.astype(f32) + fma32(c32, uy32, fma32(s32, vy32, wy32))).astype(f32)
+            fx, fy = (x32 * inv_pitch).astype(f32), (y32 * inv_pitch).astype(f32)
+            # the same pose in float64 (the FP64 binning's coordinates, up to float64 rounding)
+            ex = np.abs(fx.astype(np.float64) - X / pitch)
+            ey = np.abs(fy.astype(np.float64) - Y / pitch)
+            # the kernel's band for the run, in cells
+            pt_err = 6.0 * np.maximum(ax, ay) + 3.0 * (np.abs(wx) + np.abs(wy) + np.abs(wz)) + \
+                3.0 * max(tile_x, tile_y) * pitch
+            g = 1.5 * U24 * (pt_err + 2.0 * span * fs) / pitch + 3.0 * U24 * max(tile_x, tile_y) + 1e-6
+            ratio = np.maximum(ex, ey) / g
+            assert ratio.max() < 1.0, (pitch, tile_x, tile_y, ratio.max())
+            worst = max(worst, float(ratio.max()))
+    # the band is a worst-case bound: the observed error stays well inside it
+    assert worst < 0.7, worst
