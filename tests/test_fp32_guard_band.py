@@ -91,3 +91,26 @@ def test_guard_band_bounds_fp32_binning_error():
             worst = max(worst, float(ratio.max()))
     # the band is a worst-case bound: the observed error stays well inside it
     assert worst < 0.7, worst
+
+
+def test_height_bound_covers_fp32_height_error():
+    """The FP32 height relative to the stock, z = fma(c, u_z, fma(s, v_z,
+    z_rel + w_z)), is within eps_z = 1.5 u (5 amp_z + 4 (|z_rel| + |w_z|)) of
+    the float64 value: an ambiguous point whose z - eps_z is not below a
+    candidate cell cannot lower it."""
+    rng = np.random.default_rng(7)
+    n = 1_000_000
+    amp = rng.uniform(0.0, 10.0, n)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    uz, vz = amp * np.cos(ph), amp * np.sin(ph)
+    wz = rng.uniform(-10.0, 10.0, n)
+    zrel = rng.uniform(-15.0, 15.0, n)          # tool reference height - stock
+    th = rng.uniform(0.0, 2 * np.pi, n)
+    c, s = np.cos(th), np.sin(th)
+    zrel32, wz32 = zrel.astype(f32), wz.astype(f32)
+    zb = (zrel32 + wz32).astype(f32)
+    z32 = fma32(c.astype(f32), uz.astype(f32), fma32(s.astype(f32), vz.astype(f32), zb))
+    z64 = zrel + wz + c * uz + s * vz
+    eps = 1.5 * U24 * (5.0 * amp + 4.0 * (np.abs(zrel) + np.abs(wz)))
+    ratio = np.abs(z32.astype(np.float64) - z64) / eps
+    assert ratio.max() < 1.0, ratio.max()
