@@ -1,0 +1,128 @@
+"""The sweep's run bookkeeping against brute force (CPU, no GPU).
+
+A run of an edge point is the set of global steps s in [s_lo, s_hi] whose
+spindle phase index (s mod S) lies in the arc m0 .. m0+len-1 (mod S): the
+steps at which that point can be over a tile (Section 2.3's time loop,
+restricted per tile). The kernels never list these steps; they derive them
+from the run's iteration record (first occurrence, offset into it, lengths of
+the first and last occurrences, last revolution) by integer arithmetic with
+float-reciprocal divisions. This test models that arithmetic -- the record,
+the item form's incremental (revolution, phase offset) walk of 8-lane groups
+taking items hl and hl + 8 of every 16, and the phase form's range of
+revolutions per phase offset -- and checks both against the brute-force set
+of steps, item by item, over random runs."""
+import numpy as np
+
+f32 = np.float32
+L = 8  # lanes per run in the item form
+
+
+def imod_pos(a, S):
+    q = int(np.floor(f32(a) * (f32(1.0) / f32(S))))
+    r = a - q * S
+    while r < 0:
+        r += S
+    while r >= S:
+        r -= S
+    return r
+
+
+def idiv_floor(a, S):
+    q = int(f32(a) * (f32(1.0) / f32(S)))
+    while q * S > a:
+        q -= 1
+    while (q + 1) * S <= a:
+        q += 1
+    return q
+
+
+def run_iter(m0, ln, s_lo, s_hi, S):
+    base = s_lo - imod_pos(s_lo - m0, S)
+    if base + ln - 1 < s_lo:
+        base += S
+    if base > s_hi:
+        return None
+    f0, e0 = max(base, s_lo), min(base + ln - 1, s_hi)
+    first_off, len0 = f0 - base, e0 - f0 + 1
+    k_last = idiv_floor(s_hi - base, S)
+    if k_last == 0:
+        len_last, total = 0, len0
+    else:
+        ol = base + k_last * S
+        len_last = min(ol + ln - 1, s_hi) - ol + 1
+        total = len0 + (k_last - 1) * ln + len_last
+    return dict(occ0=base, first_off=first_off, len0=len0, k_last=k_last, len_last=len_last, total=total)
+
+
+def divmod_small(v, ln, inv_len):
+    d = int(f32(v) * inv_len)  # truncation toward zero, v >= 0
+    d += 1 if (d + 1) * ln <= v else 0
+    d -= 1 if d * ln > v else 0
+    return d, v - d * ln
+
+
+def item_walk(r, m0, ln, S):
+    """Steps and phases the item form visits, by item index."""
+    inv_len = f32(1.0) / f32(ln)
+    gap = S - ln
+    s_a = r["occ0"] + r["first_off"]
+    d2l, r2l = divmod_small(2 * L, ln, inv_len)
+    dl, rl = divmod_small(L, ln, inv_len)
+    out = {}
+    tot = r["total"]
+    for hl in range(L):
+        qa, oa = divmod_small(hl + r["first_off"], ln, inv_len)
+        base = 0
+        while base < tot:
+            ta, tb = base + hl, base + hl + L
+            ob, qb = oa + rl, qa + dl
+            if ob >= ln:
+                ob -= ln
+                qb += 1
+            for t, q, o in ((ta, qa, oa), (tb, qb, ob)):
+                if t < tot:
+                    m = m0 + o
+                    m = m - S if m >= S else m
+                    out[t] = (s_a + t + q * gap, m)
+            oa += r2l
+            qa += d2l
+            if oa >= ln:
+                oa -= ln
+                qa += 1
+            base += 2 * L
+    return out
+
+
+def phase_walk(r, ln, S):
+    """Steps the phase form visits: per phase offset, revolutions kb..ke."""
+    f0, f1 = r["first_off"], r["first_off"] + r["len0"]
+    steps = []
+    for off in range(ln):
+        kb = 0 if f0 <= off < f1 else 1
+        ke = 0 if r["k_last"] == 0 else (r["k_last"] if off < r["len_last"] else r["k_last"] - 1)
+        steps.extend(r["occ0"] + k * S + off for k in range(kb, ke + 1))
+    return sorted(steps)
+
+
+def test_run_items_and_phases_match_brute_force():
+    rng = np.random.default_rng(2603)
+    checked = 0
+    for _ in range(3000):
+        S = int(rng.integers(1, 4000))
+        m0 = int(rng.integers(0, S))
+        ln = int(rng.integers(1, S + 1))
+        s_lo = int(rng.integers(0, 10**6))
+        s_hi = s_lo + int(rng.integers(0, 6000 if rng.random() < 0.8 else 40))
+        brute = [s for s in range(s_lo, s_hi + 1) if (s - m0) % S < ln]
+        r = run_iter(m0, ln, s_lo, s_hi, S)
+        if r is None or r["total"] <= 0:
+            assert not brute
+            continue
+        assert r["total"] == len(brute)
+        items = item_walk(r, m0, ln, S)
+        assert sorted(items) == list(range(r["total"]))
+        assert [items[t][0] for t in range(r["total"])] == brute      # item t is the t-th step of the run
+        assert all(m == s % S for s, m in items.values())             # and its phase index
+        assert phase_walk(r, ln, S) == brute
+        checked += len(brute)
+    assert checked > 10**6
