@@ -126,3 +126,36 @@ def test_run_items_and_phases_match_brute_force():
         assert phase_walk(r, ln, S) == brute
         checked += len(brute)
     assert checked > 10**6
+
+
+def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
+    """Phase form: for one phase offset the x of revolution k is
+    x0 + k S fs; the kernel visits k in [max(kb, floor(min(ka, kz)) - 1),
+    min(ke, ceil(max(ka, kz)) + 1)] with ka, kz = (x_lo - x0, x_hi - x0) /
+    (S fs) in FP32. Every revolution whose x (in float64) lies within the
+    tile's x range widened by M cells must be in that range, for both feed
+    directions."""
+    rng = np.random.default_rng(61)
+    for _ in range(20000):
+        S = int(rng.integers(1, 40000))
+        fs = 10.0 ** rng.uniform(-6.0, -1.0) * (1 if rng.random() < 0.5 else -1)
+        pitch = 10.0 ** rng.uniform(-3.3, -1.7)
+        txc = int(rng.integers(1, 1025))
+        M = int(rng.integers(1, 4))
+        kb, ke = int(rng.integers(0, 2)), int(rng.integers(0, 3000))
+        if ke < kb:
+            continue
+        rev64 = S * fs
+        x0 = rng.uniform(-2.0, 2.0) - rng.uniform(0.0, 1.0) * ke * rev64
+        x_lo, x_hi = -M * pitch, (txc + M) * pitch
+        rev = f32(S) * f32(fs)
+        inv_rev = f32(1.0) / rev
+        ka = (f32(x_lo) - f32(x0)) * inv_rev
+        kz = (f32(x_hi) - f32(x0)) * inv_rev
+        k0 = max(kb, int(np.floor(min(ka, kz))) - 1)
+        k1 = min(ke, int(np.ceil(max(ka, kz))) + 1)
+        ks = np.arange(kb, ke + 1)
+        xs = x0 + ks * rev64
+        over = ks[(xs >= x_lo) & (xs <= x_hi)]
+        ok = over.size == 0 or (over.min() >= k0 and over.max() <= k1)
+        assert ok, (S, fs, x0, over, k0, k1)
