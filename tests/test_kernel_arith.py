@@ -1,0 +1,94 @@
+"""Small pieces of the kernels' arithmetic modelled and checked on the CPU.
+
+- The order-preserving cell keys: a < b as floats exactly when key(a) <
+  key(b) as unsigned integers (so atomicMin on keys keeps the lowest height),
+  and the below-the-stock test of FP64 maps, key(z) < key(stock with both
+  zeros taken as -0), decides as z < stock does -- including z or the stock
+  being +0 or -0.
+- The double-float sums of the FP32 maps' roughness: Knuth's two-sum on the
+  high parts is exact and symmetric in its operands (every lane of a
+  butterfly reduction ends with the same pair), and a sum of many floats
+  kept as a pair is accurate far beyond float precision."""
+import numpy as np
+
+f32 = np.float32
+
+
+def enc64(z):
+    b = np.asarray(z, dtype=np.float64).view(np.uint64)
+    sign = (b >> np.uint64(63)) == 1
+    return np.where(sign, ~b, b | np.uint64(1 << 63))
+
+
+def enc32(z):
+    b = np.asarray(z, dtype=np.float32).view(np.uint32)
+    sign = (b >> np.uint32(31)) == 1
+    return np.where(sign, ~b, b | np.uint32(1 << 31))
+
+
+def stock_key(stock):
+    return enc64(np.where(stock == 0.0, -0.0, stock))
+
+
+def test_keys_preserve_order():
+    rng = np.random.default_rng(1)
+    a = np.concatenate([rng.normal(0, 1e3, 10**5), [0.0, -0.0, 1e-300, -1e-300, 5e-324, -5e-324]])
+    b = np.concatenate([rng.normal(0, 1e3, 10**5), [-0.0, 0.0, -1e-300, 1e-300, -5e-324, 5e-324]])
+    lt = a < b
+    eq = a == b
+    ka, kb = enc64(a), enc64(b)
+    # strict order agrees except that -0 and +0 compare equal as floats
+    both_zero = (a == 0) & (b == 0)
+    assert np.array_equal((ka < kb)[~both_zero], lt[~both_zero])
+    assert np.array_equal((ka == kb)[~both_zero], eq[~both_zero])
+    a32, b32 = a.astype(f32), b.astype(f32)
+    z32 = (a32 == 0) & (b32 == 0)
+    assert np.array_equal((enc32(a32) < enc32(b32))[~z32], (a32 < b32)[~z32])
+
+
+def test_below_the_stock_on_keys_equals_the_fp64_comparison():
+    rng = np.random.default_rng(2)
+    stocks = np.concatenate([rng.normal(0, 5.0, 200), [0.0, -0.0, 1.25, -0.5]])
+    for st in stocks:
+        z = np.concatenate([st + rng.normal(0, 1e-3, 2000), [st, 0.0, -0.0, np.nextafter(st, -np.inf),
+                                                             np.nextafter(st, np.inf)]])
+        assert np.array_equal(enc64(z) < stock_key(np.float64(st)), z < st), st
+
+
+def two_sum(a, b):
+    s = f32(a + b)
+    bb = f32(s - a)
+    e = f32(f32(a - f32(s - bb)) + f32(b - bb))
+    return s, e
+
+
+def df_add(a, b):
+    t, e = two_sum(a[0], b[0])
+    e = f32(e + f32(a[1] + b[1]))
+    hi = f32(t + e)
+    return (hi, f32(e - f32(hi - t)))
+
+
+def test_two_sum_exact_and_symmetric():
+    rng = np.random.default_rng(3)
+    for _ in range(20000):
+        a = f32(rng.normal(0, 10.0 ** rng.uniform(-6, 3)))
+        b = f32(rng.normal(0, 10.0 ** rng.uniform(-6, 3)))
+        s, e = two_sum(a, b)
+        assert np.float64(s) + np.float64(e) == np.float64(a) + np.float64(b)  # exact
+        assert two_sum(b, a) == (s, e)                                         # symmetric
+        p, q = (a, f32(0)), (b, f32(a * 1e-8))
+        assert df_add(p, q) == df_add(q, p)
+
+
+def test_double_float_sum_is_accurate():
+    rng = np.random.default_rng(4)
+    x = (rng.normal(-0.1, 0.002, 100_000)).astype(f32)
+    acc = (f32(0), f32(0))
+    for v in x:
+        acc = df_add(acc, (v, f32(0)))
+    got = np.float64(acc[0]) + np.float64(acc[1])
+    exact = float(np.sum(x.astype(np.float64)))  # float64 of float32 values: error ~1e-16 relative
+    assert abs(got - exact) <= 1e-12 * abs(exact), (got, exact)
+    naive = float(np.cumsum(x)[-1])               # plain float32 running sum for contrast
+    assert abs(naive - exact) > 1e3 * abs(got - exact)
