@@ -23,7 +23,14 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2603_28160_gb300", "csrc")
-CUDA_INC = "/usr/local/cuda/include"
+
+
+def cuda_include():
+    """The CUDA headers next to nvcc (CUDA_HOME, then nvcc on the PATH)."""
+    for root in (os.environ.get("CUDA_HOME"), os.path.dirname(os.path.dirname(shutil.which("nvcc") or "/x/x"))):
+        if root and os.path.exists(os.path.join(root, "include", "cuda_runtime.h")):
+            return os.path.join(root, "include")
+    return None
 
 SHIM = r"""
 #include <cuda_runtime.h>
@@ -50,13 +57,13 @@ extern "C" int shim_point_runs(const float* g, const float* fr, const int* fi, i
 
 @pytest.fixture(scope="module")
 def shim():
-    gxx = shutil.which("g++")
-    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+    gxx, inc = shutil.which("g++"), cuda_include()
+    if gxx is None or inc is None:
         pytest.skip("needs g++ and the CUDA headers")
     d = tempfile.mkdtemp()
     src, lib = os.path.join(d, "shim.cpp"), os.path.join(d, "shim.so")
     open(src, "w").write(SHIM)
-    subprocess.check_call([gxx, "-O2", "-shared", "-fPIC", "-I", CSRC, "-I", CUDA_INC, src, "-o", lib])
+    subprocess.check_call([gxx, "-O2", "-shared", "-fPIC", "-I", CSRC, "-I", inc, src, "-o", lib])
     L = C.CDLL(lib)
     L.shim_point_runs.restype = C.c_int
     yield L
