@@ -92,3 +92,27 @@ def test_double_float_sum_is_accurate():
     assert abs(got - exact) <= 1e-12 * abs(exact), (got, exact)
     naive = float(np.cumsum(x)[-1])               # plain float32 running sum for contrast
     assert abs(naive - exact) > 1e3 * abs(got - exact)
+
+
+def test_planner_sinusoids_equal_the_pose():
+    """The planner writes each coordinate of an edge point's pose,
+    cos(Theta_m) u + sin(Theta_m) v + w with Theta_m = phase0 + sense m dtheta,
+    as the sinusoid w + amp cos(dtheta (m - mph)) of the step's phase index,
+    amp = |(u, v)|, mph = sense (atan2(v, u) - phase0) / dtheta mod S; the
+    enumeration solves for its arcs. Both forms agree at every phase, for both
+    spindle senses."""
+    rng = np.random.default_rng(5)
+    for _ in range(500):
+        S = int(rng.choice([360, 720, 3600, 7200]))
+        dth = 2.0 * np.pi / S
+        sense = 1 if rng.random() < 0.5 else -1
+        phase0 = np.deg2rad(rng.uniform(-360.0, 360.0))
+        u, v, w = rng.normal(0.0, 3.0, 3)
+        amp = np.hypot(u, v)
+        mph = np.fmod(sense * (np.arctan2(v, u) - phase0) / dth, S)
+        mph = mph + S if mph < 0 else mph
+        m = np.arange(S)
+        th = phase0 + sense * m * dth
+        pose = np.cos(th) * u + np.sin(th) * v + w
+        sinus = w + amp * np.cos(dth * (m - mph))
+        assert np.abs(pose - sinus).max() <= 1e-9 * max(amp, 1.0)
