@@ -345,7 +345,7 @@ int orc_pose(const orc_tool* t, const orc_process* p, int64_t s, int K, int j,
 typedef struct {
     const orc_tool* t;
     const orc_process* p;
-    int tid, n_threads;
+    int64_t s_begin, s_end;  /* global time steps [s_begin, s_end) of this thread */
     double z_ref;
     double* H;
     uint8_t* flags;
@@ -382,26 +382,26 @@ static void* fsm_worker(void* arg) {
         for (int j = 0; j < E; ++j) tool_point(t, p, 1, K, j, q + 3 * (K * E + j));
     mat4 A = m_orientation(p);
     const double stock = map_stock(p);
-    for (int pass = job->tid; pass < p->n_passes; pass += job->n_threads) {
-        for (int64_t n = 0; n < p->steps_per_pass; ++n) {          /* time step */
-            mat4 T = step_matrix(t, p, &A, job->z_ref, 1, pass, n, 0);
-            for (int K = 0; K < N; ++K) {                           /* tooth */
-                for (int j = 0; j < E; ++j) {                       /* edge point */
-                    double wp[3], w[3];
-                    m_apply(&T, q + 3 * (K * E + j), wp);
-                    to_map_frame(p, wp, w);
-                    job->st.trajectory_points++;
-                    double cx = floor((w[0] - p->x0) / p->pitch);
-                    double cy = floor((w[1] - p->y0) / p->pitch);
-                    int inside = cx >= 0.0 && cx < (double)p->nx && cy >= 0.0 && cy < (double)p->ny;
-                    if (w[2] < stock && job->flags) flag_point(p, w[0], w[1], job->flags);
-                    if (!inside) continue;
-                    size_t cell = (size_t)cy * p->nx + (size_t)cx;
-                    job->st.landed++;
-                    job->hit[cell] = 1;
-                    if (w[2] < stock) job->st.cutting++;
-                    if (w[2] < job->H[cell]) job->H[cell] = w[2]; /* keep the lowest z */
-                }
+    for (int64_t s = job->s_begin; s < job->s_end; ++s) {          /* time step */
+        int pass = (int)(s / p->steps_per_pass);
+        int64_t n = s - (int64_t)pass * p->steps_per_pass;
+        mat4 T = step_matrix(t, p, &A, job->z_ref, 1, pass, n, 0);
+        for (int K = 0; K < N; ++K) {                               /* tooth */
+            for (int j = 0; j < E; ++j) {                           /* edge point */
+                double wp[3], w[3];
+                m_apply(&T, q + 3 * (K * E + j), wp);
+                to_map_frame(p, wp, w);
+                job->st.trajectory_points++;
+                double cx = floor((w[0] - p->x0) / p->pitch);
+                double cy = floor((w[1] - p->y0) / p->pitch);
+                int inside = cx >= 0.0 && cx < (double)p->nx && cy >= 0.0 && cy < (double)p->ny;
+                if (w[2] < stock && job->flags) flag_point(p, w[0], w[1], job->flags);
+                if (!inside) continue;
+                size_t cell = (size_t)cy * p->nx + (size_t)cx;
+                job->st.landed++;
+                job->hit[cell] = 1;
+                if (w[2] < stock) job->st.cutting++;
+                if (w[2] < job->H[cell]) job->H[cell] = w[2]; /* keep the lowest z */
             }
         }
     }
@@ -409,11 +409,41 @@ static void* fsm_worker(void* arg) {
     return NULL;
 }
 
+/* Merge of the threads' private maps over the cells [c_begin, c_end): the
+ * per-cell minimum is order-free, so the merged map is the single-thread
+ * map exactly; hit and boundary-tie marks are unions. */
+typedef struct {
+    fsm_job* jobs;
+    int n_threads;
+    size_t c_begin, c_end;
+} merge_job;
+
+static void* merge_worker(void* arg) {
+    merge_job* m = (merge_job*)arg;
+    fsm_job* j0 = &m->jobs[0];
+    for (int i = 1; i < m->n_threads; ++i) {
+        const fsm_job* ji = &m->jobs[i];
+        for (size_t c = m->c_begin; c < m->c_end; ++c) {
+            if (ji->H[c] < j0->H[c]) j0->H[c] = ji->H[c];
+            j0->hit[c] |= ji->hit[c];
+            if (j0->flags) j0->flags[c] |= ji->flags[c];
+        }
+    }
+    return NULL;
+}
+
+/* Contiguous share [lo, hi) of `total` items for part i of n. */
+static void share(int64_t total, int i, int n, int64_t* lo, int64_t* hi) {
+    *lo = total / n * i + (i < total % n ? i : total % n);
+    *hi = *lo + total / n + (i < total % n ? 1 : 0);
+}
+
 int orc_fsm(const orc_tool* t, const orc_process* p, double* H, uint8_t* flags,
             orc_stats* st, int n_threads) {
     if (!valid(t, p) || !H) return -1;
+    const int64_t steps = (int64_t)p->n_passes * p->steps_per_pass;
     if (n_threads < 1) n_threads = 1;
-    if (n_threads > p->n_passes) n_threads = p->n_passes;
+    if ((int64_t)n_threads > steps) n_threads = (int)steps;
     size_t cells = (size_t)p->nx * (size_t)p->ny;
     double z_ref = resolved_z_ref(t, p);
     fsm_job* jobs = (fsm_job*)calloc((size_t)n_threads, sizeof(fsm_job));
@@ -421,8 +451,7 @@ int orc_fsm(const orc_tool* t, const orc_process* p, double* H, uint8_t* flags,
     for (int i = 0; i < n_threads; ++i) {
         jobs[i].t = t;
         jobs[i].p = p;
-        jobs[i].tid = i;
-        jobs[i].n_threads = n_threads;
+        share(steps, i, n_threads, &jobs[i].s_begin, &jobs[i].s_end);
         jobs[i].z_ref = z_ref;
         jobs[i].H = (i == 0) ? H : (double*)malloc(sizeof(double) * cells);
         jobs[i].flags = flags ? (i == 0 ? flags : (uint8_t*)calloc(cells, 1)) : NULL;
@@ -433,15 +462,25 @@ int orc_fsm(const orc_tool* t, const orc_process* p, double* H, uint8_t* flags,
     for (int i = 1; i < n_threads; ++i) pthread_create(&th[i], NULL, fsm_worker, &jobs[i]);
     fsm_worker(&jobs[0]);
     for (int i = 1; i < n_threads; ++i) pthread_join(th[i], NULL);
+    if (n_threads > 1) {
+        merge_job* mj = (merge_job*)calloc((size_t)n_threads, sizeof(merge_job));
+        for (int i = 0; i < n_threads; ++i) {
+            int64_t lo, hi;
+            share((int64_t)cells, i, n_threads, &lo, &hi);
+            mj[i].jobs = jobs;
+            mj[i].n_threads = n_threads;
+            mj[i].c_begin = (size_t)lo;
+            mj[i].c_end = (size_t)hi;
+        }
+        for (int i = 1; i < n_threads; ++i) pthread_create(&th[i], NULL, merge_worker, &mj[i]);
+        merge_worker(&mj[0]);
+        for (int i = 1; i < n_threads; ++i) pthread_join(th[i], NULL);
+        free(mj);
+    }
     orc_stats total;
     memset(&total, 0, sizeof total);
     for (int i = 0; i < n_threads; ++i) {
         if (i > 0) {
-            for (size_t c = 0; c < cells; ++c) {
-                if (jobs[i].H[c] < H[c]) H[c] = jobs[i].H[c];
-                jobs[0].hit[c] |= jobs[i].hit[c];
-                if (flags) flags[c] |= jobs[i].flags[c];
-            }
             free(jobs[i].H);
             if (flags) free(jobs[i].flags);
         }

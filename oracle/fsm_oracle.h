@@ -142,8 +142,11 @@ int orc_pose(const orc_tool* t, const orc_process* p, int64_t s, int K, int j,
 /* The FSM: scatter every trajectory point into the height map H[ny][nx]
  * (row-major, initialised to stock_z) keeping the minimum z per cell.
  * flags (may be NULL) marks cells next to a point within 1e-12 mm of a
- * sampling boundary. n_threads > 1 splits the passes across threads, each
- * with a private map, merged by min (exact). Returns 0 or -1. */
+ * sampling boundary. n_threads > 1 splits the global time steps into
+ * n_threads contiguous ranges, each swept by one thread into a private map;
+ * the maps are merged by min (exact: the per-cell minimum does not depend on
+ * the order of the points), hit and tie marks by union, counts by sum.
+ * Returns 0 or -1. */
 int orc_fsm(const orc_tool* t, const orc_process* p, double* H,
             uint8_t* flags, orc_stats* st, int n_threads);
 
