@@ -170,16 +170,17 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def oracle_sample(fraction=1.0):
-    """Bounded sample for the CPU oracle: the four middle passes of the
-    workload (same tool, grid and path; a third of the tool path), or the
-    middle `fraction` of each of those passes (the spindle phase of the first
-    sampled step kept as in the full path)."""
+def oracle_sample(fraction=1.0, n_passes=4):
+    """Bounded sample for the CPU oracle: the n_passes middle passes of the
+    workload (same tool, grid and path), or the middle `fraction` of each of
+    those passes (the spindle phase of the first sampled step kept as in the
+    full path)."""
     from paper_2603_28160_gb300 import workloads as W
     w = workload("fp64")
     p = w.process
-    mid = p.n_passes // 2 - 2
-    p2 = p.replace(n_passes=4, pass_y0=p.pass_y0 + mid * p.ae)
+    n_passes = min(n_passes, p.n_passes)
+    mid = (p.n_passes - n_passes) // 2
+    p2 = p.replace(n_passes=n_passes, pass_y0=p.pass_y0 + mid * p.ae)
     if fraction < 1.0:
         n = max(1, int(p.steps_per_pass * fraction))
         start = (p.steps_per_pass - n) // 2
@@ -187,8 +188,8 @@ def oracle_sample(fraction=1.0):
         fs = w.tool.n_teeth * p.fz / round(360.0 / p.rot_step_deg)
         p2 = p2.replace(steps_per_pass=n, pass_x0=p.pass_x0 + start * fs,
                         phase0_deg=(p.phase0_deg + p.rot_sense * s_first * p.rot_step_deg) % 360.0)
-        return W.Workload(w.name + "_4passes_%.2f" % fraction, w.tool, p2)
-    return W.Workload(w.name + "_4passes", w.tool, p2)
+        return W.Workload(w.name + "_%dpasses_%.2f" % (n_passes, fraction), w.tool, p2)
+    return W.Workload(w.name + "_%dpasses" % n_passes, w.tool, p2)
 
 
 def run_oracle_step(sample, threads):
@@ -198,18 +199,58 @@ def run_oracle_step(sample, threads):
     return time.perf_counter() - t0, r.stats
 
 
+def host_cpu():
+    """Host core count and CPU model string (lscpu, else /proc/cpuinfo)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    model = v
+                    break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or platform.machine()
+
+
 def cpu_baseline():
-    sample = oracle_sample()
-    threads = min(os.cpu_count() or 1, sample.process.n_passes)
-    dt, st = run_oracle_step(sample, threads)
-    return {"value": st["cutting"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "4 of the 12 passes (middle ones) of the same workload, full grid; plain FP64 C oracle "
-                      "evaluating all %d trajectory points, one pass per thread; %.2f s wall"
-                      % (st["trajectory_points"], dt)}
+    """The oracle as it stands on the host cores: single-threaded on two
+    middle passes, and on every core over all twelve passes (the time steps
+    split into one contiguous range per thread, private maps merged by
+    minimum). The line's value is the all-core figure."""
+    nproc, model = host_cpu()
+    one = oracle_sample(n_passes=2)
+    dt1, st1 = run_oracle_step(one, 1)
+    full = oracle_sample(n_passes=workload("fp64").process.n_passes)
+    dta, sta = run_oracle_step(full, nproc)
+    v1, va = st1["cutting"] / dt1, sta["cutting"] / dta
+    return {"value": va, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": "all 12 passes of the same workload on %d threads (%.2f s wall, %d trajectory points); "
+                      "single thread: the 2 middle passes (%.2f s, %d trajectory points)"
+                      % (nproc, dta, sta["trajectory_points"], dt1, st1["trajectory_points"]),
+            "nproc": nproc, "cpu_model": model,
+            "threads_1": {"value": v1, "unit": UNIT, "seconds": dt1, "cutting": st1["cutting"],
+                          "trajectory_points": st1["trajectory_points"], "trajectory_points_per_s":
+                              st1["trajectory_points"] / dt1},
+            "threads_all": {"value": va, "unit": UNIT, "threads": nproc, "seconds": dta, "cutting": sta["cutting"],
+                            "trajectory_points": sta["trajectory_points"], "trajectory_points_per_s":
+                                sta["trajectory_points"] / dta}}
 
 
 def reference_arm(args):
-    """The FP64 CPU oracle as the reference arm (bounded sample per step)."""
+    """The FP64 CPU oracle as the reference arm, on every host core (bounded
+    sample per step)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1 and rank != 0:
@@ -218,7 +259,8 @@ def reference_arm(args):
     # (about a tenth of the time per step) so the whole run stays in minutes
     fraction = 1.0 if args.steps + args.warmup <= 40 else 0.1
     sample = oracle_sample(fraction)
-    threads = min(os.cpu_count() or 1, sample.process.n_passes)
+    nproc, model = host_cpu()
+    threads = nproc
     for _ in range(args.warmup):
         run_oracle_step(sample, threads)
     times, cut = [], 0
@@ -228,14 +270,14 @@ def reference_arm(args):
         cut = st["cutting"]
     ms = 1e3 * sum(times) / len(times)
     value = cut / (ms / 1e3)
+    what = "4 of the 12 passes of the workload per step" + ("" if fraction == 1.0 else ", the middle tenth of each pass")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": config(workload("fp64"), {"sample": "4 middle passes of 12" + (
                 "" if fraction == 1.0 else ", middle tenth of each"), "oracle_threads": threads}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "4 of the 12 passes of the workload per step" + (
-                                 "" if fraction == 1.0 else ", the middle tenth of each pass")},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": what,
+                             "nproc": nproc, "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
