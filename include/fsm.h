@@ -180,7 +180,19 @@ typedef struct {
  *                     [3] shared-memory atomic updates issued.
  *   sweep_events      NULL or two cudaEvent_t (as void*) recorded on the
  *                     stream just before and just after the sweep launch(es),
- *                     to time the sweep kernel alone. */
+ *                     to time the sweep kernel alone.
+ *   sweep_form        how each (pass, tooth, 32-point group) task of the
+ *                     sweep walks the steps of its time window (both forms
+ *                     evaluate exactly the same points with the same
+ *                     arithmetic, so the map does not depend on the choice):
+ *                     FSM_FORM_AUTO (0): chosen per task by the library;
+ *                     FSM_FORM_ITEM (1): step by step;
+ *                     FSM_FORM_PHASE (2): spindle phase by phase, visiting
+ *                     only the revolutions of each phase that can reach the
+ *                     tile.
+ *   d_form_tasks      NULL or device int64_t[2] the sweep ADDS to: tasks
+ *                     walked in the item form [0] and in the phase form [1].
+ * Fields after sweep_events were added later; zero them for the defaults. */
 typedef struct {
     int32_t tile_x;
     int32_t tile_y;
@@ -188,7 +200,12 @@ typedef struct {
     int32_t ctas_per_sm;
     int64_t* d_counters;
     void* sweep_events[2];
+    int32_t sweep_form;
+    int32_t reserved;
+    int64_t* d_form_tasks;
 } fsm_predict_opts;
+
+enum { FSM_FORM_AUTO = 0, FSM_FORM_ITEM = 1, FSM_FORM_PHASE = 2 };
 
 /* Areal (ISO 25178-2) and line (ISO 4287) roughness of one height map,
  * Section 4.1.2. Mean plane = arithmetic mean; no form removal, no S/L
@@ -211,7 +228,11 @@ typedef struct {
 /* ---------------------------------------------------------------------- */
 
 /* Create a context bound to CUDA device `device`. Fails with FSM_E_CUDA if
- * the device cannot be used (no GPU, or the library was not built for it). */
+ * the device cannot be used (no GPU, or the library was not built for it).
+ * Every entry point taking a context makes its device current for the call
+ * and restores the calling thread's current device before returning. A
+ * context belongs to the device's CUDA primary context as it was when the
+ * context was created: after cudaDeviceReset, destroy and recreate it. */
 fsm_status fsm_create_context(int device, fsm_ctx** out);
 fsm_status fsm_destroy_context(fsm_ctx* ctx);
 
@@ -307,8 +328,11 @@ fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision,
  * device memory on every GPU that loads it, until the process exits.
  *   Limit: nx * ny <= 536870912 (2^29) cells; larger maps fail with
  *          FSM_E_INVALID and a message saying so.
- *   The first call on a device looks the array up on that device (with it
- *   made current); make that first call before any stream capture.
+ *   The first call on a context looks the array's device address up on
+ *   the context's device (with it made current) and keeps it in the
+ *   context; make that first call before any stream capture. (After a
+ *   cudaDeviceReset the address may change: recreate the context, as for
+ *   every other entry point.)
  *   All calls on a device share the one array: calls whose kernels overlap on
  *   the GPU (e.g. on two streams) race and give wrong results; order them on
  *   one stream or synchronise between them. The array keeps the last call's
@@ -382,7 +406,14 @@ fsm_status fsm_batch_destroy(fsm_ctx* ctx, fsm_batch* batch);
  * memory they need (height map + tables + scratch) fits in budget_bytes;
  * admitted requests are batched into launches on n_streams streams as they
  * arrive, so work of several batches overlaps on the device. One server per
- * context. */
+ * context. Device-resident state kept across requests: planned tool tables
+ * (edge points, phase table, group bounds) cached by every input they depend
+ * on -- the tool, ap, lead, tilt, step angle, start phase, spindle sense and
+ * surface kind (plus fz for round inserts) -- in up to 1/16 of the budget
+ * (at most 1 GiB), evicted least recently used first, so a repeated tool and
+ * set-up skips the table build; freed device memory stays in the
+ * stream-ordered pool for the next admissions; finished maps stay on the
+ * device until released. */
 fsm_status fsm_server_start(fsm_ctx* ctx, size_t budget_bytes, int32_t n_streams,
                             int32_t max_batch);
 fsm_status fsm_server_stop(fsm_ctx* ctx);
@@ -404,11 +435,55 @@ typedef struct {
 } fsm_result;
 
 /* Wait up to timeout_ms (0 = just check, <0 = forever) for a request.
- * Returns FSM_OK with *out filled, FSM_PENDING, or an error. */
+ * Returns FSM_OK with *out filled, FSM_PENDING (timeout_ms == 0),
+ * FSM_E_TIMEOUT (still running after timeout_ms > 0; the request carries
+ * on), FSM_E_CANCELLED (see fsm_cancel), or the request's failure status
+ * (e.g. FSM_E_NOMEM when its batch could not get device memory). */
 fsm_status fsm_poll(fsm_ctx* ctx, uint64_t ticket, int32_t timeout_ms, fsm_result* out);
 
-/* Return a finished request's device memory to the admission budget. */
+/* Cancel a request. A request still waiting for admission is removed and
+ * never reaches the device; one already admitted finishes its batch (kernels
+ * in flight are not interrupted) and its map is freed at completion. Either
+ * way fsm_poll then returns FSM_E_CANCELLED and fsm_release_result forgets
+ * the ticket. FSM_E_STATE if the request had already finished. */
+fsm_status fsm_cancel(fsm_ctx* ctx, uint64_t ticket);
+
+/* Return a finished (or cancelled) request's device memory to the admission
+ * budget and forget its ticket. */
 fsm_status fsm_release_result(fsm_ctx* ctx, uint64_t ticket);
+
+/* Counters of a running server (no counterpart in the paper). */
+typedef struct {
+    uint64_t submitted, completed, cancelled, failed, batches;
+    uint64_t table_hits, table_misses;   /* requests that found / did not find cached tables */
+    uint64_t bytes_in_use, bytes_peak;   /* admission budget in use (maps, tables, scratch) */
+    uint64_t table_bytes;                /* of which cached tables */
+    int32_t queue_depth, queue_peak;     /* requests waiting for admission */
+    int32_t tables_cached, reserved;
+} fsm_server_info;
+fsm_status fsm_server_stats(fsm_ctx* ctx, fsm_server_info* out);
+
+/* Device-time interval of one served batch: recorded by CUDA events on its
+ * slot's stream just before its first kernel and just after its roughness
+ * copy, in ms from an origin taken when the server started. Intervals of two
+ * slots that intersect show their batches were on the device at the same
+ * time. */
+typedef struct {
+    int32_t slot, n_requests;
+    double t_start_ms, t_end_ms;
+} fsm_batch_interval;
+
+/* Copy the most recent min(capacity, kept) completed batches (oldest first;
+ * the server keeps the last 4096) into out; *n = number copied. */
+fsm_status fsm_server_batches(fsm_ctx* ctx, fsm_batch_interval* out, int32_t capacity, int32_t* n);
+
+/* Fault injection for testing the server's failure path (host side only: no
+ * device fault is involved): the next `count` device allocations of request
+ * height maps report failure without calling the allocator. The batch that
+ * contains such a request fails as a whole -- its requests end with
+ * FSM_E_NOMEM, their memory goes back to the budget -- and the server keeps
+ * serving later requests. count = 0 clears it. */
+fsm_status fsm_server_inject_alloc_failures(fsm_ctx* ctx, int32_t count);
 
 #ifdef __cplusplus
 }

@@ -216,6 +216,11 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     return off;
 }
 
+size_t surface_table_bytes(const fsm_tool_desc& t, const fsm_process_desc& p) {
+    Surface s;
+    return fill_surface(t, p, pick_shape(p, nullptr), &s, nullptr);
+}
+
 size_t surface_overhead_bytes(const fsm_tool_desc& t, const fsm_process_desc& p) {
     Surface s;
     const Shape sh = pick_shape(p, nullptr);
@@ -237,7 +242,8 @@ fsm_status fsm_create_context(int device, fsm_ctx** out) {
     cudaError_t e = cudaGetDeviceCount(&n);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
     if (device < 0 || device >= n) return fail(FSM_E_INVALID, "no such CUDA device");
-    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
     if (prop.major * 10 + prop.minor < 100)
@@ -365,8 +371,15 @@ fsm_status check_fp32_band(const fsm_tool_desc& t, const fsm_process_desc& p, co
     return FSM_OK;
 }
 
+fsm_status check_opts(const fsm_predict_opts* o) {
+    if (o && o->sweep_form != FSM_FORM_AUTO && o->sweep_form != FSM_FORM_ITEM && o->sweep_form != FSM_FORM_PHASE)
+        return fail(FSM_E_INVALID, "sweep_form must be FSM_FORM_AUTO, FSM_FORM_ITEM or FSM_FORM_PHASE");
+    return FSM_OK;
+}
+
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st) {
+    if (fsm_status rc0 = check_opts(opts)) return rc0;
     const fsm_process_desc* self = &p;
     Shape sh = pick_shape(p, opts, &self, 1, ctx->sm_count);
     fsm_predict_opts tuned_opts;
@@ -397,6 +410,8 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (tables)");
     fill_surface(t, p, sh, &s, (char*)ws + surf_bytes);
     s.heights = d_heights;
+    s.form = opts ? opts->sweep_form : FSM_FORM_AUTO;
+    s.form_tasks = opts ? (unsigned long long*)opts->d_form_tasks : nullptr;
     Surface* d_s = (Surface*)ws;
     if ((e = launch_plan(d_s, 1, &s, 0, ctx->sm_count, st)) != cudaSuccess) {
         cudaFreeAsync(ws, st);
@@ -409,7 +424,7 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     // tiles are handed out by a device counter that the planning kernel zeroed
     e = launch_sweep_shaped(p.precision, d_s, 1, nullptr, tiles, s.tile_queue,
                             opts ? (long long*)opts->d_counters : nullptr, grid, sh.threads, smem, st,
-                            phase_form_pays(t, p, sh.tile_x));
+                            phase_form_pays(t, p, sh.tile_x, s.form));
     if (opts && opts->sweep_events[1]) cudaEventRecord((cudaEvent_t)opts->sweep_events[1], st);
     cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
@@ -470,8 +485,9 @@ fsm_status fsm_predict_surface(fsm_ctx* ctx, const fsm_tool* tool, const fsm_pro
                                const fsm_predict_opts* opts, void* stream) {
     if (!ctx || !tool || !proc) return fail(FSM_E_INVALID, "ctx/tool/proc is NULL");
     if (!d_heights) return fail(FSM_E_INVALID, "d_heights is NULL");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     return fsm::predict_one(ctx, tool->d, proc->d, d_heights, opts, (cudaStream_t)stream);
 }
 
@@ -485,8 +501,9 @@ fsm_status fsm_predict_trajectory(fsm_ctx* ctx, const fsm_tool* tool, const fsm_
                                   fsm_traj_point* d_out, int64_t capacity, void* stream) {
     if (!ctx || !tool || !proc) return fail(FSM_E_INVALID, "ctx/tool/proc is NULL");
     if (!d_out) return fail(FSM_E_INVALID, "d_out is NULL");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     return fsm::trajectory_one(ctx, tool->d, proc->d, d_out, capacity, (cudaStream_t)stream);
 }
 
@@ -497,8 +514,9 @@ fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision,
     if (nx < 1 || ny < 1) return fail(FSM_E_INVALID, "nx, ny must be >= 1");
     if (n_rows < 0 || n_cols < 0 || n_rows > FSM_MAX_PROFILES || n_cols > FSM_MAX_PROFILES)
         return fail(FSM_E_INVALID, "0 <= n_rows, n_cols <= 16");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     return fsm::roughness_one(ctx, d_heights, precision, nx, ny, n_rows, n_cols, d_out, (cudaStream_t)stream);
 }
 
@@ -507,8 +525,9 @@ fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision,
 extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc, void* d_heights,
                                    int32_t max_candidates, fsm_predict_opts* best, float* best_ms, void* stream) {
     if (!ctx || !tool || !proc || !d_heights || !best) return fail(FSM_E_INVALID, "NULL argument");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     cudaStream_t st = (cudaStream_t)stream;
     // candidates (tile_x, tile_y, threads): wide, short tiles shared by many
     // warps first (they amortise the enumeration and keep x ranges tight)

@@ -40,8 +40,11 @@ struct BatchLayout {
 // the buffer (NULL to size only).
 fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
                        const fsm_process_desc* const* procs, void* const* heights,
-                       fsm_roughness_out* d_rough, const fsm_predict_opts* opts, char* base, BatchLayout* L) {
+                       fsm_roughness_out* d_rough, const fsm_predict_opts* opts, char* base, BatchLayout* L,
+                       const TableRef* trefs = nullptr) {
     if (n < 1) return fail(FSM_E_INVALID, "batch size must be >= 1");
+    if (fsm_status rc0 = check_opts(opts)) return rc0;
+    const int form = opts ? opts->sweep_form : FSM_FORM_AUTO;
     std::vector<int> order;
     order.reserve(n);
     for (int grp = 0; grp < 2; ++grp)
@@ -62,7 +65,7 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     L->rough = d_rough != nullptr;
     for (int i = 0; i < n; ++i) {
         const bool f64 = procs[i]->precision == FSM_FP64;
-        if (phase_form_pays(*tools[i], *procs[i], f64 ? L->sh64.tile_x : L->sh32.tile_x))
+        if (phase_form_pays(*tools[i], *procs[i], f64 ? L->sh64.tile_x : L->sh32.tile_x, form))
             (f64 ? L->phase_form64 : L->phase_form32) = true;
     }
     L->counters = opts ? (long long*)opts->d_counters : nullptr;
@@ -84,7 +87,8 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
         const Shape& sh = procs[i]->precision == FSM_FP64 ? L->sh64 : L->sh32;
         if ((rc = check_fp32_band(*tools[i], *procs[i], sh)) != FSM_OK) return rc;
         toff[k] = tables;
-        tables += fill_surface(*tools[i], *procs[i], sh, &hs[k], nullptr);
+        const size_t tb = fill_surface(*tools[i], *procs[i], sh, &hs[k], nullptr);
+        if (!trefs || !trefs[i].base) tables += tb;  // tables held elsewhere take no batch space
         L->plan_work = std::max(L->plan_work, hs[k].n_teeth * hs[k].E + hs[k].S);
     }
     std::vector<int> tb64(L->n64 + 1, 0), tb32(L->n32 + 1, 0), cb64(L->n64 + 1, 0), cb32(L->n32 + 1, 0);
@@ -128,8 +132,15 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     for (int k = 0; k < n; ++k) {
         const int i = order[k];
         const Shape& sh = procs[i]->precision == FSM_FP64 ? L->sh64 : L->sh32;
-        fill_surface(*tools[i], *procs[i], sh, &hs[k], base + L->off_tables + toff[k]);
+        const bool held = trefs && trefs[i].base;
+        fill_surface(*tools[i], *procs[i], sh, &hs[k], held ? trefs[i].base : base + L->off_tables + toff[k]);
+        if (held) {
+            hs[k].cached = trefs[i].ready ? 1 : 0;
+            hs[k].tile_queue = nullptr;  // the batch's own queue hands out tiles
+        }
         hs[k].heights = heights[i];
+        hs[k].form = form;
+        hs[k].form_tasks = opts ? (unsigned long long*)opts->d_form_tasks : nullptr;
         RoughJob& jb = jobs[k];
         jb.h = heights[i];
         jb.nx = hs[k].nx;
@@ -204,14 +215,18 @@ static fsm_status unpack(int n, const fsm_tool* const* tools, const fsm_process*
 fsm_status predict_batch_descs(fsm_ctx* ctx, int n, const fsm_tool_desc* const* td,
                                const fsm_process_desc* const* pd, void* const* d_heights,
                                fsm_roughness_out* d_rough, const fsm_predict_opts* opts, cudaStream_t st,
-                               PinnedSlot* slot) {
+                               PinnedSlot* slot, const TableRef* trefs) {
     BatchLayout L;
-    fsm_status rc = build_batch(ctx, n, td, pd, d_heights, d_rough, opts, nullptr, &L);
+    fsm_status rc = build_batch(ctx, n, td, pd, d_heights, d_rough, opts, nullptr, &L, trefs);
     if (rc != FSM_OK) return rc;
     char* ws = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&ws, L.total, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (batch)");
-    rc = build_batch(ctx, n, td, pd, d_heights, d_rough, opts, ws, &L);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(FSM_E_NOMEM, "cudaMallocAsync (batch): out of memory")
+                                              : cuda_fail(e, "cudaMallocAsync (batch)");
+    }
+    rc = build_batch(ctx, n, td, pd, d_heights, d_rough, opts, ws, &L, trefs);
     if (rc == FSM_OK) {
         // stage the image in pinned memory so the copy does not block the host
         if (slot && slot->ensure(L.blob.size()) == cudaSuccess) {
@@ -247,8 +262,9 @@ fsm_status fsm_predict_batch(fsm_ctx* ctx, int32_t n, const fsm_tool* const* too
     std::vector<const fsm_process_desc*> pd;
     fsm_status rc = unpack(n, tools, procs, d_heights, &td, &pd);
     if (rc != FSM_OK) return rc;
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     return predict_batch_descs(ctx, n, td.data(), pd.data(), d_heights, d_rough, opts, (cudaStream_t)stream,
                                nullptr);
 }
@@ -261,8 +277,9 @@ fsm_status fsm_batch_create(fsm_ctx* ctx, int32_t n, const fsm_tool* const* tool
     std::vector<const fsm_process_desc*> pd;
     fsm_status rc = unpack(n, tools, procs, d_heights, &td, &pd);
     if (rc != FSM_OK) return rc;
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     fsm_batch* b = new fsm_batch();
     rc = build_batch(ctx, n, td.data(), pd.data(), d_heights, d_rough, opts, nullptr, &b->L);
     if (rc != FSM_OK) {
@@ -290,12 +307,14 @@ fsm_status fsm_batch_create(fsm_ctx* ctx, int32_t n, const fsm_tool* const* tool
 
 fsm_status fsm_batch_run(fsm_ctx* ctx, fsm_batch* batch, void* stream) {
     if (!ctx || !batch) return fail(FSM_E_INVALID, "ctx/batch is NULL");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
     return run_batch(ctx, batch->L, batch->d_buf, (cudaStream_t)stream);
 }
 
 fsm_status fsm_batch_destroy(fsm_ctx* ctx, fsm_batch* batch) {
     if (!ctx || !batch) return fail(FSM_E_INVALID, "ctx/batch is NULL");
-    cudaSetDevice(ctx->device);
+    DeviceGuard dev_guard(ctx->device);
     cudaError_t e = cudaFree(batch->d_buf);
     delete batch;
     return e == cudaSuccess ? FSM_OK : cuda_fail(e, "cudaFree (batch)");

@@ -56,6 +56,9 @@ struct Surface {
     double wall_y;
     // ---- launch geometry (inputs) ----
     int32_t tile_x, tile_y, ntx, nty;
+    int32_t form;             // FSM_FORM_* of the sweep's phase 2
+    int32_t cached;           // tables and group bounds already built (a server's table cache)
+    unsigned long long* form_tasks;  // NULL or [2]: tasks walked in the item / phase form
     // ---- tables (device pointers, inputs) ----
     float4* tool32;   // [N*E][4]: (ux,vx,wx,uz) (uy,vy,wy,vz) (wz,amp_y,mph_y,amp_z) (mph_z,amp_x,mph_x,0)
     double* tool64;   // [9][N*E]: ux uy uz vx vy vz wx wy wz

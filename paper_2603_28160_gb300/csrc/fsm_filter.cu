@@ -284,8 +284,9 @@ extern "C" fsm_status fsm_filter(fsm_ctx* ctx, const void* d_heights, int32_t pr
         return fail(FSM_E_INVALID, "filter cutoffs must be finite and >= 0");
     const double hs = lambda_s / pitch, hc = lambda_c / pitch;
     if (hs > kMaxHalfWidth || hc > kMaxHalfWidth) return fail(FSM_E_INVALID, "lambda / pitch must be <= 4096");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
     cudaStream_t st = (cudaStream_t)stream;
     const int R = precision == FSM_FP32 ? kR32 : kR64;
     Weights w[2];

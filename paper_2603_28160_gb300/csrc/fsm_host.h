@@ -32,6 +32,8 @@ struct fsm_ctx {
     std::map<std::string, std::array<int, 4>> tuned;
     // resident sweep CTAs per SM: (precision, threads, shared bytes) -> count
     std::map<std::array<long long, 3>, int> occupancy;
+    // device address of the allocation-free roughness scratch (first use)
+    char* noalloc_scratch = nullptr;
 };
 
 namespace fsm {
@@ -67,6 +69,30 @@ struct PinnedSlot {
     }
 };
 
+// Makes ctx's device current for the duration of an entry point and gives
+// the calling thread its previous current device back on every return, so a
+// host thread that drives several GPUs keeps its own choice of device.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != device) {
+            err = cudaSetDevice(device);
+            changed = err == cudaSuccess && prev >= 0;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 fsm_status fail(fsm_status st, const std::string& msg);
 fsm_status cuda_fail(cudaError_t e, const char* what);
 
@@ -86,6 +112,8 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
 size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh, Surface* s,
                     char* base);
 fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* smem, int* blocks_per_sm);
+// Validate the caller's prediction overrides (NULL = defaults).
+fsm_status check_opts(const fsm_predict_opts* o);
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st);
 fsm_status check_fp32_band(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh);
@@ -97,11 +125,24 @@ fsm_status roughness_one(fsm_ctx* ctx, const void* d_h, int precision, int nx, i
 // Device bytes one surface needs beyond its height map (tables + scratch).
 size_t surface_overhead_bytes(const fsm_tool_desc& t, const fsm_process_desc& p);
 
+// Device tables of one surface held outside a batch (a server's table
+// cache): `base` is laid out as fill_surface lays out a surface's tables;
+// `ready` says they were built by an earlier, completed launch (the planning
+// kernels then skip them), else this launch builds them there.
+struct TableRef {
+    char* base = nullptr;
+    bool ready = false;
+};
+
 // One-shot batch on stream-ordered scratch; `slot` (optional) stages the
-// upload in pinned memory.
+// upload in pinned memory; `trefs` (optional, one per surface) places
+// surfaces' tables outside the batch's scratch.
 fsm_status predict_batch_descs(fsm_ctx* ctx, int n, const fsm_tool_desc* const* td,
                                const fsm_process_desc* const* pd, void* const* d_heights,
                                fsm_roughness_out* d_rough, const fsm_predict_opts* opts, cudaStream_t st,
-                               PinnedSlot* slot);
+                               PinnedSlot* slot, const TableRef* trefs = nullptr);
+
+// Bytes of a surface's device tables (the layout fill_surface gives).
+size_t surface_table_bytes(const fsm_tool_desc& t, const fsm_process_desc& p);
 
 }  // namespace fsm

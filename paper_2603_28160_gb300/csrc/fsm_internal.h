@@ -37,7 +37,9 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
 // phase form, and the per-task choice keeps runs of few revolutions item by
 // item (ball raster FP64 4.55 -> 3.57 ms with 512x32 tiles, 8 mm floor
 // 79.6 -> 55.0 ms).
-inline bool phase_form_pays(const fsm_tool_desc& t, const fsm_process_desc& p, int tile_x) {
+inline bool phase_form_pays(const fsm_tool_desc& t, const fsm_process_desc& p, int tile_x, int form = 0) {
+    if (form == FSM_FORM_PHASE) return true;
+    if (form == FSM_FORM_ITEM) return false;
     if (p.precision == FSM_FP64) return true;
     const double feeds = (double)tile_x * p.pitch / ((double)t.n_teeth * p.fz);
     return feeds >= 3.0;

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
     if (sidx >= n) return;
     const Surface& sf = use_one ? one : surfs[sidx];
     if (use_one && blockIdx.y == 0 && threadIdx.x == 0) surfs[sidx] = one;
+    if (sf.cached) return;  // tables built by an earlier launch and kept on the device
     __shared__ double A[9];
     __shared__ double kap[2];
     __shared__ double run_c[2];                  // runout offset (x, y)
@@ -242,11 +243,17 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
     const int N = sf->n_teeth, E = sf->E, S = sf->S;
     if (tid == 0) {
         if (sf->tile_queue) *sf->tile_queue = 0;
+        // cached tables keep the reduction of the launch that built them in part 0
         double zlo = 1e300, rx = 0.0, ry = 0.0;
-        for (int q = 0; q < parts; ++q) {
+        for (int q = 0; q < (sf->cached ? 1 : parts); ++q) {
             zlo = fmin(zlo, sf->plan_part[4 * q]);
             rx = fmax(rx, sf->plan_part[4 * q + 1]);
             ry = fmax(ry, sf->plan_part[4 * q + 2]);
+        }
+        if (!sf->cached) {
+            sf->plan_part[0] = zlo;
+            sf->plan_part[1] = rx;
+            sf->plan_part[2] = ry;
         }
         const double dth = deg2rad(sf->rot_step_deg);
         double zr = sf->stock_z - sf->ap - zlo;  // workpiece height of the tool reference
@@ -283,7 +290,10 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
     // group): the y range of the points over the phases in which they are
     // below the stock (the tile-independent z limit of the enumeration), and
     // their lowest z. A group outside a tile's y band has no runs there.
+    // (Cached tables keep theirs: the limit, stock - z_ref, is ap plus the
+    // tables' lowest z, a function of the cached inputs.)
     __syncthreads();
+    if (sf->cached) return;
     const int G = (E + 31) / 32;
     const float zhi = (float)(sf->stock - sf->z_ref) + kMarginMm;
     const float fS = (float)S;
@@ -1131,21 +1141,25 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             AmbQueue* aq = FP64 ? nullptr : aqs + warp;
             // runs that come back for many revolutions share their per-phase
             // work (phase form); others are walked item by item
-            if constexpr (!kPhases) {
-                sweep_items<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
-                __syncwarp();
-                continue;
+            bool by_phase = false;
+            if constexpr (kPhases) {
+                if (sf.form == FSM_FORM_PHASE) {
+                    by_phase = true;
+                } else if (sf.form != FSM_FORM_ITEM) {
+                    int tot = 0, phases = 0;
+                    for (int a = 0; a < ws.n[lane]; ++a) {
+                        tot += rec_total(ws.run[lane][a]);
+                        phases += ws.run[lane][a].len;
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                        phases += __shfl_xor_sync(0xffffffffu, phases, o);
+                    }
+                    by_phase = phase_form_task<FP64>(tot, phases);
+                }
             }
-            int tot = 0, phases = 0;
-            for (int a = 0; a < ws.n[lane]; ++a) {
-                tot += rec_total(ws.run[lane][a]);
-                phases += ws.run[lane][a].len;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                phases += __shfl_xor_sync(0xffffffffu, phases, o);
-            }
-            if (phase_form_task<FP64>(tot, phases))
+            if (sf.form_tasks && lane == 0) atomicAdd(sf.form_tasks + (by_phase ? 1 : 0), 1ull);
+            if (by_phase)
                 sweep_phases<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
             else
                 sweep_items<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
@@ -1986,26 +2000,22 @@ constexpr size_t kNoAllocBytes = 512 + 7 * sizeof(double) * kNoAllocChunks;  // 
 // One per device that loads the library, kept until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the array, looked up once per device with that device
-// current (in host code the symbol names a host-side stand-in, not memory
-// the GPU can use).
-static char* noalloc_scratch(int device, cudaError_t* err) {
-    constexpr int kMaxDevices = 64;
-    static std::mutex mu;
-    static char* addr[kMaxDevices] = {};
-    if (device < 0 || device >= kMaxDevices) {
-        *err = cudaErrorInvalidDevice;
-        return nullptr;
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[device]) {
+// Device address of the array on ctx's device, looked up on the context's
+// first call with that device current and kept in the context (in host code
+// the symbol names a host-side stand-in, not memory the GPU can use). A
+// context lives inside one CUDA primary context of its device: after a
+// cudaDeviceReset the library's contexts must be recreated, which also
+// repeats this look-up.
+static char* noalloc_scratch(fsm_ctx* ctx, cudaError_t* err) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->noalloc_scratch) {
         void* p = nullptr;
         *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (*err != cudaSuccess) return nullptr;
-        addr[device] = (char*)p;
+        ctx->noalloc_scratch = (char*)p;
     }
     *err = cudaSuccess;
-    return addr[device];
+    return ctx->noalloc_scratch;
 }
 
 }  // namespace fsm
@@ -2023,9 +2033,10 @@ extern "C" fsm_status fsm_roughness_noalloc(fsm_ctx* ctx, const void* d_heights,
     if (n > kNoAllocMaxCells)
         return fail(FSM_E_INVALID, "fsm_roughness_noalloc handles at most 2^29 cells (" +
                                        std::to_string(kNoAllocMaxCells) + "); this map has " + std::to_string(n));
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-    char* ws = noalloc_scratch(ctx->device, &e);
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    cudaError_t e = cudaSuccess;
+    char* ws = noalloc_scratch(ctx, &e);
     if (!ws) return cuda_fail(e, "cudaGetSymbolAddress (no-alloc scratch)");
     RoughJob jb;
     jb.h = d_heights;

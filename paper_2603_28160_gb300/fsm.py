@@ -47,7 +47,11 @@ class ProcessDesc(C.Structure):
 
 class PredictOpts(C.Structure):
     _fields_ = [("tile_x", C.c_int32), ("tile_y", C.c_int32), ("block_threads", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("d_counters", C.c_void_p), ("sweep_events", C.c_void_p * 2)]
+                ("ctas_per_sm", C.c_int32), ("d_counters", C.c_void_p), ("sweep_events", C.c_void_p * 2),
+                ("sweep_form", C.c_int32), ("reserved", C.c_int32), ("d_form_tasks", C.c_void_p)]
+
+
+FORMS = {"auto": 0, "item": 1, "phase": 2}
 
 
 class RoughnessOut(C.Structure):
@@ -64,6 +68,19 @@ class Result(C.Structure):
     _fields_ = [("d_heights", C.c_void_p), ("precision", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
                 ("status", C.c_int32), ("rough", RoughnessOut), ("queue_s", C.c_double),
                 ("latency_s", C.c_double)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("cancelled", C.c_uint64),
+                ("failed", C.c_uint64), ("batches", C.c_uint64), ("table_hits", C.c_uint64),
+                ("table_misses", C.c_uint64), ("bytes_in_use", C.c_uint64), ("bytes_peak", C.c_uint64),
+                ("table_bytes", C.c_uint64), ("queue_depth", C.c_int32), ("queue_peak", C.c_int32),
+                ("tables_cached", C.c_int32), ("reserved", C.c_int32)]
+
+
+class BatchInterval(C.Structure):
+    _fields_ = [("slot", C.c_int32), ("n_requests", C.c_int32), ("t_start_ms", C.c_double),
+                ("t_end_ms", C.c_double)]
 
 
 ROUGH_BYTES = C.sizeof(RoughnessOut)
@@ -92,6 +109,10 @@ SIGNATURES = {
     "fsm_submit": [_P, _P, _P, C.POINTER(C.c_uint64)],
     "fsm_poll": [_P, C.c_uint64, C.c_int32, C.POINTER(Result)],
     "fsm_release_result": [_P, C.c_uint64],
+    "fsm_cancel": [_P, C.c_uint64],
+    "fsm_server_stats": [_P, C.POINTER(ServerInfo)],
+    "fsm_server_batches": [_P, C.POINTER(BatchInterval), C.c_int32, C.POINTER(C.c_int32)],
+    "fsm_server_inject_alloc_failures": [_P, C.c_int32],
     "fsm_predict_trajectory": [_P, _P, _P, _P, C.c_int64, _P],
     "fsm_trajectory_records": [_P, _P, C.POINTER(C.c_int64)],
     "fsm_filter": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
@@ -235,10 +256,16 @@ class Context:
 
     # -- single surface ---------------------------------------------------
     @staticmethod
-    def _opts(tile=None, threads=None, counters=None, events=None, ctas_per_sm=None) -> Optional[PredictOpts]:
-        if tile is None and threads is None and counters is None and events is None and ctas_per_sm is None:
+    def _opts(tile=None, threads=None, counters=None, events=None, ctas_per_sm=None, form=None,
+              form_tasks=None) -> Optional[PredictOpts]:
+        if (tile is None and threads is None and counters is None and events is None and ctas_per_sm is None
+                and form is None and form_tasks is None):
             return None
         o = PredictOpts()
+        if form is not None:
+            o.sweep_form = FORMS[form]
+        if form_tasks is not None:  # CUDA int64 tensor of 2: tasks in the item and the phase form
+            o.d_form_tasks = form_tasks.data_ptr()
         if tile is not None:
             o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
         if threads is not None:
@@ -253,10 +280,11 @@ class Context:
         return o
 
     def predict_surface(self, tool: _Handle, proc: _Handle, out, tile=None, threads=None, counters=None,
-                        stream=None, events=None, ctas_per_sm=None) -> None:
+                        stream=None, events=None, ctas_per_sm=None, form=None, form_tasks=None) -> None:
         """Enqueue fsm_predict_surface writing into the CUDA tensor `out`.
-        events: optional pair of torch.cuda.Event recorded around the sweep."""
-        o = self._opts(tile, threads, counters, events, ctas_per_sm)
+        events: optional pair of torch.cuda.Event recorded around the sweep;
+        form: "auto", "item" or "phase" (fsm_predict_opts.sweep_form)."""
+        o = self._opts(tile, threads, counters, events, ctas_per_sm, form, form_tasks)
         self._call("fsm_predict_surface", self.ptr, tool.ptr, proc.ptr, out.data_ptr(),
                    C.byref(o) if o is not None else None, _stream_ptr(stream))
 
@@ -317,9 +345,9 @@ class Context:
         return n, ta, pa, ha
 
     def predict_batch(self, tools, procs, outs, rough_buf=None, tile=None, threads=None, counters=None,
-                      stream=None, events=None) -> None:
+                      stream=None, events=None, form=None, form_tasks=None) -> None:
         n, ta, pa, ha = self._arrays(tools, procs, outs)
-        o = self._opts(tile, threads, counters, events)
+        o = self._opts(tile, threads, counters, events, form=form, form_tasks=form_tasks)
         self._call("fsm_predict_batch", self.ptr, n, ta, pa, ha,
                    rough_buf.data_ptr() if rough_buf is not None else None,
                    C.byref(o) if o is not None else None, _stream_ptr(stream))
@@ -356,6 +384,24 @@ class Context:
 
     def release(self, ticket: int) -> None:
         self._call("fsm_release_result", self.ptr, C.c_uint64(ticket))
+
+    def cancel(self, ticket: int) -> None:
+        self._call("fsm_cancel", self.ptr, C.c_uint64(ticket))
+
+    def server_stats(self) -> dict:
+        info = ServerInfo()
+        self._call("fsm_server_stats", self.ptr, C.byref(info))
+        return {k: getattr(info, k) for k, _ in ServerInfo._fields_ if k != "reserved"}
+
+    def server_batches(self, capacity: int = 4096) -> List[dict]:
+        buf = (BatchInterval * capacity)()
+        n = C.c_int32()
+        self._call("fsm_server_batches", self.ptr, buf, int(capacity), C.byref(n))
+        return [{"slot": b.slot, "n_requests": b.n_requests, "t_start_ms": b.t_start_ms, "t_end_ms": b.t_end_ms}
+                for b in buf[:n.value]]
+
+    def server_inject_alloc_failures(self, count: int) -> None:
+        self._call("fsm_server_inject_alloc_failures", self.ptr, int(count))
 
 
 class Batch:

@@ -10,11 +10,11 @@ SA_REL = {"fp64": 1e-9, "fp32": 1e-4}
 MAX_TIE_FRACTION = 1e-4
 
 
-def gpu_map(ctx, F, w, tile=None, counters=None):
+def gpu_map(ctx, F, w, tile=None, counters=None, form=None, form_tasks=None):
     import torch
     t, p = ctx.tool(w.tool), ctx.process(w.process)
     out = F.heights_tensor(w.process)
-    ctx.predict_surface(t, p, out, tile=tile, counters=counters)
+    ctx.predict_surface(t, p, out, tile=tile, counters=counters, form=form, form_tasks=form_tasks)
     torch.cuda.synchronize()
     return out
 

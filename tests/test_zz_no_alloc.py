@@ -44,6 +44,52 @@ def test_noalloc_matches_allocating_entry_point_two_calls_in_a_row():
             assert np.allclose(got[k], ref[k], rtol=1e-12, atol=0.0, equal_nan=True), k
 
 
+def _default_pool_attr(rt, attr, value=None):
+    """Read (or, with value, set) a uint64 attribute of device 0's default
+    stream-ordered memory pool, the pool fsm_roughness allocates from."""
+    import ctypes
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), 0) == 0
+    v = ctypes.c_uint64(0 if value is None else value)
+    if value is None:
+        assert rt.cudaMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+    else:
+        assert rt.cudaMemPoolSetAttribute(pool, attr, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_noalloc_leaves_the_device_pool_untouched():
+    """The defining property: no device allocation. The high watermark of
+    the stream-ordered pool does not move across a no-alloc call, while the
+    allocating entry point (the control) raises it."""
+    import ctypes
+
+    import torch
+
+    from paper_2603_28160_gb300 import fsm as F
+
+    USED_CURRENT, USED_HIGH = 7, 8  # cudaMemPoolAttrUsedMemCurrent / UsedMemHigh
+    ctx = F.Context(0)
+    rt = None
+    for line in open("/proc/self/maps"):
+        if "libcudart.so" in line.split()[-1]:
+            rt = ctypes.CDLL(line.split()[-1])
+            break
+    if rt is None:
+        pytest.skip("CUDA runtime not found in the process")
+    rng = np.random.default_rng(11)
+    H = torch.from_numpy(rng.normal(0.0, 0.001, size=(700, 900)).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    _roughness_via(ctx, F, "fsm_roughness_noalloc", H, 10, 10)  # first call: address look-up
+    base = _default_pool_attr(rt, USED_CURRENT)
+    _default_pool_attr(rt, USED_HIGH, 0)  # resets the watermark to what is in use now
+    _roughness_via(ctx, F, "fsm_roughness_noalloc", H, 10, 10)
+    _roughness_via(ctx, F, "fsm_roughness_noalloc", H, 10, 10)
+    assert _default_pool_attr(rt, USED_HIGH) <= base
+    _roughness_via(ctx, F, "fsm_roughness", H, 10, 10)  # control: allocates its partial sums
+    assert _default_pool_attr(rt, USED_HIGH) > base
+
+
 def test_noalloc_rejects_maps_above_its_limit():
     import torch
 
