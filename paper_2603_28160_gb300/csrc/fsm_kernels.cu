@@ -990,8 +990,11 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         // (see the item form)
         const float hg = gc >= 0.5f ? -1.0f : 0.5f - gc;
         const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
-        const float x_hi = (float)(txc + M) * pitch;  // tile x range plus M cells each side, tile-local
-        const float x_lo = -(float)M * pitch;
+        // tile x range plus M cells each side, tile-local, and half a cell for
+        // the rounding of the linear revolution model below (its error, a few
+        // float roundings of the tile-local x, is far below half a cell)
+        const float x_hi = ((float)(txc + M) + 0.5f) * pitch;
+        const float x_lo = -((float)M + 0.5f) * pitch;
         const int f0 = r.first_off, f1 = r.first_off + r.len0;
         for (int ob = 0; ob < lmax; ob += L) {
             const int off = ob + hl;
@@ -1014,8 +1017,8 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             // ... and among them those whose x lies within a cell of the tile
             const float x0 = fmaf((float)(r.occ0 + offc - sA), fs32, r.dxA) + px;
             const float ka = (x_lo - x0) * inv_rev, kz = (x_hi - x0) * inv_rev;
-            const int k0 = max(kb, (int)floorf(fminf(ka, kz)) - 1);
-            const int k1 = min(ke, (int)ceilf(fmaxf(ka, kz)) + 1);
+            const int k0 = max(kb, (int)ceilf(fminf(ka, kz)));
+            const int k1 = min(ke, (int)floorf(fmaxf(ka, kz)));
             Cell e;
             bool below;
             if constexpr (F64) {  // below the stock by the FP64 height
@@ -1027,8 +1030,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             }
             const bool row = vo && below && ky >= -M && ky <= tyc - 1 + M;
             const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
-            int n_max = n_it;
-            for (int o2 = 16; o2 > 0; o2 >>= 1) n_max = max(n_max, __shfl_xor_sync(0xffffffffu, n_max, o2));
+            const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_it);
             const bool ky_in = (unsigned)ky < (unsigned)tyc;
             const float dy = fabsf(ry - 0.5f);
             for (int kk = 0; kk < n_max; ++kk) {
