@@ -204,9 +204,9 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     s->tool64 = (double*)(base + off);
     off += align256(NE * 9 * sizeof(double));
     s->ph32 = (float2*)(base + off);
-    off += align256((size_t)s->S * sizeof(float2));
+    off += align256(2 * (size_t)s->S * sizeof(float2));
     s->ph64 = (double2*)(base + off);
-    off += align256((size_t)s->S * sizeof(double2));
+    off += align256(2 * (size_t)s->S * sizeof(double2));
     s->groups = (float4*)(base + off);
     off += align256(G * sizeof(float4));
     s->plan_part = (double*)(base + off);

@@ -60,10 +60,12 @@ struct Surface {
     int32_t cached;           // tables and group bounds already built (a server's table cache)
     unsigned long long* form_tasks;  // NULL or [2]: tasks walked in the item / phase form
     // ---- tables (device pointers, inputs) ----
-    float4* tool32;   // [N*E][4]: (ux,vx,wx,uz) (uy,vy,wy,vz) (wz,amp_y,mph_y,amp_z) (mph_z,amp_x,mph_x,0)
+    // [N*E][4]: (ux,vx,wx,uz) (uy,vy,wy,vz) (wz,amp_y,mph_y,amp_z) (mph_z,amp_x,mph_x,0); the x and y
+    // rows (ux..wy) are in cells (divided by the pitch), everything else in mm
+    float4* tool32;
     double* tool64;   // [9][N*E]: ux uy uz vx vy vz wx wy wz
-    float2* ph32;     // [S] (cos, sin) of Theta_m
-    double2* ph64;    // [S]
+    float2* ph32;     // [2S] (cos, sin) of Theta_m, m mod S: two turns, so m0 + offset needs no wrap
+    double2* ph64;    // [2S]
     float4* groups;   // [N * ceil(E/32)]: (min P_y, max P_y while below the stock, min P_z, 0) over 32 points
     double* plan_part;  // [kPlanParts][4]: per planning block, lowest z, x and y reach
     int* tile_queue;    // next-tile counter of a single-surface sweep (zeroed by planning)
@@ -80,6 +82,7 @@ struct Surface {
     float zrel_f;                   // z_ref - stock
     float fs_hi, fs_lo;             // fs as an unevaluated float pair (fs_hi + fs_lo)
     float fs_f, inv_fs_f, dth_f, inv_dth_f, inv_pitch_f;
+    float fsc_hi, fsc_lo, fsc_f;    // feed per step in cells (fs / pitch), as a float pair and rounded
     float guard_extra;              // FP32 rounding of the bin scaling, in cells
 };
 
@@ -254,10 +257,11 @@ struct PointGeom {
     float wx, wy, wz, amp_x, amp_y, amp_z, mph_x, mph_y, mph_z;
 };
 
-FSM_HD PointGeom load_geom(const float4* t4) {
+// t4: the point's FP32 table row; pitch: the map pitch (x and y rows are in cells)
+FSM_HD PointGeom load_geom(const float4* t4, float pitch) {
     PointGeom g;
-    g.wx = t4[0].z;
-    g.wy = t4[1].z;
+    g.wx = t4[0].z * pitch;
+    g.wy = t4[1].z * pitch;
     g.wz = t4[2].x;
     g.amp_y = t4[2].y;
     g.mph_y = t4[2].z;

@@ -203,9 +203,11 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
             amp[d] = (float)a;
             mph[d] = (float)m;
         }
+        // x and y rows in cells, so the sweep bins without a scaling step
         float4* t32 = sf.tool32 + 4 * (size_t)idx;
-        t32[0] = make_float4((float)u[0], (float)v[0], (float)w[0], (float)u[2]);
-        t32[1] = make_float4((float)u[1], (float)v[1], (float)w[1], (float)v[2]);
+        const double ip = 1.0 / sf.pitch;
+        t32[0] = make_float4((float)(u[0] * ip), (float)(v[0] * ip), (float)(w[0] * ip), (float)u[2]);
+        t32[1] = make_float4((float)(u[1] * ip), (float)(v[1] * ip), (float)(w[1] * ip), (float)v[2]);
         t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
         t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
         // lowest workpiece z of the point over a turn (exact FP64; min is
@@ -215,13 +217,13 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         rx = fmaxf(rx, (float)(fabs(w[0]) + a64[0]));
         ry = fmaxf(ry, (float)(fabs(w[1]) + a64[1]));
     }
-    // phase table
+    // phase table, two turns (entry m + S repeats entry m)
     for (int m = first; m < S; m += stride) {
         double th = deg2rad(sf.phase0_deg + sigma * ((double)m * sf.rot_step_deg));
         double sn, cs;
         sincos(th, &sn, &cs);
-        sf.ph64[m] = make_double2(cs, sn);
-        sf.ph32[m] = make_float2((float)cs, (float)sn);
+        sf.ph64[m] = sf.ph64[m + S] = make_double2(cs, sn);
+        sf.ph32[m] = sf.ph32[m + S] = make_float2((float)cs, (float)sn);
     }
     zlo = block_min_d(zlo, shd);
     rx = block_max_f(rx, shf);
@@ -282,6 +284,10 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         sf->dth_f = (float)dth;
         sf->inv_dth_f = (float)(1.0 / dth);
         sf->inv_pitch_f = (float)(1.0 / sf->pitch);
+        const double fsc = fs / sf->pitch;
+        sf->fsc_hi = (float)fsc;
+        sf->fsc_lo = (float)(fsc - (double)sf->fsc_hi);
+        sf->fsc_f = (float)fsc;
         // the bin scaling x_l * (1/pitch) rounds twice, relative to |x_l / pitch|
         const double u24 = 5.9604644775390625e-8;
         sf->guard_extra = (float)(3.0 * u24 * (double)max(sf->tile_x, sf->tile_y) + 1e-6);
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         const int j = g * 32 + lane;
         float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
         if (j < E) {
-            const PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j));
+            const PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), (float)sf->pitch);
             zmin = geo.wz - geo.amp_z;
             ArcF za;
             ArcI ia[kMaxArcs];
@@ -345,7 +351,7 @@ __device__ __forceinline__ void warp_flush(Counters& c, long long* out) {
 struct RunRec {
     int32_t m0, len, occ0, first_off, len0;
     int32_t k_last, len_last;  // last revolution of the window and its length
-    float dxA;      // FP32 path: tile-local x of the pass at the run's first step
+    float dxA;      // FP32 path: tile-local x of the pass at the run's first step, in cells
     float g_cells;  // FP32 path: bin ambiguity band of this run (cells)
 };
 
@@ -376,8 +382,9 @@ constexpr int kPassCache = 64;
 
 // Per-tile values shared by all warps, computed once per tile in FP64.
 struct TileShared {
-    float ylo[kPassCache], yhi[kPassCache], dy[kPassCache];
-    float dx_hi, dx_lo;  // pass_x0 - tile origin x, as a float pair
+    float ylo[kPassCache], yhi[kPassCache];  // mm, for the enumeration
+    float dy[kPassCache];                     // pass line - tile origin y, in cells
+    float dx_hi, dx_lo;  // pass_x0 - tile origin x in cells, as a float pair
     float xlo, xhi;      // tile x extent relative to pass_x0, margins included
     float zhi;           // stock - z_ref + margin
 };
@@ -437,10 +444,10 @@ __device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCt
         const double yc = path_y(sf, p);
         ts.ylo[p] = (float)(tc.Y0 - yc) - kMarginMm;
         ts.yhi[p] = (float)(y1 - yc) + kMarginMm;
-        ts.dy[p] = (float)(yc - tc.Y0);
+        ts.dy[p] = (float)((yc - tc.Y0) * sf.inv_pitch);
     }
     if (threadIdx.x == 0) {
-        const double d = sf.pass_x0 - tc.X0;
+        const double d = (sf.pass_x0 - tc.X0) * sf.inv_pitch;
         ts.dx_hi = (float)d;
         ts.dx_lo = (float)(d - (double)ts.dx_hi);
         ts.xlo = (float)(tc.X0 - sf.pass_x0) - kMarginMm;
@@ -461,7 +468,7 @@ __device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<Cell>
         const double yc = path_y(sf, p);
         *ylo = (float)(tc.Y0 - yc) - kMarginMm;
         *yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
-        *dy = (float)(yc - tc.Y0);
+        *dy = (float)((yc - tc.Y0) * sf.inv_pitch);
     }
 }
 
@@ -484,8 +491,9 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         t4[2] = tp[2];
         const float4 t3 = tp[3];
         PointGeom geo;
-        geo.wx = t4[0].z;
-        geo.wy = t4[1].z;
+        const float pitch = (float)sf.pitch;  // the x, y rows are in cells
+        geo.wx = t4[0].z * pitch;
+        geo.wy = t4[1].z * pitch;
         geo.wz = t4[2].x;
         geo.amp_y = t4[2].y;
         geo.mph_y = t4[2].z;
@@ -529,7 +537,7 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
             r.len_last = it.len_last;
             const int32_t sA = it.occ0 + it.first_off;
             const int32_t nA = f.reversed ? f.n_steps - 1 - (sA - f.s0) : sA - f.s0;
-            r.dxA = df_affine(ts.dx_hi, ts.dx_lo, nA, sf.fs_hi, sf.fs_lo);
+            r.dxA = df_affine(ts.dx_hi, ts.dx_lo, nA, sf.fsc_hi, sf.fsc_lo);  // cells
             const float span_mm = (float)(runs[a].s_hi - runs[a].s_lo) * sf.fs_f;
             r.g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * sf.inv_pitch_f + sf.guard_extra;
         }
@@ -780,17 +788,25 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
     *r = v - d * len;
 }
 
-// Item form of phase 2, for runs of few revolutions: the task's runs are
-// taken four at a time, one per group of L = 8 lanes; each lane evaluates
-// items hl and hl + L of every 2L of its group's run, written as two
-// interleaved, mostly predicated chains (the runs average ~70 items, so
-// narrower groups waste fewer slots at run ends and share the per-run
-// shuffles among more runs). Counted from phase 0 of the first occurrence
-// (v = t + first_off; the first occurrence is complete up to the window's
-// end whenever there is a second one), item t lies in revolution q = v / len
-// at phase offset v mod len, q (S - len) + t steps after the run's first
-// item; the lane advances (q, offset) by 2L items per iteration without a
-// division.
+// Shared FP32 binning of both walks (tile-local, in cells): the point's
+// x offset from the phase table and the x and y rows of its table entry
+// (already divided by the pitch), the pass position from the run's anchor
+// and the steps after the run's first item:
+//     x = fma(ds, fs, dxA) + fma(cos, ux, fma(sin, vx, wx)),
+//     y = dyp + fma(cos, uy, fma(sin, vy, wy)),
+// cell = (floor x, floor y), ambiguous within the run's guard band gc of a
+// cell boundary.
+
+// Item form of phase 2: the task's runs are taken four at a time, one per
+// group of L = 8 lanes; each lane evaluates items hl and hl + L of every 2L
+// of its group's run, written as two interleaved, mostly predicated chains
+// (the runs average ~70 items, so narrower groups waste fewer slots at run
+// ends and share the per-run shuffles among more runs). Counted from phase 0
+// of the first occurrence (v = t + first_off; the first occurrence is
+// complete up to the window's end whenever there is a second one), item t
+// lies in revolution q = v / len at phase offset v mod len, q (S - len) + t
+// steps after the run's first item; the lane advances (q, offset) by 2L
+// items per iteration without a division.
 constexpr int kItemLanes = 8;
 template <bool F64>
 __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
@@ -801,8 +817,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
     const int lane = threadIdx.x & 31;
     const int hl = lane & (L - 1), grp = lane / L;
     const int S = sf.S;
-    const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
-    const float inv_pitch = sf.inv_pitch_f;
+    const float fs32 = pass_reversed(sf, p) ? -sf.fsc_f : sf.fsc_f;  // cells per step; back on a return pass
     const float2* __restrict__ ph32 = sf.ph32;
     const double2* __restrict__ ph64 = sf.ph64;
     const int NE = sf.n_teeth * sf.E;
@@ -860,9 +875,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
             int32_t ob = oa + rl, qb = qa + dl;
             if (ob >= len) { ob -= len; ++qb; }
             const int32_t dsa = ta + qa * gap, dsb = tb + qb * gap;  // steps after the run's first item
-            int32_t ma = r.m0 + oa, mb = r.m0 + ob;
-            ma = ma >= S ? ma - S : ma;
-            mb = mb >= S ? mb - S : mb;
+            const int32_t ma = r.m0 + oa, mb = r.m0 + ob;             // < 2S: the table holds two turns
             oa += r2l;
             qa += d2l;
             if (oa >= len) { oa -= len; ++qa; }
@@ -871,14 +884,15 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
             cnt.evaluated += (unsigned)va + (unsigned)vb;
             const float za = fmaf(ca.x, uz, fmaf(ca.y, vz, zb));
             const float zb2 = fmaf(cb.x, uz, fmaf(cb.y, vz, zb));
-            const float xa = fmaf((float)dsa, fs32, r.dxA) + fmaf(ca.x, ux, fmaf(ca.y, vx, wx));
-            const float xb = fmaf((float)dsb, fs32, r.dxA) + fmaf(cb.x, ux, fmaf(cb.y, vx, wx));
-            const float ya = dyp + fmaf(ca.x, uy, fmaf(ca.y, vy, wy));
-            const float yb = dyp + fmaf(cb.x, uy, fmaf(cb.y, vy, wy));
-            const float fxa = xa * inv_pitch, fya = ya * inv_pitch, fxb = xb * inv_pitch, fyb = yb * inv_pitch;
-            const float lxa = floorf(fxa), lya = floorf(fya), lxb = floorf(fxb), lyb = floorf(fyb);
-            const float rxa = fxa - lxa, rya = fya - lya, rxb = fxb - lxb, ryb = fyb - lyb;
-            const int ia = (int)lxa, ka = (int)lya, ib = (int)lxb, kb = (int)lyb;
+            const float fxa = fmaf((float)dsa, fs32, r.dxA) + fmaf(ca.x, ux, fmaf(ca.y, vx, wx));
+            const float fxb = fmaf((float)dsb, fs32, r.dxA) + fmaf(cb.x, ux, fmaf(cb.y, vx, wx));
+            const float fya = dyp + fmaf(ca.x, uy, fmaf(ca.y, vy, wy));
+            const float fyb = dyp + fmaf(cb.x, uy, fmaf(cb.y, vy, wy));
+            // floor by one conversion each, the fraction by subtraction
+            const int ia = __float2int_rd(fxa), ka = __float2int_rd(fya);
+            const int ib = __float2int_rd(fxb), kb = __float2int_rd(fyb);
+            const float rxa = fxa - __int2float_rn(ia), rya = fya - __int2float_rn(ka);
+            const float rxb = fxb - __int2float_rn(ib), ryb = fyb - __int2float_rn(kb);
             Cell ea, eb;
             bool cut_a, cut_b;
             if constexpr (F64) {  // below the stock by the FP64 height
@@ -924,15 +938,17 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
     drain_queues<F64>(sf, tc, ws, aq, p, an, qn, cnt);
 }
 
-// Phase form of phase 2, for runs of many revolutions. The task's runs are
-// taken four at a time, one per group of L = 8 lanes, and every lane takes
-// phase offsets of its run. Height, y cell and the point's x offset depend
-// on the spindle phase alone, so they are computed once per offset; the
-// revolutions in which that phase lies inside the run's step window differ
-// only by a shift of S fs in x, and the ones that can bring the point within
-// a cell of the tile are found in closed form and visited. Each visit
-// evaluates exactly as a single item would (the same FP32 pose, binning,
-// guard band and FP64 re-binning).
+// Phase form of phase 2. The task's runs are taken four at a time, one per
+// group of L = 8 lanes, and every lane takes phase offsets of its run.
+// Height, y cell and the point's x offset depend on the spindle phase alone,
+// so they are computed once per offset; the revolutions of that phase differ
+// only by a shift of S fs in x, and those whose x lies within the tile (plus
+// M cells and half a cell each side: the ambiguous neighbours, and margin for
+// the rounding of the linear revolution model) are found in closed form and
+// visited two at a time -- a tile some whole number of revolutions of feed
+// wide keeps that number nearly constant across lanes. Each visit bins
+// exactly as an item of the item form (same x and y arithmetic, guard band
+// and FP64 re-binning), so both forms give the same maps and counts.
 template <bool F64>
 __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
                                              int g, int p, WarpScratch& ws, AmbQueue* aq, const float4 (&t4)[3],
@@ -942,9 +958,9 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
     constexpr int L = kItemLanes;
     const int hl = lane & (L - 1), grp = lane / L;
     const int S = sf.S;
-    const float fs32 = pass_reversed(sf, p) ? -sf.fs_f : sf.fs_f;  // x moves back on a return pass
-    const float inv_pitch = sf.inv_pitch_f;
-    const float pitch = 1.0f / inv_pitch;
+    const float fS = (float)S;
+    const bool back = pass_reversed(sf, p);
+    const float fs32 = back ? -sf.fsc_f : sf.fsc_f;  // cells per step; back on a return pass
     const float2* __restrict__ ph32 = sf.ph32;
     const double2* __restrict__ ph64 = sf.ph64;
     const int NE = sf.n_teeth * sf.E;
@@ -953,8 +969,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
     const int tile_x = sf.tile_x;
     Cell* cells = tc.cells;
     const int txc = tc.txc, tyc = tc.tyc;
-    const float rev = (float)S * fs32;            // x shift per revolution
-    const float inv_rev = 1.0f / rev;
+    const float inv_rev = 1.0f / (fS * fs32);  // revolutions per cell of x
     int R = ws.n[lane];
     for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
     int qn = 0;  // queued re-bins (warp-uniform)
@@ -990,35 +1005,27 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         // (see the item form)
         const float hg = gc >= 0.5f ? -1.0f : 0.5f - gc;
         const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
-        // tile x range plus M cells each side, tile-local, and half a cell for
-        // the rounding of the linear revolution model below (its error, a few
-        // float roundings of the tile-local x, is far below half a cell)
-        const float x_hi = ((float)(txc + M) + 0.5f) * pitch;
-        const float x_lo = -((float)M + 0.5f) * pitch;
+        // x range of the visits, tile-local cells; k increases toward the
+        // far end on a forward pass and toward the near end on a return pass
+        const float x_near = -((float)M + 0.5f), x_far = (float)(txc + M) + 0.5f;
+        const float xk_lo = back ? x_far : x_near, xk_hi = back ? x_near : x_far;
+        const float d_first = (float)(r.occ0 - sA);  // steps from the run's first item to phase 0 of its first turn
         const int f0 = r.first_off, f1 = r.first_off + r.len0;
+        // the phase-table entry of the next offset is loaded one round ahead
+        // (the table does not stay in the L1 left beside a large tile)
+        float2 c_next = __ldg(ph32 + r.m0 + (hl < len ? hl : 0));
         for (int ob = 0; ob < lmax; ob += L) {
             const int off = ob + hl;
             const bool vo = off < len;
             const int offc = vo ? off : 0;
-            int32_t m = r.m0 + offc;
-            m = m >= S ? m - S : m;
-            const float2 c = __ldg(ph32 + m);
+            const int32_t m = r.m0 + offc;  // < 2S: the table holds two turns
+            const float2 c = c_next;
+            c_next = __ldg(ph32 + r.m0 + (off + L < len ? off + L : 0));
             const float z = fmaf(c.x, uz, fmaf(c.y, vz, zb));
             const float px = fmaf(c.x, ux, fmaf(c.y, vx, wx));
-            const float y = dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
-            const float fy = y * inv_pitch;
-            const float ly = floorf(fy);
-            const float ry = fy - ly;
-            const int ky = (int)ly;
-            // revolutions of this phase inside the window: the first only for
-            // offsets it covers, the last only below its length
-            const int kb = (offc >= f0 && offc < f1) ? 0 : 1;
-            const int ke = r.k_last == 0 ? 0 : (offc < r.len_last ? r.k_last : r.k_last - 1);
-            // ... and among them those whose x lies within a cell of the tile
-            const float x0 = fmaf((float)(r.occ0 + offc - sA), fs32, r.dxA) + px;
-            const float ka = (x_lo - x0) * inv_rev, kz = (x_hi - x0) * inv_rev;
-            const int k0 = max(kb, (int)ceilf(fminf(ka, kz)));
-            const int k1 = min(ke, (int)floorf(fmaxf(ka, kz)));
+            const float fy = dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
+            const int ky = __float2int_rd(fy);  // floor: one conversion, the fraction by subtraction
+            const float ry = fy - __int2float_rn(ky);
             Cell e;
             bool below;
             if constexpr (F64) {  // below the stock by the FP64 height
@@ -1029,32 +1036,56 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
                 e = cell_key(z);
             }
             const bool row = vo && below && ky >= -M && ky <= tyc - 1 + M;
+            // revolutions of this phase inside the run's step window: the
+            // first only for offsets it covers, the last only below its length
+            const int kb = (offc >= f0 && offc < f1) ? 0 : 1;
+            const int ke = r.k_last == 0 ? 0 : (offc < r.len_last ? r.k_last : r.k_last - 1);
+            // ... and within the x range: revolution k is d0 + k S steps after
+            // the run's first item, at x ~ x0 + k S fs
+            const float d0 = d_first + (float)offc;
+            const float x0 = fmaf(d0, fs32, r.dxA) + px;
+            const int k0 = max(kb, __float2int_ru((xk_lo - x0) * inv_rev));
+            const int k1 = min(ke, __float2int_rd((xk_hi - x0) * inv_rev));
             const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
             const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_it);
             const bool ky_in = (unsigned)ky < (unsigned)tyc;
             const float dy = fabsf(ry - 0.5f);
-            for (int kk = 0; kk < n_max; ++kk) {
-                const bool v = kk < n_it;
-                const int32_t s = r.occ0 + (k0 + kk) * S + offc;
-                const float x = fmaf((float)(s - sA), fs32, r.dxA) + px;
-                const float fx = x * inv_pitch;
-                const float lx = floorf(fx);
-                const float rx = fx - lx;
-                const int ix = (int)lx;
-                cnt.evaluated += (unsigned)v;
-                const bool in = v && ky_in && (unsigned)ix < (unsigned)txc;
-                const bool amb = fmaxf(fabsf(rx - 0.5f), dy) > hg;  // within gc of a cell boundary
-                const bool upd = in && !amb;
-                cnt.cutting += F64 ? (unsigned)upd : (unsigned)in;
-                const int ci = ky * tile_x + ix;
-                const Cell cv = upd ? cells[ci] : (Cell)0;
-                if (upd && e < cv) {
-                    atomicMin(cells + ci, e);
+            float ds = fmaf((float)k0, fS, d0);  // steps after the run's first item (an exact integer)
+            for (int kk = 0; kk < n_max; kk += 2) {
+                const bool va = kk < n_it, vb = kk + 1 < n_it;
+                const float dsb = ds + fS;
+                const float fxa = fmaf(ds, fs32, r.dxA) + px;
+                const float fxb = fmaf(dsb, fs32, r.dxA) + px;
+                const int ia = __float2int_rd(fxa), ib = __float2int_rd(fxb);
+                const float rxa = fxa - __int2float_rn(ia), rxb = fxb - __int2float_rn(ib);
+                cnt.evaluated += (unsigned)va + (unsigned)vb;
+                const bool in_a = va && ky_in && (unsigned)ia < (unsigned)txc;
+                const bool in_b = vb && ky_in && (unsigned)ib < (unsigned)txc;
+                const bool amb_a = fmaxf(fabsf(rxa - 0.5f), dy) > hg;  // within gc of a cell boundary
+                const bool amb_b = fmaxf(fabsf(rxb - 0.5f), dy) > hg;
+                const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
+                cnt.cutting += F64 ? (unsigned)upd_a + (unsigned)upd_b : (unsigned)in_a + (unsigned)in_b;
+                const int cia = ky * tile_x + ia, cib = ky * tile_x + ib;
+                const Cell cva = upd_a ? cells[cia] : (Cell)0;
+                const Cell cvb = upd_b ? cells[cib] : (Cell)0;
+                if (upd_a && e < cva) {
+                    atomicMin(cells + cia, e);
                     ++cnt.atomics;
                 }
-                const bool pw = v && amb && ix >= -M && ix <= txc - 1 + M;  // (v: ky in [-M, tyc - 1 + M])
-                if (__any_sync(0xffffffffu, pw))
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pw, ix, ky, rx, ry, gc, z, eps_z, s, m, idx, an, qn, cnt);
+                if (upd_b && e < cvb) {
+                    atomicMin(cells + cib, e);
+                    ++cnt.atomics;
+                }
+                // (va, vb: ky in [-M, tyc - 1 + M], below the stock)
+                const bool pa = va && amb_a && ia >= -M && ia <= txc - 1 + M;
+                const bool pb = vb && amb_b && ib >= -M && ib <= txc - 1 + M;
+                if (__any_sync(0xffffffffu, pa || pb)) {
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ky, rxa, ry, gc, z, eps_z, sA + (int32_t)ds, m,
+                                        idx, an, qn, cnt);
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pb, ib, ky, rxb, ry, gc, z, eps_z, sA + (int32_t)dsb, m,
+                                        idx, an, qn, cnt);
+                }
+                ds = dsb + fS;
             }
         }
     }

@@ -7,8 +7,8 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "fsm.h")).read()
+def declared_functions(header="fsm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(fsm_[a-z_]+)\s*\(", src)))
 
@@ -26,6 +26,42 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(path)
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_probe_library_exports_its_header():
+    """The micro-benchmark library exports what include/fsm_probe.h declares,
+    and its binding covers it."""
+    from paper_2603_28160_gb300 import build, probe
+    build.build()
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    names = declared_functions("fsm_probe.h")
+    assert names == ["fsm_probe_run"]
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(probe.SIGNATURES)
+
+
+def test_probe_struct_matches_the_header():
+    import subprocess
+    import tempfile
+    from paper_2603_28160_gb300 import probe
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fsm_probe.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(fsm_probe_result), offsetof(fsm_probe_result, sms),
+         offsetof(fsm_probe_result, ms_total));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        open(c, "w").write(code)
+        exe = os.path.join(d, "p")
+        subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert got == [ctypes.sizeof(probe.ProbeResult), probe.ProbeResult.sms.offset, probe.ProbeResult.ms_total.offset]
 
 
 def test_binding_signatures_cover_the_header():

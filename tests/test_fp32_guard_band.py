@@ -1,16 +1,17 @@
 """The FP32 binning's guard band bounds its FP32 error (CPU, no GPU).
 
 FP32 maps and the binning of FP64 maps place an edge point in a cell from
-FP32 tile-local coordinates; a point within the guard band of a cell
-boundary is re-binned with the FP64 pose. The maps equal the FP64 binning
-only if the band bounds the FP32 error of every point. This test models the
-sweep's FP32 arithmetic for the tile-local x and y of a pose -- the run
-anchor from a float pair of the pass offset and of the feed per step
-(double-float affine step), fused multiply-adds of the rounded phase table
-and tool vectors, the bin scaling -- with each fused multiply-add rounded
-once (float32 products are exact in float64), against the same pose in
-float64, over random tools, phases, tiles, pitches, feeds and run spans, and
-checks the error in cells against the band the kernel computes for the run:
+FP32 tile-local coordinates in cells; a point within the guard band of a
+cell boundary is re-binned with the FP64 pose. The maps equal the FP64
+binning only if the band bounds the FP32 error of every point. This test
+models the sweep's FP32 arithmetic for the tile-local x and y of a pose --
+the tool rows and the pass offsets divided by the pitch in float64 and
+rounded once, the run anchor from a float pair of the pass offset and of the
+feed per step (double-float affine step), fused multiply-adds of the rounded
+phase table and tool rows -- with each fused multiply-add rounded once
+(float32 products are exact in float64), against the same pose in float64,
+over random tools, phases, tiles, pitches, feeds and run spans, and checks
+the error in cells against the band the kernel computes for the run:
 1.5 u (6 max(amp_x, amp_y) + 3 (|w_x| + |w_y| + |w_z|) + 3 tile pitch
 + 2 span) / pitch + 3 u tile + 1e-6, u = 2^-24."""
 import numpy as np
@@ -65,20 +66,20 @@ def test_guard_band_bounds_fp32_binning_error():
             px = c * ux + s * vx + wx
             d = X - ds * fs - px - n_a * fs          # pass_x0 - tile origin
             dyp = Y - (c * uy + s * vy + wy)         # pass line - tile origin (y)
-            # FP32 inputs as the planner stores them
+            # FP32 inputs as the planner stores them: x and y rows in cells
             c32, s32 = c.astype(f32), s.astype(f32)
-            ux32, vx32, wx32 = ux.astype(f32), vx.astype(f32), wx.astype(f32)
-            uy32, vy32, wy32 = uy.astype(f32), vy.astype(f32), wy.astype(f32)
-            d_hi = d.astype(f32)
-            d_lo = (d - d_hi.astype(np.float64)).astype(f32)
-            fs_hi = fs.astype(f32)
-            fs_lo = (fs - fs_hi.astype(np.float64)).astype(f32)
-            inv_pitch = f32(1.0 / pitch)
-            # the kernel's FP32 arithmetic
+            ux32, vx32, wx32 = (ux / pitch).astype(f32), (vx / pitch).astype(f32), (wx / pitch).astype(f32)
+            uy32, vy32, wy32 = (uy / pitch).astype(f32), (vy / pitch).astype(f32), (wy / pitch).astype(f32)
+            dc = d / pitch
+            d_hi = dc.astype(f32)
+            d_lo = (dc - d_hi.astype(np.float64)).astype(f32)
+            fsc = fs / pitch
+            fs_hi = fsc.astype(f32)
+            fs_lo = (fsc - fs_hi.astype(np.float64)).astype(f32)
+            # the kernel's FP32 arithmetic, in cells
             dxa = df_affine(d_hi, d_lo, n_a, fs_hi, fs_lo)
-            x32 = (fma32(ds.astype(f32), fs_hi, dxa) + fma32(c32, ux32, fma32(s32, vx32, wx32))).astype(f32)
-            y32 = (dyp.astype(f32) + fma32(c32, uy32, fma32(s32, vy32, wy32))).astype(f32)
-            fx, fy = (x32 * inv_pitch).astype(f32), (y32 * inv_pitch).astype(f32)
+            fx = (fma32(ds.astype(f32), fs_hi, dxa) + fma32(c32, ux32, fma32(s32, vx32, wx32))).astype(f32)
+            fy = ((dyp / pitch).astype(f32) + fma32(c32, uy32, fma32(s32, vy32, wy32))).astype(f32)
             # the same pose in float64 (the FP64 binning's coordinates, up to float64 rounding)
             ex = np.abs(fx.astype(np.float64) - X / pitch)
             ey = np.abs(fy.astype(np.float64) - Y / pitch)

@@ -128,34 +128,51 @@ def test_run_items_and_phases_match_brute_force():
     assert checked > 10**6
 
 
+def fma32(a, b, c):
+    """fmaf of float32 arrays: the product is exact in float64, one rounding."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(f32)
+
+
 def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
-    """Phase form: for one phase offset the x of revolution k is
-    x0 + k S fs; the kernel visits k in [max(kb, floor(min(ka, kz)) - 1),
-    min(ke, ceil(max(ka, kz)) + 1)] with ka, kz = (x_lo - x0, x_hi - x0) /
-    (S fs) in FP32. Every revolution whose x (in float64) lies within the
-    tile's x range widened by M cells must be in that range, for both feed
-    directions."""
+    """Phase form: for one phase offset, revolution k of a run is
+    ds_k = d0 + k S steps after the run's first item, at tile-local x (cells)
+    fma(ds_k, fs, dxA) + px in FP32. The kernel visits k in
+    [max(kb, ceil((lo - x0) / (S fs))), min(ke, floor((hi - x0) / (S fs)))],
+    x0 = fma(d0, fs, dxA) + px, with (lo, hi) = (-(M + 1/2), txc + M + 1/2)
+    (swapped on a return pass, fs < 0), in FP32. Every revolution whose
+    FP32 x lies within the tile widened by M cells, [-M, txc + M), must be
+    visited, for both feed directions."""
     rng = np.random.default_rng(61)
-    for _ in range(20000):
+    hit = 0
+    for _ in range(4000):
         S = int(rng.integers(1, 40000))
-        fs = 10.0 ** rng.uniform(-6.0, -1.0) * (1 if rng.random() < 0.5 else -1)
-        pitch = 10.0 ** rng.uniform(-3.3, -1.7)
+        fs = f32(10.0 ** rng.uniform(-4.0, 1.0) * (1 if rng.random() < 0.5 else -1))  # cells per step
         txc = int(rng.integers(1, 1025))
         M = int(rng.integers(1, 4))
-        kb, ke = int(rng.integers(0, 2)), int(rng.integers(0, 3000))
-        if ke < kb:
+        kb, ke = int(rng.integers(0, 2)), int(rng.integers(0, 400))
+        if ke < kb or abs(float(fs)) * S * ke > 1e6:
             continue
-        rev64 = S * fs
-        x0 = rng.uniform(-2.0, 2.0) - rng.uniform(0.0, 1.0) * ke * rev64
-        x_lo, x_hi = -M * pitch, (txc + M) * pitch
-        rev = f32(S) * f32(fs)
-        inv_rev = f32(1.0) / rev
-        ka = (f32(x_lo) - f32(x0)) * inv_rev
-        kz = (f32(x_hi) - f32(x0)) * inv_rev
-        k0 = max(kb, int(np.floor(min(ka, kz))) - 1)
-        k1 = min(ke, int(np.ceil(max(ka, kz))) + 1)
+        d0 = f32(-int(rng.integers(0, S)) + int(rng.integers(0, S)))
+        px = f32(rng.uniform(-3000.0, 3000.0))
+        # an anchor that brings some revolutions over the tile
+        k_mid = rng.uniform(kb, ke + 1)
+        dxa = f32(rng.uniform(-M - 2, txc + M + 2) - float(px) - (float(d0) + k_mid * S) * float(fs))
+        back = fs < 0
+        lo, hi = f32(-(M + 0.5)), f32(txc + M + 0.5)
+        k_lo, k_hi = (hi, lo) if back else (lo, hi)
+        inv_rev = f32(1.0) / (f32(S) * fs)
+        x0 = (fma32(np.array([d0]), np.array([fs]), np.array([dxa]))[0] + px).astype(f32)
+        k0 = max(kb, int(np.ceil(f32((k_lo - x0) * inv_rev))))
+        k1 = min(ke, int(np.floor(f32((k_hi - x0) * inv_rev))))
         ks = np.arange(kb, ke + 1)
-        xs = x0 + ks * rev64
-        over = ks[(xs >= x_lo) & (xs <= x_hi)]
+        ds = (f32(d0) + ks.astype(np.float64) * S).astype(f32)
+        xs = (fma32(ds, np.full(ks.size, fs, f32), np.full(ks.size, dxa, f32)) + px).astype(f32).astype(np.float64)
+        over = ks[(xs >= -M) & (xs < txc + M)]
+        hit += over.size
         ok = over.size == 0 or (over.min() >= k0 and over.max() <= k1)
-        assert ok, (S, fs, x0, over, k0, k1)
+        assert ok, (S, fs, float(x0), over, k0, k1)
+        # and the range is tight: its revolutions span no more x than the
+        # widened tile (txc + 2M + 1 cells), up to float rounding
+        if k1 > k0:
+            assert (k1 - k0) * abs(float(fs)) * S <= (txc + 2 * M + 1) * (1 + 1e-5) + 1e-3
+    assert hit > 1000
