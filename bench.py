@@ -29,9 +29,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "edge-point evals/s and surfaces/s at <=5 nm height error; p50/p99 latency"
 UNIT = "cutting edge-point evaluations/s"
-FP32_FLOPS_PER_EVAL = 16  # 6 FMA pose (12) + 2 tile offsets + 2 bin scalings
+# algorithmic work of one cutting evaluation (the survey's count for the
+# FP32 path): 9 FFMA (3x3 pose) + 3 FADD (tile offset) + 2 FMUL (bin
+# scaling) = 23 flops; as instruction lanes, those 14 plus 2 float->int
+# conversions, ~6 integer/compare operations, 1 shared load and at most 1
+# shared atomic = 24. (The kernel's own pose is cheaper: 7 FFMA + 2 FADD in
+# cell units, 16 flops.)
+FP32_FLOPS_PER_EVAL = 23
+ISSUE_LANES_PER_EVAL = 24
+KERNEL_FLOPS_PER_EVAL = 16
 FP64_HEIGHT_FLOPS = 5     # FP64 maps: the height row of the pose (2 FMA + 1 add) per evaluation
-FP64_PEAK_TFLOPS = 1.25   # nominal FP64 rate of GB300
 TRAJ_FP64_FLOPS = 15      # one FP64 pose: 3 x (2 FMA + 1 add)
 L2_FLUSH_BYTES = 256 << 20
 
@@ -56,13 +63,21 @@ def parse():
                     help="only the single-surface FP32 and FP64 steps (profiling runs)")
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-rate", type=float, default=30.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="seconds of arrivals per served rate")
+    ap.add_argument("--serve-rates", default="40,80,160,320",
+                    help="Poisson arrival rates (requests/s) of the served leg, comma separated")
+    ap.add_argument("--serve-setups", type=int, default=64,
+                    help="served requests draw tool and set-up from a catalogue of this many (0: all distinct)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the served leg (after the single-surface steps) and print its record")
     ap.add_argument("--width", type=float, default=5.0,
                     help="patch width in mm (5.0 = the measured configuration; smaller for profiling)")
     args = ap.parse_args()
     if args.skip_extras:
         for k in ("cpu_baseline", "batch", "large", "serve", "paper", "trajectory", "wall", "filter"):
+            setattr(args, "skip_" + k, True)
+    if args.serve_only:
+        for k in ("cpu_baseline", "batch", "large", "paper", "trajectory", "wall", "filter", "fp64"):
             setattr(args, "skip_" + k, True)
     global WIDTH
     WIDTH = args.width
@@ -283,26 +298,61 @@ def reference_arm(args):
     return 0
 
 
-def fp32_alu_peak(torch, device, sm_max_mhz=None):
-    """FP32 FMA peak of the GPU in TFLOP/s: SMs x 128 lanes x 2 flop x max SM clock."""
-    props = torch.cuda.get_device_properties(device)
-    sm_max = sm_max_mhz or 2070.0
-    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-    return peak, "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (props.multi_processor_count, sm_max)
+def unit_peaks(device):
+    """Measured rates of the units the kernels are bound by (the
+    micro-benchmarks of libfsm_probe.so, best of 3 x 3 runs), with the
+    copy bandwidth from MEASURED_PEAKS.json for the HBM-bound kernels."""
+    from paper_2603_28160_gb300 import probe
+    runs = [probe.run(device, 3) for _ in range(3)]
+    best = {k: max(r[k] for r in runs) for k in probe.FIELDS}
+    best["source"] = "measured by libfsm_probe.so on this GPU (sustained, every SM, best of 9 runs)"
+    return best
 
 
-def fp64_roofline(cutting, sweep_ms, fp32_peak):
-    """Roofline of an FP64-map sweep: its binning is FP32 arithmetic (against
-    the FP32 peak, as for FP32 maps); its heights run on the FP64 pipe, at
-    most one 5-flop height per evaluation (the phase form shares one among
-    the revolutions of a phase)."""
-    a32 = cutting * FP32_FLOPS_PER_EVAL / (sweep_ms / 1e3) / 1e12
+def issue_peak(sms, sm_mhz):
+    """Instruction-issue peak: 4 schedulers x 32 lanes per SM per clock."""
+    return sms * 128 * sm_mhz * 1e6
+
+
+def sweep_roofline(cutting, atomics, sweep_ms, peaks, sms, sm_mhz):
+    """The sweep against the units that bound it: FP32 arithmetic (the
+    survey's 23 flops per cutting evaluation against the measured FFMA rate),
+    instruction issue (24 algorithmic instruction lanes per cutting
+    evaluation against 128 lanes per SM per clock at the sampled clock) and
+    shared-memory atomics (the atomicMin updates against the measured
+    conflict-free rate)."""
+    t = sweep_ms / 1e3
+    a = cutting * FP32_FLOPS_PER_EVAL / t / 1e12
+    fp32 = peaks["fp32_flops"] / 1e12
+    ip = issue_peak(sms, sm_mhz)
+    ia = cutting * ISSUE_LANES_PER_EVAL / t
+    return {"bound": "alu", "achieved": a, "peak": fp32, "unit": "TFLOP/s", "frac": a / fp32,
+            "peak_source": "measured FP32 FFMA rate (libfsm_probe.so)",
+            "flops_per_cutting_eval": FP32_FLOPS_PER_EVAL, "kernel_flops_per_cutting_eval": KERNEL_FLOPS_PER_EVAL,
+            "issue": {"achieved": ia, "peak": ip, "unit": "instruction lanes/s", "frac": ia / ip,
+                      "lanes_per_cutting_eval": ISSUE_LANES_PER_EVAL,
+                      "peak_source": "%d SMs x 128 lanes x %.0f MHz (median SM clock of the timed region)"
+                                     % (sms, sm_mhz)},
+            "atoms": {"achieved": atomics / t, "peak": peaks["atoms32_ops"], "unit": "shared atomicMin/s",
+                      "frac": atomics / t / peaks["atoms32_ops"],
+                      "peak_source": "measured conflict-free 32-bit shared atomicMin rate"}}
+
+
+def fp64_roofline(cutting, atomics, sweep_ms, peaks, sms, sm_mhz):
+    """Roofline of an FP64-map sweep: its binning is FP32 arithmetic (as for
+    FP32 maps); its heights run on the FP64 pipe, at most one 5-flop height
+    per evaluation (the phase form shares one among the revolutions of a
+    phase), against the measured DFMA rate."""
+    r = sweep_roofline(cutting, atomics, sweep_ms, peaks, sms, sm_mhz)
     a64 = cutting * FP64_HEIGHT_FLOPS / (sweep_ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": a32, "peak": fp32_peak, "unit": "TFLOP/s", "frac": a32 / fp32_peak,
-            "flops_per_cutting_eval": FP32_FLOPS_PER_EVAL,
-            "fp64_heights": {"achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
-                             "frac": a64 / FP64_PEAK_TFLOPS, "flops_per_cutting_eval": FP64_HEIGHT_FLOPS,
-                             "note": "upper bound on the heights computed"}}
+    p64 = peaks["fp64_flops"] / 1e12
+    r["fp64_heights"] = {"achieved": a64, "peak": p64, "unit": "TFLOP/s (FP64)", "frac": a64 / p64,
+                         "flops_per_cutting_eval": FP64_HEIGHT_FLOPS, "peak_source": "measured DFMA rate",
+                         "note": "upper bound on the heights computed"}
+    r["atoms"]["peak"] = peaks["atoms64_ops"]
+    r["atoms"]["frac"] = r["atoms"]["achieved"] / peaks["atoms64_ops"]
+    r["atoms"]["peak_source"] = "measured conflict-free 64-bit shared atomicMin rate"
+    return r
 
 
 def time_steps(ctx, F, tool, proc, out, rough, K, flush, precision, events_sweep=True):
@@ -381,7 +431,7 @@ def side_wall_leg(ctx, F, flush, steps=3):
                             "ctas_per_sm": tuned["ctas_per_sm"]}}
 
 
-def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
+def batched_leg(ctx, F, n, steps, peaks, rank=0, ws_count=1):
     """The Latin-hypercube batch (FP32) in one persistent launch per precision,
     prepared once and replayed as a CUDA graph. With several ranks each rank
     takes a disjoint share of the surfaces (see paper_2603_28160_gb300.shard)."""
@@ -456,6 +506,12 @@ def batched_leg(ctx, F, n, steps, rank=0, ws_count=1):
             "surfaces": len(ws), "cells": cells, "cutting": cutting, "steps": steps, "ms_per_step": mean,
             "surfaces_per_s": len(ws) / (mean / 1e3), "value": cutting / (mean / 1e3), "unit": UNIT,
             "launch": "prepared batch replayed as one CUDA graph (planning, persistent sweep, roughness)",
+            "roofline": {"bound": "alu", "achieved": cutting * FP32_FLOPS_PER_EVAL / (mean / 1e3) / 1e12,
+                         "peak": peaks["fp32_flops"] / 1e12, "unit": "TFLOP/s",
+                         "frac": cutting * FP32_FLOPS_PER_EVAL / (mean / 1e3) / peaks["fp32_flops"],
+                         "flops_per_cutting_eval": FP32_FLOPS_PER_EVAL,
+                         "note": "whole replay time (planning, sweeps and roughness of every surface)",
+                         "peak_source": "measured FP32 FFMA rate (libfsm_probe.so)"},
             "vs_plain_fp64": {"surfaces": k, "fp32_batch_surfaces_per_s": k / (fp32_ms / 1e3),
                               "fp64_single_surface_surfaces_per_s": k / (fp64_ms / 1e3),
                               "speedup": fp64_ms / fp32_ms}}
@@ -547,7 +603,7 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
-def trajectory_leg(ctx, F, flush, steps=5):
+def trajectory_leg(ctx, F, flush, peaks, steps=5):
     """Trajectory map of the metric's workload (every time step of the 12
     passes, every tooth): planning, the per-phase argmin table and the
     records, timed as one call. Bound by the 32-byte record writes."""
@@ -576,9 +632,9 @@ def trajectory_leg(ctx, F, flush, steps=5):
     # one FP64 pose per record (15 flops) against GB300's FP64 rate binds
     # before the 32 B record write does
     return {"records": n, "bytes": n * F.TRAJ_BYTES, "ms": mean, "records_per_s": n / (mean / 1e3),
-            "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
-                         "frac": tf / FP64_PEAK_TFLOPS,
-                         "peak_source": "nominal FP64",
+            "roofline": {"bound": "alu", "achieved": tf, "peak": peaks["fp64_flops"] / 1e12,
+                         "unit": "TFLOP/s (FP64)", "frac": tf / (peaks["fp64_flops"] / 1e12),
+                         "peak_source": "measured DFMA rate (libfsm_probe.so)",
                          "note": "algorithmic work = 15 FP64 flops (one pose) per (step, tooth) record; call "
                                  "time includes planning and the per-phase argmin table",
                          "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
@@ -621,13 +677,32 @@ def filter_leg(ctx, F, flush, steps=3):
     return out
 
 
-def served_leg(ctx, F, seconds, rate, seed=5):
-    """Poisson request stream through fsm_submit/fsm_poll (continuous batching,
-    120 GB admission budget, 70 % FP32 / 30 % FP64, 0.25-25 Mcells)."""
+def busy_fraction(log):
+    """Share of the span of a batch log during which some batch was on the
+    device (union of the batches' device-time intervals)."""
+    iv = sorted((b["t_start_ms"], b["t_end_ms"]) for b in log)
+    if not iv:
+        return None
+    busy, cur_s, cur_e = 0.0, iv[0][0], iv[0][1]
+    for a, b in iv[1:]:
+        if a > cur_e:
+            busy += cur_e - cur_s
+            cur_s, cur_e = a, b
+        else:
+            cur_e = max(cur_e, b)
+    busy += cur_e - cur_s
+    span = iv[-1][1] - iv[0][0]
+    return busy / span if span > 0 else None
+
+
+def served_run(ctx, F, seconds, rate, setups, seed=5):
+    """One Poisson request stream through fsm_submit/fsm_poll (continuous
+    batching, 120 GB admission budget, 70 % FP32 / 30 % FP64, 0.25-25 Mcells),
+    every result polled and released in arrival order."""
     import threading
     from paper_2603_28160_gb300 import workloads as W
     n = max(1, int(seconds * rate))
-    reqs = W.serve_stream(n, seed=seed)
+    reqs = W.serve_stream(n, seed=seed, n_setups=setups or None)
     arrivals = W.poisson_arrivals(n, rate, seed=seed)
     handles = [(ctx.tool(w.tool), ctx.process(w.process)) for w in reqs]
     ctx.server_start(budget_bytes=120 << 30, n_streams=4, max_batch=64)
@@ -644,25 +719,76 @@ def served_leg(ctx, F, seconds, rate, seed=5):
             ctx.release(tickets[i])
         done.set()
 
-    th = threading.Thread(target=collect)
-    th.start()
-    t0 = time.perf_counter()
-    for i in range(n):
-        wait = arrivals[i] - (time.perf_counter() - t0)
-        if wait > 0:
-            time.sleep(wait)
-        tickets[i] = ctx.submit(*handles[i])
-    done.wait()
-    elapsed = time.perf_counter() - t0
-    th.join()
-    ctx.server_stop()
+    try:
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(n):
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets[i] = ctx.submit(*handles[i])
+        done.wait()
+        elapsed = time.perf_counter() - t0
+        th.join()
+        stats = ctx.server_stats()
+        log = ctx.server_batches()
+    finally:
+        ctx.server_stop()
     srt = sorted(lat)
-    return {"workload": "serve_stream: Poisson arrivals at %.0f/s for %.0f s, batch-distribution tools, "
-                        "0.25-25 Mcells, 30%% FP64" % (rate, seconds),
-            "requests": n, "fp64_requests": sum(w.process.precision == "fp64" for w in reqs),
-            "elapsed_s": elapsed, "surfaces_per_s": n / elapsed,
+    return {"rate": rate, "requests": n, "fp64_requests": sum(w.process.precision == "fp64" for w in reqs),
+            "cells": sum(w.process.cells for w in reqs), "elapsed_s": elapsed, "surfaces_per_s": n / elapsed,
+            "cells_per_s": sum(w.process.cells for w in reqs) / elapsed,
             "p50_ms": 1e3 * srt[len(srt) // 2], "p99_ms": 1e3 * srt[min(n - 1, int(0.99 * n))],
-            "queue_p50_ms": 1e3 * sorted(queue)[n // 2], "budget_gb": 120, "streams": 4}
+            "queue_p50_ms": 1e3 * sorted(queue)[n // 2], "queue_p99_ms": 1e3 * sorted(queue)[min(n - 1, int(0.99 * n))],
+            "batches": stats["batches"], "mean_batch": n / max(1, stats["batches"]),
+            "table_hits": stats["table_hits"], "table_misses": stats["table_misses"],
+            "bytes_peak_gb": stats["bytes_peak"] / 2 ** 30, "queue_peak": stats["queue_peak"],
+            "device_busy": busy_fraction(log)}
+
+
+def served_leg(ctx, F, seconds, rates, setups, seed=5):
+    """Served stream at increasing Poisson rates: throughput tracks the
+    arrivals until the server saturates; the highest throughput reached is
+    its capacity on this request mix."""
+    import torch
+    from paper_2603_28160_gb300 import workloads as W
+    runs = [served_run(ctx, F, seconds, r, setups, seed) for r in rates]
+    best = max(runs, key=lambda r: r["surfaces_per_s"])
+    # the plain FP64 single-surface form on the same requests (the first 64
+    # of the stream, all in FP64, one fsm_predict_surface + fsm_roughness at a
+    # time), for the served-versus-plain comparison
+    k = 64
+    sub = [W.Workload(w.name, w.tool, w.process.replace(precision="fp64"))
+           for w in W.serve_stream(k, seed=seed, n_setups=setups or None)]
+    rough = torch.zeros(F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+    hs = [(ctx.tool(w.tool), ctx.process(w.process)) for w in sub]
+    out = torch.empty(max(w.process.cells for w in sub), dtype=torch.float64, device="cuda")
+    for (t_, p_), w in list(zip(hs, sub))[:2]:  # warm
+        ctx.predict_surface(t_, p_, out[:w.process.cells])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for (t_, p_), w in zip(hs, sub):
+        o_ = out[:w.process.cells].view(w.process.ny, w.process.nx)
+        ctx.predict_surface(t_, p_, o_)
+        ctx.roughness_async(o_, F.FSM_FP64, rough)
+    e1.record()
+    torch.cuda.synchronize()
+    plain = k / (e0.elapsed_time(e1) / 1e3)
+    del out
+    torch.cuda.empty_cache()
+    sat = [r for r in runs if r["surfaces_per_s"] < 0.9 * r["rate"]]
+    return {"workload": "serve_stream: Poisson arrivals, batch-distribution requests (%s), 0.25-25 Mcells, "
+                        "30%% FP64, %g s per rate" % ("tools and set-ups from a catalogue of %d" % setups if setups
+                                                     else "every tool and set-up drawn afresh", seconds),
+            "budget_gb": 120, "streams": 4, "max_batch": 64, "rates": runs,
+            "capacity_surfaces_per_s": best["surfaces_per_s"], "capacity_at_rate": best["rate"],
+            "saturated": bool(sat), "saturation_rate": sat[0]["rate"] if sat else None,
+            "surfaces_per_s": best["surfaces_per_s"], "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
+            "vs_plain_fp64": {"fp64_single_surface_surfaces_per_s": plain, "requests": k,
+                              "served_capacity_over_plain_fp64": best["surfaces_per_s"] / plain,
+                              "note": "the first %d requests of the stream in FP64, one surface at a time" % k}}
 
 
 def gb300_arm(args):
@@ -707,6 +833,11 @@ def gb300_arm(args):
     p50 = statistics.median(step_ms)
     p99 = sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]
     sweep_mean = sum(sweep_ms) / len(sweep_ms)
+    # the measured rates of the units the kernels are bound by (outside the
+    # timed region) and the clock the timed region ran at
+    peaks = unit_peaks(local)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz_live = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
 
     # end to end through the C ABI with host buffers: descriptors cross the
     # ABI and the map plus the roughness record are copied back to pinned
@@ -754,13 +885,14 @@ def gb300_arm(args):
         ctx.predict_surface(t64, p64, out64, counters=cnt64)
         torch.cuda.synchronize()
         cut64 = int(cnt64[1].item())
+        at64 = int(cnt64[3].item())
         k64 = max(3, args.steps // 10)
         s64, sw64 = time_steps(ctx, F, t64, p64, out64, rough, k64, flush, "fp64")
         ms64 = max_over_ranks(sum(s64) / len(s64), ws)
         sw64_mean = sum(sw64) / len(sw64)
         fp64 = {"value": ws * cut64 / (ms64 / 1e3), "ms_per_step": ms64, "steps": k64,
                 "sweep_ms": sw64_mean, "cutting": cut64,
-                "roofline": fp64_roofline(cut64, sw64_mean, fp32_alu_peak(torch, local)[0])}
+                "roofline": fp64_roofline(cut64, at64, sw64_mean, peaks, sms, sm_mhz_live)}
         del out64
 
     large = None
@@ -774,31 +906,31 @@ def gb300_arm(args):
         side = side_wall_leg(ctx, F, flush)
     traj = None
     if not args.skip_trajectory and rank == 0:
-        traj = trajectory_leg(ctx, F, flush)
+        traj = trajectory_leg(ctx, F, flush, peaks)
     paper = None
     if not args.skip_paper and rank == 0:
         paper = paper_case2_leg(ctx, F, flush)
     batched = None
     if not args.skip_batch:
-        batched = batched_leg(ctx, F, args.batch_size, args.batch_steps, rank, ws)
+        batched = batched_leg(ctx, F, args.batch_size, args.batch_steps, peaks, rank, ws)
         if ws > 1:
             bms = max_over_ranks(batched["ms_per_step"], ws)
             batched["ms_per_step_max_over_ranks"] = bms
             batched["surfaces_per_s"] = args.batch_size / (bms / 1e3)
     served = None
     if not args.skip_serve and rank == 0:
-        served = served_leg(ctx, F, args.serve_seconds, args.serve_rate)
+        served = served_leg(ctx, F, args.serve_seconds, [float(r) for r in args.serve_rates.split(",")],
+                            args.serve_setups)
     barrier(ws)
 
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel (the FP32 sweep): algorithmic FP32 flops
-    # per cutting evaluation / live event time of the sweep launch
-    # (FP64 maps bin with the same FP32 arithmetic; their FP64 heights are
-    # reported beside it against the FP64 rate)
-    peak, peak_note = fp32_alu_peak(torch, local, clk.get("sm_max_mhz"))
-    achieved = cutting * FP32_FLOPS_PER_EVAL / (sweep_mean / 1e3) / 1e12
+    # roofline of the dominant kernel (the sweep): algorithmic work per
+    # cutting evaluation / live event time of the sweep launch, against the
+    # measured unit rates
+    roof = (sweep_roofline if args.precision == "fp32" else fp64_roofline)(cutting, atomics, sweep_mean, peaks, sms,
+                                                                           sm_mhz_live)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sweep_%s_raster_ball_d10.json" % args.precision)
     if os.path.exists(prof):
@@ -808,6 +940,7 @@ def gb300_arm(args):
                 traffic = pj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
+    roof.update({"traffic": traffic, "kernel": "sweep_kernel<%s>" % args.precision.upper(), "sweep_ms": sweep_mean})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -818,10 +951,8 @@ def gb300_arm(args):
         "work": {"cutting": cutting, "evaluated": evaluated, "rebinned_fp64": rebinned, "atomics": atomics,
                  "trajectory_points": w.trajectory_points,
                  "trajectory_points_per_s": ws * w.trajectory_points / (ms / 1e3)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "sweep_kernel<%s>" % args.precision.upper(),
-                     "sweep_ms": sweep_mean, "flops_per_cutting_eval": FP32_FLOPS_PER_EVAL,
-                     "peak_source": peak_note},
+        "roofline": roof,
+        "unit_peaks": peaks,
         "e2e": {"value": ws * cutting / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3,
                 "steps": e2e_steps, "streams": nbuf,

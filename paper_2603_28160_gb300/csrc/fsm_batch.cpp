@@ -57,8 +57,8 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     fsm_process_desc p64 = *procs[0], p32 = *procs[0];
     p64.precision = FSM_FP64;
     p32.precision = FSM_FP32;
-    L->sh64 = pick_shape(p64, opts, procs, n, ctx->sm_count);
-    L->sh32 = pick_shape(p32, opts, procs, n, ctx->sm_count);
+    L->sh64 = pick_shape(p64, opts, procs, n, ctx->sm_count, tools);
+    L->sh32 = pick_shape(p32, opts, procs, n, ctx->sm_count, tools);
     fsm_status rc;
     if (L->n64 && (rc = sweep_config(ctx, FSM_FP64, L->sh64, &L->smem64, &L->bps64)) != FSM_OK) return rc;
     if (L->n32 && (rc = sweep_config(ctx, FSM_FP32, L->sh32, &L->smem32, &L->bps32)) != FSM_OK) return rc;

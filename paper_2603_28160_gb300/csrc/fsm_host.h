@@ -104,9 +104,11 @@ size_t align256(size_t v);
 // Key of the autotuner's table for a tool/process pair.
 std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p);
 // Sweep shape: the caller's override, else the default ladder step for this
-// precision given the tiles of the surfaces in `group` (may be NULL).
+// precision given the tiles of the surfaces in `group` (may be NULL); with
+// `tools` (one per group entry), a lone surface of this precision gets a
+// tile width aligned to its feed per revolution.
 Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm_process_desc* const* group = nullptr,
-                 int n_group = 0, int sm_count = 0);
+                 int n_group = 0, int sm_count = 0, const fsm_tool_desc* const* tools = nullptr);
 // Fill a device plan from the descriptors. Table pointers are laid out from
 // `base`; returns the table bytes (call with base = NULL to size).
 size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Shape& sh, Surface* s,

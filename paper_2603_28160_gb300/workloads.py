@@ -335,13 +335,29 @@ def lhs_batch(n: int = 4096, seed: int = 4096, precision: str = "fp32",
 
 
 def serve_stream(n: int, seed: int = 5, fp64_fraction: float = 0.3, rot_step_deg: float = 0.1,
-                 n_edge: int = 200, cells_range=(0.25e6, 25e6)) -> List[Workload]:
+                 n_edge: int = 200, cells_range=(0.25e6, 25e6), n_setups: Optional[int] = None) -> List[Workload]:
     """Requests of a served stream: tools and cutting conditions drawn from
     the batch distribution (seeded Latin hypercube), square patches whose
     cell count is log-uniform in [0.25, 25] Mcells at 1-5 um pitch, and a
-    seeded 30 % of the requests in FP64 (the rest FP32)."""
+    seeded 30 % of the requests in FP64 (the rest FP32).
+
+    n_setups: None draws every request's tool and set-up afresh. A number
+    draws them from a seeded catalogue of that many set-ups -- tool, depth of
+    cut, lead, tilt, step angle and pitch, as a dataset generator sweeping
+    feeds and step-overs over a fixed tool set would -- while feed,
+    step-over, patch size and precision stay per request."""
     rng = np.random.default_rng(seed + 1000)
     base = lhs_batch(n=n, seed=seed, rot_step_deg=rot_step_deg, n_edge=n_edge)
+    if n_setups is not None:
+        cat = lhs_batch(n=n_setups, seed=seed + 7, rot_step_deg=rot_step_deg, n_edge=n_edge)
+        pick = np.random.default_rng(seed + 2000).integers(0, n_setups, size=n)
+        mixed = []
+        for w, k in zip(base, pick):
+            c = cat[int(k)]
+            mixed.append(Workload(w.name, c.tool, w.process.replace(
+                ap=c.process.ap, lead_deg=c.process.lead_deg, tilt_deg=c.process.tilt_deg,
+                rot_step_deg=c.process.rot_step_deg, pitch=c.process.pitch, phase0_deg=c.process.phase0_deg)))
+        base = mixed
     out = []
     for w in base:
         t, p = w.tool, w.process
