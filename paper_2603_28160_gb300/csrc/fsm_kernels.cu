@@ -381,7 +381,12 @@ struct WarpScratch {
 constexpr int kPassCache = 64;
 
 // Per-tile values shared by all warps, computed once per tile in FP64.
+// Tasks of a tile whose group-reject outcome is tabulated at the tile's
+// start (one bit each; later tasks are tested as they are taken).
+constexpr int kTaskBits = 4096;
+
 struct TileShared {
+    uint32_t accept[kTaskBits / 32];          // task t may have runs here (group reject passed)
     float ylo[kPassCache], yhi[kPassCache];  // mm, for the enumeration
     float dy[kPassCache];                     // pass line - tile origin y, in cells
     float dx_hi, dx_lo;  // pass_x0 - tile origin x in cells, as a float pair
@@ -869,18 +874,25 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         divmod_small(2 * L, len, inv_len, &d2l, &r2l);
         divmod_small(L, len, inv_len, &dl, &rl);
         divmod_small(hl + r.first_off, len, inv_len, &qa, &oa);
+        // phase-table entries of the next iteration are loaded one iteration
+        // ahead (the table does not stay in the L1 left beside a large tile)
+        int32_t ob = oa + rl, qb = qa + dl;
+        if (ob >= len) { ob -= len; ++qb; }
+        float2 ca_next = __ldg(ph32 + r.m0 + oa), cb_next = __ldg(ph32 + r.m0 + ob);
         for (int base = 0; base < tmax; base += 2 * L) {
             const int ta = base + hl, tb = ta + L;
             const bool va = ta < tot, vb = tb < tot;
-            int32_t ob = oa + rl, qb = qa + dl;
-            if (ob >= len) { ob -= len; ++qb; }
             const int32_t dsa = ta + qa * gap, dsb = tb + qb * gap;  // steps after the run's first item
             const int32_t ma = r.m0 + oa, mb = r.m0 + ob;             // < 2S: the table holds two turns
+            const float2 ca = ca_next, cb = cb_next;
             oa += r2l;
             qa += d2l;
             if (oa >= len) { oa -= len; ++qa; }
-            const float2 ca = __ldg(ph32 + ma);
-            const float2 cb = __ldg(ph32 + mb);
+            ob = oa + rl;
+            qb = qa + dl;
+            if (ob >= len) { ob -= len; ++qb; }
+            ca_next = __ldg(ph32 + r.m0 + oa);
+            cb_next = __ldg(ph32 + r.m0 + ob);
             cnt.evaluated += (unsigned)va + (unsigned)vb;
             const float za = fmaf(ca.x, uz, fmaf(ca.y, vz, zb));
             const float zb2 = fmaf(cb.x, uz, fmaf(cb.y, vz, zb));
@@ -1153,6 +1165,25 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
 
         const int G = (sf.E + 31) / 32;
         const int n_tasks = sf.n_passes * sf.n_teeth * G;
+        // group reject of the tile's first tasks, a warp per 32 tasks: the
+        // bounds loads of many tasks are in flight at once, and a warp then
+        // skips rejected tasks with one shared load instead of a global one
+        const int n_bits = min(n_tasks, kTaskBits);
+        for (int w0 = warp * 32; w0 < n_bits; w0 += nwarps * 32) {
+            const int t = w0 + lane;
+            bool ok = false;
+            if (t < n_bits) {
+                const int p = t / (sf.n_teeth * G);
+                const int rem = t - p * sf.n_teeth * G;
+                float ylo, yhi, dyp;
+                pass_band(sf, tc, ts, p, &ylo, &yhi, &dyp);
+                const float4 gb = sf.groups[rem];  // rem = K * G + g
+                ok = !(gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi);
+            }
+            const unsigned bits = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) ts.accept[w0 >> 5] = bits;
+        }
+        __syncthreads();
         const double tile_x1 = tc.X0 + (double)tc.txc * sf.pitch;
         const double pass_x1 = sf.pass_x0 + (double)(sf.steps_per_pass - 1) * sf.fs;
         const bool x_miss = (pass_x1 + sf.reach_x < tc.X0 - 1e-3) || (sf.pass_x0 - sf.reach_x > tile_x1 + 1e-3);
@@ -1164,10 +1195,13 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             const int p = task / (sf.n_teeth * G);
             const int rem = task - p * sf.n_teeth * G;
             const int K = rem / G, g = rem - K * G;
+            if (task < kTaskBits && !((ts.accept[task >> 5] >> (task & 31)) & 1u)) continue;  // warp-uniform
             float ylo, yhi, dyp;
             pass_band(sf, tc, ts, p, &ylo, &yhi, &dyp);
-            const float4 gb = sf.groups[K * G + g];
-            if (gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi) continue;  // warp-uniform
+            if (task >= kTaskBits) {
+                const float4 gb = sf.groups[K * G + g];
+                if (gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi) continue;  // warp-uniform
+            }
             float4 t4[3];
             float2 pt;
             if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4, pt)) continue;
