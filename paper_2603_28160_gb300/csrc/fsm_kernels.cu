@@ -813,7 +813,11 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
 // steps after the run's first item; the lane advances (q, offset) by 2L
 // items per iteration without a division.
 constexpr int kItemLanes = 8;
-template <bool F64>
+#ifndef FSM_ITEM_CHAINS
+#define FSM_ITEM_CHAINS 2
+#endif
+constexpr int kItemChains = FSM_ITEM_CHAINS;  // items per lane and iteration (independent chains)
+template <bool F64, int U = kItemChains>
 __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
                                             int g, int p, WarpScratch& ws, AmbQueue* aq, const float4 (&t4)[3],
                                             float2 pt, Counters& cnt) {
@@ -870,80 +874,89 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
         const int32_t len = r.len, gap = S - len;
         const float inv_len = 1.0f / (float)len;
-        int32_t d2l, r2l, dl, rl, qa, oa;  // 2L and L items in (revolutions, phases); item hl
-        divmod_small(2 * L, len, inv_len, &d2l, &r2l);
+        // lane hl takes items hl + k L (k < U) of every U L: item index
+        // (revolution q, phase offset o), advanced by L items between its U
+        // chains and by U L items per iteration without a division
+        int32_t dUL, rUL, dl, rl, q0, o0;
+        divmod_small(U * L, len, inv_len, &dUL, &rUL);
         divmod_small(L, len, inv_len, &dl, &rl);
-        divmod_small(hl + r.first_off, len, inv_len, &qa, &oa);
-        // phase-table entries of the next iteration are loaded one iteration
-        // ahead (the table does not stay in the L1 left beside a large tile)
-        int32_t ob = oa + rl, qb = qa + dl;
-        if (ob >= len) { ob -= len; ++qb; }
-        float2 ca_next = __ldg(ph32 + r.m0 + oa), cb_next = __ldg(ph32 + r.m0 + ob);
-        for (int base = 0; base < tmax; base += 2 * L) {
-            const int ta = base + hl, tb = ta + L;
-            const bool va = ta < tot, vb = tb < tot;
-            const int32_t dsa = ta + qa * gap, dsb = tb + qb * gap;  // steps after the run's first item
-            const int32_t ma = r.m0 + oa, mb = r.m0 + ob;             // < 2S: the table holds two turns
-            const float2 ca = ca_next, cb = cb_next;
-            oa += r2l;
-            qa += d2l;
-            if (oa >= len) { oa -= len; ++qa; }
-            ob = oa + rl;
-            qb = qa + dl;
-            if (ob >= len) { ob -= len; ++qb; }
-            ca_next = __ldg(ph32 + r.m0 + oa);
-            cb_next = __ldg(ph32 + r.m0 + ob);
-            cnt.evaluated += (unsigned)va + (unsigned)vb;
-            const float za = fmaf(ca.x, uz, fmaf(ca.y, vz, zb));
-            const float zb2 = fmaf(cb.x, uz, fmaf(cb.y, vz, zb));
-            const float fxa = fmaf((float)dsa, fs32, r.dxA) + fmaf(ca.x, ux, fmaf(ca.y, vx, wx));
-            const float fxb = fmaf((float)dsb, fs32, r.dxA) + fmaf(cb.x, ux, fmaf(cb.y, vx, wx));
-            const float fya = dyp + fmaf(ca.x, uy, fmaf(ca.y, vy, wy));
-            const float fyb = dyp + fmaf(cb.x, uy, fmaf(cb.y, vy, wy));
-            // floor by one conversion each, the fraction by subtraction
-            const int ia = __float2int_rd(fxa), ka = __float2int_rd(fya);
-            const int ib = __float2int_rd(fxb), kb = __float2int_rd(fyb);
-            const float rxa = fxa - __int2float_rn(ia), rya = fya - __int2float_rn(ka);
-            const float rxb = fxb - __int2float_rn(ib), ryb = fyb - __int2float_rn(kb);
-            Cell ea, eb;
-            bool cut_a, cut_b;
-            if constexpr (F64) {  // below the stock by the FP64 height
-                ea = cell_key(height64(__ldg(ph64 + ma), uz64, vz64, wz64, zr));
-                eb = cell_key(height64(__ldg(ph64 + mb), uz64, vz64, wz64, zr));
-                cut_a = va && ea < below_key;
-                cut_b = vb && eb < below_key;
+        divmod_small(hl + r.first_off, len, inv_len, &q0, &o0);
+        int32_t oi[U], qi[U];
+        float2 cn[U];  // phase-table entries of the next iteration, loaded one iteration ahead
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (k == 0) {
+                oi[0] = o0;
+                qi[0] = q0;
             } else {
-                cut_a = va && za < 0.f;
-                cut_b = vb && zb2 < 0.f;
-                ea = cell_key(za);
-                eb = cell_key(zb2);
+                oi[k] = oi[k - 1] + rl;
+                qi[k] = qi[k - 1] + dl;
+                if (oi[k] >= len) { oi[k] -= len; ++qi[k]; }
             }
-            const bool in_a = cut_a && (unsigned)ia < (unsigned)txc && (unsigned)ka < (unsigned)tyc;
-            const bool in_b = cut_b && (unsigned)ib < (unsigned)txc && (unsigned)kb < (unsigned)tyc;
-            // within gc of a cell boundary: |r - 1/2| > 1/2 - gc on either axis
-            const bool amb_a = fmaxf(fabsf(rxa - 0.5f), fabsf(rya - 0.5f)) > hg;
-            const bool amb_b = fmaxf(fabsf(rxb - 0.5f), fabsf(ryb - 0.5f)) > hg;
-            const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
-            // FP32 maps count the FP32 cell; FP64 maps count ambiguous points when re-binned
-            cnt.cutting += F64 ? (unsigned)upd_a + (unsigned)upd_b : (unsigned)in_a + (unsigned)in_b;
-            const int cia = ka * tile_x + ia, cib = kb * tile_x + ib;
-            const Cell cva = upd_a ? cells[cia] : (Cell)0;
-            const Cell cvb = upd_b ? cells[cib] : (Cell)0;
-            if (upd_a && ea < cva) {
-                atomicMin(cells + cia, ea);
-                ++cnt.atomics;
+            cn[k] = __ldg(ph32 + r.m0 + oi[k]);
+        }
+        for (int base = 0; base < tmax; base += U * L) {
+            int32_t ds[U], mi[U];
+            float2 cs[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                ds[k] = base + hl + k * L + qi[k] * gap;  // steps after the run's first item
+                mi[k] = r.m0 + oi[k];                      // < 2S: the table holds two turns
+                cs[k] = cn[k];
+                oi[k] += rUL;
+                qi[k] += dUL;
+                if (oi[k] >= len) { oi[k] -= len; ++qi[k]; }
+                cn[k] = __ldg(ph32 + r.m0 + oi[k]);
             }
-            if (upd_b && eb < cvb) {
-                atomicMin(cells + cib, eb);
-                ++cnt.atomics;
+            bool push_any = false;
+            bool pk[U];
+            int ik[U], kk[U];
+            float rxk[U], ryk[U], zk[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const bool v = base + hl + k * L < tot;
+                const float2 c = cs[k];
+                cnt.evaluated += (unsigned)v;
+                const float z = fmaf(c.x, uz, fmaf(c.y, vz, zb));
+                const float fx = fmaf((float)ds[k], fs32, r.dxA) + fmaf(c.x, ux, fmaf(c.y, vx, wx));
+                const float fy = dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
+                // floor by one conversion each, the fraction by subtraction
+                const int ix = __float2int_rd(fx), ky = __float2int_rd(fy);
+                const float rx = fx - __int2float_rn(ix), ry = fy - __int2float_rn(ky);
+                Cell e;
+                bool cut;
+                if constexpr (F64) {  // below the stock by the FP64 height
+                    e = cell_key(height64(__ldg(ph64 + mi[k]), uz64, vz64, wz64, zr));
+                    cut = v && e < below_key;
+                } else {
+                    cut = v && z < 0.f;
+                    e = cell_key(z);
+                }
+                const bool in = cut && (unsigned)ix < (unsigned)txc && (unsigned)ky < (unsigned)tyc;
+                // within gc of a cell boundary: |r - 1/2| > 1/2 - gc on either axis
+                const bool amb = fmaxf(fabsf(rx - 0.5f), fabsf(ry - 0.5f)) > hg;
+                const bool upd = in && !amb;
+                // FP32 maps count the FP32 cell; FP64 maps count ambiguous points when re-binned
+                cnt.cutting += F64 ? (unsigned)upd : (unsigned)in;
+                const int ci = ky * tile_x + ix;
+                const Cell cv = upd ? cells[ci] : (Cell)0;
+                if (upd && e < cv) {
+                    atomicMin(cells + ci, e);
+                    ++cnt.atomics;
+                }
+                pk[k] = cut && amb && ix >= -M && ix <= txc - 1 + M && ky >= -M && ky <= tyc - 1 + M;
+                push_any |= pk[k];
+                ik[k] = ix;
+                kk[k] = ky;
+                rxk[k] = rx;
+                ryk[k] = ry;
+                zk[k] = z;
             }
-            const bool pa = cut_a && amb_a && ia >= -M && ia <= txc - 1 + M && ka >= -M && ka <= tyc - 1 + M;
-            const bool pb = cut_b && amb_b && ib >= -M && ib <= txc - 1 + M && kb >= -M && kb <= tyc - 1 + M;
-            if (__any_sync(0xffffffffu, pa || pb)) {
-                push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ka, rxa, rya, gc, za, eps_z, sA + dsa, ma, idx, an,
-                                    qn, cnt);
-                push_ambiguous<F64>(sf, tc, ws, aq, p, pb, ib, kb, rxb, ryb, gc, zb2, eps_z, sA + dsb, mb, idx, an,
-                                    qn, cnt);
+            if (__any_sync(0xffffffffu, push_any)) {
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pk[k], ik[k], kk[k], rxk[k], ryk[k], gc, zk[k], eps_z,
+                                        sA + ds[k], mi[k], idx, an, qn, cnt);
             }
         }
     }
