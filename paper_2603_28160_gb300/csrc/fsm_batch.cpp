@@ -119,8 +119,10 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
     L->off_cb32 = off;  off += align256(sizeof(int) * (L->n32 + 1));
     const size_t blob_end = off;
     // per group: 7 partial sums per chunk, then the sync words of its maps
-    L->off_part64 = off; off += align256(sizeof(double) * 7 * (size_t)L->chunks64 + rough_sync_bytes(L->n64));
-    L->off_part32 = off; off += align256(sizeof(double) * 7 * (size_t)L->chunks32 + rough_sync_bytes(L->n32));
+    L->off_part64 = off;
+    off += align256(sizeof(double) * rough_part_doubles(L->chunks64, L->n64, L->max_prof) + rough_sync_bytes(L->n64));
+    L->off_part32 = off;
+    off += align256(sizeof(double) * rough_part_doubles(L->chunks32, L->n32, L->max_prof) + rough_sync_bytes(L->n32));
     L->off_tables = off; off += tables;
     L->total = off;
     if (!base) return FSM_OK;
@@ -184,12 +186,14 @@ fsm_status run_batch(fsm_ctx* ctx, const BatchLayout& L, char* base, cudaStream_
         const RoughJob* jobs = (const RoughJob*)(base + L.off_jobs);
         if (L.n64 && (e = launch_roughness_jobs(FSM_FP64, jobs, L.n64, (const int*)(base + L.off_cb64), L.chunks64,
                                                 L.max_prof, (double*)(base + L.off_part64),
-                                                base + L.off_part64 + sizeof(double) * 7 * (size_t)L.chunks64,
+                                                base + L.off_part64 +
+                                                    sizeof(double) * rough_part_doubles(L.chunks64, L.n64, L.max_prof),
                                                 st)) != cudaSuccess)
             return cuda_fail(e, "roughness (FP64)");
         if (L.n32 && (e = launch_roughness_jobs(FSM_FP32, jobs + L.n64, L.n32, (const int*)(base + L.off_cb32),
                                                 L.chunks32, L.max_prof, (double*)(base + L.off_part32),
-                                                base + L.off_part32 + sizeof(double) * 7 * (size_t)L.chunks32,
+                                                base + L.off_part32 +
+                                                    sizeof(double) * rough_part_doubles(L.chunks32, L.n32, L.max_prof),
                                                 st)) !=
                          cudaSuccess)
             return cuda_fail(e, "roughness (FP32)");

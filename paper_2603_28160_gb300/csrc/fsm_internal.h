@@ -52,7 +52,8 @@ cudaError_t launch_trajectory(const Surface* d_surf, int S, int n_teeth, long lo
 
 // Roughness of a set of maps of one precision. Map j is cut into
 // ceil(n/kChunk) chunks; d_chunk_base[j] is its first chunk (n_jobs+1
-// entries). d_part: 7 * total_chunks doubles of scratch; d_sync:
+// entries). d_part: rough_part_doubles(total_chunks, n_jobs, max_profiles)
+// doubles of scratch; d_sync:
 // rough_sync_bytes(n_jobs) of scratch (8-byte aligned; cleared by the call).
 // max_profiles = the largest n_rows + n_cols of any job. One memset and two
 // launches.
@@ -64,6 +65,9 @@ struct RoughJob {
     fsm_roughness_out* out;
 };
 size_t rough_sync_bytes(int n_jobs);
+// Doubles of roughness partials: 7 per chunk, then 4 per profile segment
+// (5 segments of max_profiles profiles per job).
+size_t rough_part_doubles(int total_chunks, int n_jobs, int max_profiles);
 cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_jobs, const int* d_chunk_base,
                                   int total_chunks, int max_profiles, double* d_part, void* d_sync,
                                   cudaStream_t st);

@@ -1369,6 +1369,35 @@ __device__ __forceinline__ double block_sum_df(float2 v, double* sh /*[32]*/) {
     return (double)x.x + (double)x.y;
 }
 
+// Four block sums of double-float values in one fixed tree (one pair of
+// barriers instead of four); thread 0 gets the results. sh: 128 doubles.
+__device__ __forceinline__ void block_sum_df4(const float2 (&v)[4], double* sh, double (&out)[4]) {
+    float2* s2 = reinterpret_cast<float2*>(sh);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    float2 a[4] = {v[0], v[1], v[2], v[3]};
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            a[k] = df_add(a[k], make_float2(__shfl_xor_sync(0xffffffffu, a[k].x, o),
+                                            __shfl_xor_sync(0xffffffffu, a[k].y, o)));
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s2[4 * warp + k] = a[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = lane < nw ? s2[4 * lane + k] : make_float2(0.f, 0.f);
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                a[k] = df_add(a[k], make_float2(__shfl_xor_sync(0xffffffffu, a[k].x, o),
+                                                __shfl_xor_sync(0xffffffffu, a[k].y, o)));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = (double)a[k].x + (double)a[k].y;
+    }
+}
+
 __device__ __forceinline__ int find_job(const int* base, int n, int b) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1438,16 +1467,18 @@ __device__ __forceinline__ void job_mean_if_last(const RoughJob* __restrict__ jo
 }
 
 template <typename T>
-__device__ void profile_block(const RoughJob* __restrict__ jobs, int pb, int per_job, double* sh);
+__device__ void profile_seg1(const RoughJob* __restrict__ jobs, int item, int per_job, double* ppart, double* sh);
 __device__ void finalize_job(const RoughJob* __restrict__ jobs, const int* __restrict__ chunk_base,
-                             const double* part, const double* part2, int j, double mu, double* sh);
+                             const double* part, const double* part2, int j, double mu, int per_job,
+                             const double* ppart, double* sh);
+__device__ void finalize_profiles(const RoughJob& jb, int j, int per_job, const double* ppart);
 
 template <typename T>
 __device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, int n_jobs,
                                             const int* __restrict__ chunk_base, double* part, int total_chunks,
                                             int per_job, void* sync, int b, double* sh) {
-    if (b >= total_chunks) {  // items past the chunks are profiles
-        profile_block<T>(jobs, b - total_chunks, per_job, sh);
+    if (b >= total_chunks) {  // items past the chunks are profile segments
+        profile_seg1<T>(jobs, b - total_chunks, per_job, part + 7 * (size_t)total_chunks, sh);
         return;
     }
     const int j = find_job(chunk_base, n_jobs, b);
@@ -1486,7 +1517,8 @@ __device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, i
 // the areal values. Chunk partials written by other blocks of the running
 // launch are read past L1.
 __device__ void finalize_job(const RoughJob* __restrict__ jobs, const int* __restrict__ chunk_base,
-                             const double* part, const double* part2, int j, double mu, double* sh) {
+                             const double* part, const double* part2, int j, double mu, int per_job,
+                             const double* ppart, double* sh) {
     const RoughJob jb = jobs[j];
     const int c0 = chunk_base[j], c1 = chunk_base[j + 1];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1522,112 +1554,188 @@ __device__ void finalize_job(const RoughJob* __restrict__ jobs, const int* __res
         out->n_rows = jb.n_rows;
         out->n_cols = jb.n_cols;
     }
+    finalize_profiles(jb, j, per_job, ppart);
 }
 
-// Profiles: block index pb handles profile q = pb mod per_job of job
-// j = pb / per_job (rows first, then columns).
-template <typename T>
-__device__ void profile_block(const RoughJob* __restrict__ jobs, int pb, int per_job, double* sh) {
-    const int j = pb / per_job, q = pb - j * per_job;
-    const RoughJob jb = jobs[j];
-    if (q >= jb.n_rows + jb.n_cols) return;
-    const bool row = q < jb.n_rows;
-    const int r = row ? q : q - jb.n_rows;
-    const int nx = jb.nx, ny = jb.ny;
-    const int L = row ? nx : ny;
-    int fixed;
-    size_t stride, base;
-    if (row) {
-        fixed = (int)(((long long)(2 * r + 1) * ny) / (2 * jb.n_rows));
-        base = (size_t)fixed * nx;
-        stride = 1;
+// Profiles, cut into the 5 segments of Rz ([floor(s L/5), floor((s+1) L/5))),
+// one block per segment in each pass: pass 1 takes each segment's sum, min
+// and max, pass 2 its sum of |z - profile mean| (the mean from the five sums,
+// in segment order, identical in every block). Item i of a pass is segment
+// i mod 5 of profile (i / 5) mod per_job (rows first, then columns) of job
+// i / (5 per_job). Partials: ppart[((j per_job + q) 5 + seg) 4 + {sum, min,
+// max, |dev|}].
+constexpr int kRzSegments = 5;
+// Resident blocks per SM the roughness passes are compiled for (registers
+// capped so a 25 Mcell map's chunks and profile segments fit in one wave).
+constexpr int kRoughBlocksPerSm = 6;
+
+struct ProfileSeg {
+    bool valid, row;
+    int r, fixed, L, lo, hi;  // profile r of its kind at row/column `fixed`, length L, segment [lo, hi)
+    size_t base, stride;      // cell a of the profile: base + a stride
+};
+
+__device__ __forceinline__ ProfileSeg profile_seg(const RoughJob& jb, int q, int seg) {
+    ProfileSeg ps;
+    ps.valid = q < jb.n_rows + jb.n_cols;
+    ps.row = q < jb.n_rows;
+    ps.r = ps.row ? q : q - jb.n_rows;
+    if (ps.row) {
+        ps.fixed = jb.n_rows > 0 ? (int)(((long long)(2 * ps.r + 1) * jb.ny) / (2 * jb.n_rows)) : 0;
+        ps.base = (size_t)ps.fixed * jb.nx;
+        ps.stride = 1;
+        ps.L = jb.nx;
     } else {
-        fixed = (int)(((long long)(2 * r + 1) * nx) / (2 * jb.n_cols));
-        base = (size_t)fixed;
-        stride = (size_t)nx;
+        ps.fixed = jb.n_cols > 0 ? (int)(((long long)(2 * ps.r + 1) * jb.nx) / (2 * jb.n_cols)) : 0;
+        ps.base = (size_t)ps.fixed;
+        ps.stride = (size_t)jb.nx;
+        ps.L = jb.ny;
     }
+    ps.lo = (int)(((long long)seg * ps.L) / kRzSegments);
+    ps.hi = (int)(((long long)(seg + 1) * ps.L) / kRzSegments);
+    return ps;
+}
+
+// Pass 1 of a profile segment: sum (double-float for FP32 maps, each value
+// exact), min and max (exact in the map's precision).
+template <typename T>
+__device__ void profile_seg1(const RoughJob* __restrict__ jobs, int item, int per_job, double* ppart, double* sh) {
+    const int j = item / (per_job * kRzSegments), rem = item - j * per_job * kRzSegments;
+    const int q = rem / kRzSegments, seg = rem - q * kRzSegments;
+    const RoughJob jb = jobs[j];
+    const ProfileSeg ps = profile_seg(jb, q, seg);
+    if (!ps.valid) return;
     const T* h = reinterpret_cast<const T*>(jb.h);
-    // the profile is read from the map once, into shared memory when it fits
-    // (47 KB: 12032 floats or 6016 doubles); the passes below read it there
-    constexpr int kCache = 48128 / (int)sizeof(T);
-    __shared__ T pv[kCache];
-    const bool cached = L <= kCache;
-    if (cached) {
-        for (int a = threadIdx.x; a < L; a += blockDim.x) pv[a] = h[base + (size_t)a * stride];
-        __syncthreads();
-    }
-    auto value = [&](int a) -> double { return cached ? (double)pv[a] : (double)h[base + (size_t)a * stride]; };
-    double mu, ra;
-    if (sizeof(T) == 4 && cached) {
-        // FP32 maps: mean and mean |z - mu| in double-float on the FP32 pipes
-        // (each deviation formed exactly: two-sum of z and -mu_hi, less mu_lo)
+    double sum, mn, mx;
+    if constexpr (sizeof(T) == 4) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int a = threadIdx.x; a < L; a += blockDim.x) acc = df_add(acc, make_float2((float)pv[a], 0.f));
-        mu = block_sum_df(acc, sh) / (double)L;
+        float fn = 3.0e38f, fx = -3.0e38f;
+        for (int a = ps.lo + threadIdx.x; a < ps.hi; a += blockDim.x) {
+            const float z = (float)h[ps.base + (size_t)a * ps.stride];
+            acc = df_add(acc, make_float2(z, 0.f));
+            fn = fminf(fn, z);
+            fx = fmaxf(fx, z);
+        }
+        sum = block_sum_df(acc, sh);
+        mn = (double)block_minmax_f<1>(fn, sh);
+        mx = (double)block_minmax_f<2>(fx, sh);
+    } else {
+        double acc = 0.0, dn = 1e300, dx = -1e300;
+        for (int a = ps.lo + threadIdx.x; a < ps.hi; a += blockDim.x) {
+            const double z = (double)h[ps.base + (size_t)a * ps.stride];
+            acc += z;
+            dn = fmin(dn, z);
+            dx = fmax(dx, z);
+        }
+        sum = block_reduce<0>(acc, sh);
+        mn = block_reduce<1>(dn, sh);
+        mx = block_reduce<2>(dx, sh);
+    }
+    if (threadIdx.x == 0) {
+        double* o = ppart + 4 * (size_t)item;
+        o[0] = sum;
+        o[1] = mn;
+        o[2] = mx;
+    }
+}
+
+// Mean of a profile from its segments' pass-1 sums (fixed order).
+__device__ __forceinline__ double profile_mean(const double* ppart, int prof, int L) {
+    double s = 0.0;
+    for (int seg = 0; seg < kRzSegments; ++seg) s += __ldcg(ppart + 4 * ((size_t)prof * kRzSegments + seg));
+    return s / (double)L;
+}
+
+// Pass 2 of a profile segment: sum of |z - profile mean| (FP32 maps:
+// double-float, each deviation formed exactly).
+template <typename T>
+__device__ void profile_seg2(const RoughJob* __restrict__ jobs, int item, int per_job, double* ppart, double* sh) {
+    const int j = item / (per_job * kRzSegments), rem = item - j * per_job * kRzSegments;
+    const int q = rem / kRzSegments, seg = rem - q * kRzSegments;
+    const RoughJob jb = jobs[j];
+    const ProfileSeg ps = profile_seg(jb, q, seg);
+    if (!ps.valid) return;
+    const T* h = reinterpret_cast<const T*>(jb.h);
+    const double mu = profile_mean(ppart, j * per_job + q, ps.L);
+    double dev;
+    if constexpr (sizeof(T) == 4) {
         const float mu_hi = (float)mu, mu_lo = (float)(mu - (double)mu_hi);
         float2 w = make_float2(0.f, 0.f);
-        for (int a = threadIdx.x; a < L; a += blockDim.x) {
+        for (int a = ps.lo + threadIdx.x; a < ps.hi; a += blockDim.x) {
             float d, e, dh, dl;
-            two_sum((float)pv[a], -mu_hi, &d, &e);
+            two_sum((float)h[ps.base + (size_t)a * ps.stride], -mu_hi, &d, &e);
             two_sum(d, e - mu_lo, &dh, &dl);  // z - mu as a normalised pair: its sign is dh's
             w = df_add(w, dh < 0.f ? make_float2(-dh, -dl) : make_float2(dh, dl));
         }
-        ra = block_sum_df(w, sh) / (double)L;
+        dev = block_sum_df(w, sh);
     } else {
-        double s = 0.0;
-        for (int a = threadIdx.x; a < L; a += blockDim.x) s += value(a);
-        mu = block_reduce<0>(s, sh) / (double)L;
         double w = 0.0;
-        for (int a = threadIdx.x; a < L; a += blockDim.x) w += fabs(value(a) - mu);
-        ra = block_reduce<0>(w, sh) / (double)L;
+        for (int a = ps.lo + threadIdx.x; a < ps.hi; a += blockDim.x)
+            w += fabs((double)h[ps.base + (size_t)a * ps.stride] - mu);
+        dev = block_reduce<0>(w, sh);
     }
-    double rz = 0.0;
-    for (int seg = 0; seg < 5; ++seg) {  // Rz: max - min over 5 segments [floor(qL/5), floor((q+1)L/5))
-        const int lo = (int)(((long long)seg * L) / 5), hi = (int)(((long long)(seg + 1) * L) / 5);
-        double mx, mn;
-        if constexpr (sizeof(T) == 4) {  // exact in the map's own precision
-            float fx = -3.0e38f, fn = 3.0e38f;
-            for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
-                const float z = cached ? (float)pv[a] : (float)h[base + (size_t)a * stride];
-                fx = fmaxf(fx, z);
-                fn = fminf(fn, z);
-            }
-            mx = (double)block_minmax_f<2>(fx, sh);
-            mn = (double)block_minmax_f<1>(fn, sh);
-        } else {
-            mx = -1e300;
-            mn = 1e300;
-            for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
-                const double z = value(a);
-                mx = fmax(mx, z);
-                mn = fmin(mn, z);
-            }
-            mx = block_reduce<2>(mx, sh);
-            mn = block_reduce<1>(mn, sh);
+    if (threadIdx.x == 0) ppart[4 * (size_t)item + 3] = dev;
+}
+
+// Profile results of job j (the block finalising the job; a thread per
+// profile, its segments combined in order).
+__device__ void finalize_profiles(const RoughJob& jb, int j, int per_job, const double* ppart) {
+    fsm_roughness_out* out = jb.out;
+    for (int q = threadIdx.x; q < jb.n_rows + jb.n_cols; q += blockDim.x) {
+        const ProfileSeg ps = profile_seg(jb, q, 0);
+        const int prof = j * per_job + q;
+        double dev = 0.0, rz = 0.0;
+        for (int seg = 0; seg < kRzSegments; ++seg) {
+            const double* o = ppart + 4 * ((size_t)prof * kRzSegments + seg);
+            dev += __ldcg(o + 3);
+            rz += __ldcg(o + 2) - __ldcg(o + 1);
         }
-        rz += mx - mn;
-    }
-    if (threadIdx.x == 0) {
-        const double rzv = L >= 5 ? rz / 5.0 : __longlong_as_double(0x7ff8000000000000ll);
-        fsm_roughness_out* out = jb.out;
-        if (row) {
-            out->row_index[r] = fixed;
-            out->Ra_row[r] = ra;
-            out->Rz_row[r] = rzv;
+        const double ra = dev / (double)ps.L;
+        const double rzv = ps.L >= kRzSegments ? rz / (double)kRzSegments : __longlong_as_double(0x7ff8000000000000ll);
+        if (ps.row) {
+            out->row_index[ps.r] = ps.fixed;
+            out->Ra_row[ps.r] = ra;
+            out->Rz_row[ps.r] = rzv;
         } else {
-            out->col_index[r] = fixed;
-            out->Ra_col[r] = ra;
-            out->Rz_col[r] = rzv;
+            out->col_index[ps.r] = ps.fixed;
+            out->Ra_col[ps.r] = ra;
+            out->Rz_col[ps.r] = rzv;
         }
     }
 }
 
+
+// End of a pass-2 item of job j: the block completing the job's last item
+// (chunks and profile segments) combines it.
+__device__ __forceinline__ void finish2(const RoughJob* __restrict__ jobs, int n_jobs,
+                                        const int* __restrict__ chunk_base, const double* part, const double* part2,
+                                        void* sync, int total_chunks, int per_job, int j, double* sh) {
+    const RoughSync rs = rough_sync(sync, n_jobs);
+    const int items = chunk_base[j + 1] - chunk_base[j] + per_job * kRzSegments;
+    if (last_chunk_block(rs.done2, j, items))
+        finalize_job(jobs, chunk_base, part, part2, j, __ldcg(rs.mean + j), per_job,
+                     part + 7 * (size_t)total_chunks, sh);
+}
+
+// Pass-2 items past the chunks are profile segments; true if b was one.
+template <typename T>
+__device__ __forceinline__ bool rough2_profile(const RoughJob* __restrict__ jobs, int n_jobs,
+                                               const int* __restrict__ chunk_base, const double* part,
+                                               const double* part2, void* sync, int total_chunks, int per_job, int b,
+                                               double* sh) {
+    if (b < total_chunks) return false;
+    const int it = b - total_chunks;
+    profile_seg2<T>(jobs, it, per_job, const_cast<double*>(part) + 7 * (size_t)total_chunks, sh);
+    finish2(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, it / (per_job * kRzSegments), sh);
+    return true;
+}
 
 // Pass 2: per chunk sums of |d|, d^2, d^3, d^4 about the job mean -> part2[b*4 + a]
 template <typename T>
 __device__ __forceinline__ void rough2_item(const RoughJob* __restrict__ jobs, int n_jobs,
                                             const int* __restrict__ chunk_base, const double* part, double* part2,
-                                            void* sync, int b, double* sh) {
+                                            void* sync, int total_chunks, int per_job, int b, double* sh) {
+    if (rough2_profile<T>(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, b, sh)) return;
     const int j = find_job(chunk_base, n_jobs, b);
     const RoughJob jb = jobs[j];
     const RoughSync rs = rough_sync(sync, n_jobs);
@@ -1653,9 +1761,8 @@ __device__ __forceinline__ void rough2_item(const RoughJob* __restrict__ jobs, i
         double* o = part2 + 4 * (size_t)b;
         o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
     }
-    // the block that finishes a job's last chunk combines the job
-    if (last_chunk_block(rs.done2, j, chunk_base[j + 1] - chunk_base[j]))
-        finalize_job(jobs, chunk_base, part, part2, j, mu, sh);
+    // the block that finishes a job's last item combines the job
+    finish2(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, j, sh);
 }
 
 // FP32 maps: the same two passes with 16-byte loads and no FP64 arithmetic
@@ -1671,8 +1778,8 @@ __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p 
 __device__ __forceinline__ void rough1_f32_item(const RoughJob* __restrict__ jobs, int n_jobs,
                                                 const int* __restrict__ chunk_base, double* part, int total_chunks,
                                                 int per_job, void* sync, int b, double* sh) {
-    if (b >= total_chunks) {  // items past the chunks are profiles
-        profile_block<float>(jobs, b - total_chunks, per_job, sh);
+    if (b >= total_chunks) {  // items past the chunks are profile segments
+        profile_seg1<float>(jobs, b - total_chunks, per_job, part + 7 * (size_t)total_chunks, sh);
         return;
     }
     const int j = find_job(chunk_base, n_jobs, b);
@@ -1736,7 +1843,8 @@ __device__ __forceinline__ void dev_terms(float z, float mu_hi, float mu_lo, flo
 
 __device__ __forceinline__ void rough2_f32_item(const RoughJob* __restrict__ jobs, int n_jobs,
                                                 const int* __restrict__ chunk_base, const double* part, double* part2,
-                                                void* sync, int b, double* sh) {
+                                                void* sync, int total_chunks, int per_job, int b, double* sh) {
+    if (rough2_profile<float>(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, b, sh)) return;
     const int j = find_job(chunk_base, n_jobs, b);
     const RoughJob jb = jobs[j];
     const RoughSync rs = rough_sync(sync, n_jobs);
@@ -1777,54 +1885,62 @@ __device__ __forceinline__ void rough2_f32_item(const RoughJob* __restrict__ job
         }
     }
     double vs[4];
-    for (int k = 0; k < 4; ++k) vs[k] = block_sum_df(v[k], sh);
+    block_sum_df4(v, sh, vs);
     if (threadIdx.x == 0) {
         double* o = part2 + 4 * (size_t)b;
         o[0] = vs[0]; o[1] = vs[1]; o[2] = vs[2]; o[3] = vs[3];
     }
-    // the block that finishes a job's last chunk combines the job
-    if (last_chunk_block(rs.done2, j, chunk_base[j + 1] - chunk_base[j]))
-        finalize_job(jobs, chunk_base, part, part2, j, mu, sh);
+    // the block that finishes a job's last item combines the job
+    finish2(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, j, sh);
 }
 
 // Persistent roughness passes: blocks walk the items (pass 1: profiles, then chunks)
 // in a grid stride; partial results are stored per chunk, so the combine
 // order does not depend on which block took which chunk.
 template <typename T>
-__global__ void __launch_bounds__(256) rough1_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(256, kRoughBlocksPerSm) rough1_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
                                                      const int* __restrict__ chunk_base, double* part,
                                                      int total_chunks, int per_job, void* sync, int n_items) {
     __shared__ double sh[32];
-    const int n_prof = n_items - total_chunks;  // profiles first: they are the longest items
+    const int n_prof = n_items - total_chunks;  // profile segments first
     for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
         const int item = b < n_prof ? total_chunks + b : b - n_prof;
         rough1_item<T>(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, item, sh);
     }
 }
-__global__ void __launch_bounds__(256) rough1_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(256, kRoughBlocksPerSm) rough1_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
                                                          const int* __restrict__ chunk_base, double* part,
                                                          int total_chunks, int per_job, void* sync, int n_items) {
     __shared__ double sh[32];
-    const int n_prof = n_items - total_chunks;  // profiles first: they are the longest items
+    const int n_prof = n_items - total_chunks;  // profile segments first
     for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
         const int item = b < n_prof ? total_chunks + b : b - n_prof;
         rough1_f32_item(jobs, n_jobs, chunk_base, part, total_chunks, per_job, sync, item, sh);
     }
 }
+// Pass 2 walks the profile segments first, then the chunks.
 template <typename T>
-__global__ void __launch_bounds__(256) rough2_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(256, kRoughBlocksPerSm) rough2_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
                                                      const int* __restrict__ chunk_base, const double* part,
-                                                     double* part2, void* sync, int total_chunks) {
+                                                     double* part2, void* sync, int total_chunks, int per_job,
+                                                     int n_items) {
     __shared__ double sh[32];
-    for (int b = blockIdx.x; b < total_chunks; b += gridDim.x)
-        rough2_item<T>(jobs, n_jobs, chunk_base, part, part2, sync, b, sh);
+    const int n_prof = n_items - total_chunks;
+    for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
+        const int item = b < n_prof ? total_chunks + b : b - n_prof;
+        rough2_item<T>(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, item, sh);
+    }
 }
-__global__ void __launch_bounds__(256) rough2_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(256, kRoughBlocksPerSm) rough2_f32_kernel(const RoughJob* __restrict__ jobs, int n_jobs,
                                                          const int* __restrict__ chunk_base, const double* part,
-                                                         double* part2, void* sync, int total_chunks) {
-    __shared__ double sh[32];
-    for (int b = blockIdx.x; b < total_chunks; b += gridDim.x)
-        rough2_f32_item(jobs, n_jobs, chunk_base, part, part2, sync, b, sh);
+                                                         double* part2, void* sync, int total_chunks, int per_job,
+                                                         int n_items) {
+    __shared__ double sh[128];
+    const int n_prof = n_items - total_chunks;
+    for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
+        const int item = b < n_prof ? total_chunks + b : b - n_prof;
+        rough2_f32_item(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, item, sh);
+    }
 }
 
 // ===========================================================================
@@ -2031,9 +2147,13 @@ cudaError_t launch_roughness_one(int precision, const RoughJob& jb, char* d_ws, 
     return launch_roughness_jobs(precision, d_job, 1, d_base, chunks, jb.n_rows + jb.n_cols, d_part, d_sync, st);
 }
 
+size_t rough_part_doubles(int total_chunks, int n_jobs, int max_profiles) {
+    return 7 * (size_t)total_chunks + 4 * (size_t)kRzSegments * (size_t)n_jobs * (size_t)max_profiles;
+}
+
 size_t roughness_one_ws_bytes(size_t n) {
     const size_t chunks = (n + kChunk - 1) / kChunk;
-    return 512 + 7 * sizeof(double) * chunks;
+    return 512 + sizeof(double) * rough_part_doubles((int)chunks, 1, 2 * FSM_MAX_PROFILES);
 }
 
 size_t rough_sync_bytes(int n_jobs) { return ((8 * (size_t)n_jobs + 7) & ~(size_t)7) + 8 * (size_t)n_jobs; }
@@ -2045,21 +2165,25 @@ cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_j
     double* part2 = d_part + 3 * (size_t)total_chunks;
     cudaError_t e = cudaMemsetAsync(d_sync, 0, rough_sync_bytes(n_jobs), st);
     if (e != cudaSuccess) return e;
-    // pass 1 (+ the profiles as extra blocks; each job's last block stores
-    // the mean), pass 2 (+ the final combine in each job's last block)
-    const int items1 = total_chunks + n_jobs * max_profiles;
+    // pass 1 (profile segments, then the chunks; each job's last chunk block
+    // stores the mean), pass 2 (the same items; each job's last block
+    // combines it); both persistent, kRoughBlocksPerSm blocks per SM
+    const int per_job = max(max_profiles, 1);
+    const int items = total_chunks + n_jobs * per_job * kRzSegments;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int g1 = std::min(items1, 4 * sms), g2 = std::min(total_chunks, 8 * sms);
+    const int g = std::min(items, kRoughBlocksPerSm * sms);
     if (precision == 0) {
-        rough1_kernel<double><<<g1, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, total_chunks, max_profiles,
-                                                 d_sync, items1);
-        rough2_kernel<double><<<g2, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2, d_sync, total_chunks);
+        rough1_kernel<double><<<g, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, total_chunks, per_job, d_sync,
+                                                items);
+        rough2_kernel<double><<<g, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2, d_sync, total_chunks,
+                                                per_job, items);
     } else {
-        rough1_f32_kernel<<<g1, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, total_chunks, max_profiles,
-                                             d_sync, items1);
-        rough2_f32_kernel<<<g2, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2, d_sync, total_chunks);
+        rough1_f32_kernel<<<g, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, total_chunks, per_job, d_sync,
+                                            items);
+        rough2_f32_kernel<<<g, 256, 0, st>>>(d_jobs, n_jobs, d_chunk_base, d_part, part2, d_sync, total_chunks,
+                                            per_job, items);
     }
     return cudaGetLastError();
 }
@@ -2075,7 +2199,8 @@ namespace fsm {
 
 constexpr size_t kNoAllocMaxCells = (size_t)1 << 29;
 constexpr size_t kNoAllocChunks = (kNoAllocMaxCells + kChunk - 1) / kChunk;
-constexpr size_t kNoAllocBytes = 512 + 7 * sizeof(double) * kNoAllocChunks;  // about 0.9 MiB
+constexpr size_t kNoAllocBytes =
+    512 + sizeof(double) * (7 * kNoAllocChunks + 4 * 5 * 2 * FSM_MAX_PROFILES);  // about 0.9 MiB
 
 // One per device that loads the library, kept until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
