@@ -344,6 +344,22 @@ fsm_status fsm_roughness_noalloc(fsm_ctx* ctx, const void* d_heights, int32_t pr
                                  int32_t ny, int32_t n_rows, int32_t n_cols,
                                  fsm_roughness_out* d_out, void* stream);
 
+/* Moment partials of a device height map, or of one row band of a map that
+ * several devices computed band by band (each band is the map's rows
+ * [k0, k1): the same process with y0 + k0 pitch and k1 - k0 rows). With
+ * d = z - about, writes 8 doubles to DEVICE d_out: [0] cells, [1] sum d,
+ * [2] min z, [3] max z, [4] sum |d|, [5] sum d^2, [6] sum d^3, [7] sum d^4,
+ * each summed in a fixed order (FP64 maps in FP64; FP32 maps: d as an exact
+ * float pair, terms summed in double-float). Combining bands: add [0], [1]
+ * (about a common value) and take min/max of [2], [3] over the bands; the
+ * map's mean is about + sum d / n; a second call per band with about = that
+ * mean gives the bands' shares of the central sums of Section 4.1.2's Sa,
+ * Sq, Ssk, Sku (added over the bands). Stream-ordered scratch of 64 bytes
+ * per 32768 cells. Asynchronous on `stream`. (An extension: the paper's
+ * method runs on one CPU.) */
+fsm_status fsm_moment_partials(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx, int32_t ny,
+                               double about, double* d_out, void* stream);
+
 /* ISO 16610-61 areal Gaussian filtering of a device height map (an
  * extension for comparing predictions with measured surfaces: the paper's
  * profilometer applies an S-filter of 10 um and an L-filter of 0.8 mm,

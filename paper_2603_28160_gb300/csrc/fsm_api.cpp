@@ -552,6 +552,26 @@ fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision,
     return fsm::roughness_one(ctx, d_heights, precision, nx, ny, n_rows, n_cols, d_out, (cudaStream_t)stream);
 }
 
+fsm_status fsm_moment_partials(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx, int32_t ny,
+                               double about, double* d_out, void* stream) {
+    if (!ctx || !d_heights || !d_out) return fail(FSM_E_INVALID, "ctx/d_heights/d_out is NULL");
+    if (precision != FSM_FP64 && precision != FSM_FP32) return fail(FSM_E_INVALID, "unknown precision");
+    if (nx < 1 || ny < 1) return fail(FSM_E_INVALID, "nx, ny must be >= 1");
+    if (!isfinite(about)) return fail(FSM_E_INVALID, "about must be finite");
+    DeviceGuard dev_guard(ctx->device);
+    if (dev_guard.err != cudaSuccess) return cuda_fail(dev_guard.err, "cudaSetDevice");
+    const size_t n = (size_t)nx * (size_t)ny;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* ws = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&ws, moment_ws_bytes(n), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (moments)");
+    e = launch_moments(precision, d_heights, n, about, ws, d_out, st);
+    cudaError_t e2 = cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "moment kernels");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return FSM_OK;
+}
+
 }  // extern "C"
 
 extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc, void* d_heights,

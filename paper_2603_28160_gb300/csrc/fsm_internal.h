@@ -71,6 +71,11 @@ size_t rough_part_doubles(int total_chunks, int n_jobs, int max_profiles);
 cudaError_t launch_roughness_jobs(int precision, const RoughJob* d_jobs, int n_jobs, const int* d_chunk_base,
                                   int total_chunks, int max_profiles, double* d_part, void* d_sync,
                                   cudaStream_t st);
+// Moment partials of n cells about `about` (see fsm_moment_partials):
+// d_ws of moment_ws_bytes(n) bytes, 8 doubles to d_out; two launches.
+size_t moment_ws_bytes(size_t n);
+cudaError_t launch_moments(int precision, const void* d_h, size_t n, double about, double* d_ws, double* d_out,
+                           cudaStream_t st);
 // One map; d_ws of roughness_one_ws_bytes(n) bytes (256-aligned).
 size_t roughness_one_ws_bytes(size_t n);
 cudaError_t launch_roughness_one(int precision, const RoughJob& jb, char* d_ws, cudaStream_t st);

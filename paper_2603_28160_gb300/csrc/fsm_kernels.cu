@@ -1944,6 +1944,102 @@ __global__ void __launch_bounds__(256, kRoughBlocksPerSm) rough2_f32_kernel(cons
 }
 
 // ===========================================================================
+// Moment partials of a map or of one band of a map (a map split into row
+// bands over several devices combines its roughness from these): chunk b of
+// the map gives [n, sum d, min z, max z, sum |d|, sum d^2, sum d^3, sum d^4]
+// with d = z - about; a single block then adds the chunks in chunk order.
+// FP64 maps: FP64; FP32 maps: each d formed as a float pair, the terms in
+// double-float on the FP32 pipes.
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) moment_chunks_kernel(const T* __restrict__ h, size_t n, double about,
+                                                            double* __restrict__ part) {
+    __shared__ double sh[32];
+    const size_t lo = (size_t)blockIdx.x * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+    double r[8];
+    if constexpr (sizeof(T) == 4) {
+        const float a_hi = (float)about, a_lo = (float)(about - (double)a_hi);
+        float2 acc[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float mn = 3.0e38f, mx = -3.0e38f;
+        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const float z = (float)h[i];
+            float d, e, dh, dl;
+            two_sum(z, -a_hi, &d, &e);
+            two_sum(d, e - a_lo, &dh, &dl);  // z - about as a normalised pair
+            const float d2 = dh * dh, d3 = d2 * dh;
+            acc[0] = df_add(acc[0], make_float2(dh, dl));
+            acc[1] = df_add(acc[1], dh < 0.f ? make_float2(-dh, -dl) : make_float2(dh, dl));
+            acc[2] = df_add(acc[2], make_float2(d2, fmaf(dh, dh, -d2) + 2.f * dh * dl));
+            acc[3] = df_add(acc[3], make_float2(d3, 0.f));
+            acc[4] = df_add(acc[4], make_float2(d2 * d2, 0.f));
+            mn = fminf(mn, z);
+            mx = fmaxf(mx, z);
+        }
+        r[1] = block_sum_df(acc[0], sh);
+        r[4] = block_sum_df(acc[1], sh);
+        r[5] = block_sum_df(acc[2], sh);
+        r[6] = block_sum_df(acc[3], sh);
+        r[7] = block_sum_df(acc[4], sh);
+        r[2] = (double)block_minmax_f<1>(mn, sh);
+        r[3] = (double)block_minmax_f<2>(mx, sh);
+    } else {
+        double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, mn = 1e300, mx = -1e300;
+        for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const double z = (double)h[i];
+            const double d = z - about, d2 = d * d;
+            a[0] += d;
+            a[1] += fabs(d);
+            a[2] += d2;
+            a[3] += d2 * d;
+            a[4] += d2 * d2;
+            mn = fmin(mn, z);
+            mx = fmax(mx, z);
+        }
+        r[1] = block_reduce<0>(a[0], sh);
+        r[4] = block_reduce<0>(a[1], sh);
+        r[5] = block_reduce<0>(a[2], sh);
+        r[6] = block_reduce<0>(a[3], sh);
+        r[7] = block_reduce<0>(a[4], sh);
+        r[2] = block_reduce<1>(mn, sh);
+        r[3] = block_reduce<2>(mx, sh);
+    }
+    if (threadIdx.x == 0) {
+        r[0] = (double)(hi - lo);
+        for (int k = 0; k < 8; ++k) part[8 * (size_t)blockIdx.x + k] = r[k];
+    }
+}
+
+__global__ void __launch_bounds__(256) moment_combine_kernel(const double* __restrict__ part, int chunks,
+                                                             double* __restrict__ out) {
+    __shared__ double sh[32];
+    double v[8] = {0.0, 0.0, 1e300, -1e300, 0.0, 0.0, 0.0, 0.0};
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        const double* p = part + 8 * (size_t)c;
+        v[0] += p[0]; v[1] += p[1]; v[4] += p[4]; v[5] += p[5]; v[6] += p[6]; v[7] += p[7];
+        v[2] = fmin(v[2], p[2]);
+        v[3] = fmax(v[3], p[3]);
+    }
+    double r[8];
+    for (int k = 0; k < 8; ++k) r[k] = k == 2 ? block_reduce<1>(v[k], sh) : k == 3 ? block_reduce<2>(v[k], sh)
+                                                                                   : block_reduce<0>(v[k], sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) out[k] = r[k];
+}
+
+size_t moment_ws_bytes(size_t n) { return 8 * sizeof(double) * ((n + kChunk - 1) / kChunk); }
+
+cudaError_t launch_moments(int precision, const void* d_h, size_t n, double about, double* d_ws, double* d_out,
+                           cudaStream_t st) {
+    const int chunks = (int)((n + kChunk - 1) / kChunk);
+    if (precision == 0)
+        moment_chunks_kernel<double><<<chunks, 256, 0, st>>>((const double*)d_h, n, about, d_ws);
+    else
+        moment_chunks_kernel<float><<<chunks, 256, 0, st>>>((const float*)d_h, n, about, d_ws);
+    moment_combine_kernel<<<1, 256, 0, st>>>(d_ws, chunks, d_out);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
 // Launchers (called by the C ABI layer)
 // ===========================================================================
 // ---------------------------------------------------------------------------

@@ -116,6 +116,7 @@ SIGNATURES = {
     "fsm_predict_trajectory": [_P, _P, _P, _P, C.c_int64, _P],
     "fsm_trajectory_records": [_P, _P, C.POINTER(C.c_int64)],
     "fsm_filter": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P, _P],
+    "fsm_moment_partials": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _P, _P],
 }
 
 _lib = None
@@ -326,6 +327,17 @@ class Context:
         ny, nx = heights.shape
         self._call("fsm_roughness", self.ptr, heights.data_ptr(), int(precision), nx, ny, int(n_rows),
                    int(n_cols), out_buf.data_ptr(), _stream_ptr(stream))
+
+    def moment_partials(self, heights, about: float, stream=None) -> np.ndarray:
+        """fsm_moment_partials of a CUDA height map: [n, sum d, min z, max z,
+        sum |d|, sum d^2, sum d^3, sum d^4], d = z - about (host copy)."""
+        import torch
+        ny, nx = heights.shape
+        prec = FSM_FP64 if heights.dtype == torch.float64 else FSM_FP32
+        out = torch.zeros(8, dtype=torch.float64, device=heights.device)
+        self._call("fsm_moment_partials", self.ptr, heights.data_ptr(), prec, nx, ny, float(about), out.data_ptr(),
+                   _stream_ptr(stream))
+        return out.cpu().numpy()
 
     def roughness(self, heights, n_rows=10, n_cols=10, stream=None) -> dict:
         import torch
