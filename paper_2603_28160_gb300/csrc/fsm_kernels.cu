@@ -1398,6 +1398,40 @@ __device__ __forceinline__ void block_sum_df4(const float2 (&v)[4], double* sh, 
     }
 }
 
+// FP64 maps' moments on the FP32 pipes (GB300 runs FP64 at 1/64 of the
+// FP32 rate): a double as an unevaluated float pair hi + lo, from its bits
+// (hi: the top 24 significant bits, truncated; lo: the other 29, rounded to
+// a float), |z - (hi + lo)| <= 2^-47 |z|, no FP64 instruction; magnitudes
+// outside [2^-60, 2^100] (zero included) take FP64 conversions.
+// The rare magnitudes by FP64 conversions, in a call of its own so the
+// compiler cannot turn the branch into predicated FP64 instructions that
+// every cell would issue.
+__device__ __noinline__ float2 split_double_slow(double z) {
+    const float hi = (float)z;
+    return make_float2(hi, (float)(z - (double)hi));
+}
+
+__device__ __forceinline__ float2 split_double(double z) {
+    const unsigned hw = (unsigned)__double2hiint(z), lw = (unsigned)__double2loint(z);
+    const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
+    if (e < -60 || e > 100) return split_double_slow(z);
+    const unsigned sign = hw & 0x80000000u;
+    // fraction bits 51..29 (hw's 20, lw's top 3) and 28..0 (lw's rest)
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    const unsigned rem = lw & 0x1FFFFFFFu;  // worth rem * 2^(e - 52)
+    float lo = 0.f;
+    if (rem) lo = __uint_as_float((__float_as_uint(__uint2float_rn(rem)) + ((unsigned)(e - 52) << 23)) | sign);
+    return make_float2(hi, lo);
+}
+
+// x * y of double-float pairs (the leading product's rounding error by fma).
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+    const float p = x.x * y.x;
+    const float pe = fmaf(x.x, y.x, -p) + fmaf(x.x, y.y, x.y * y.x);
+    const float hi = p + pe;
+    return make_float2(hi, pe - (hi - p));
+}
+
 __device__ __forceinline__ int find_job(const int* base, int n, int b) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1486,29 +1520,38 @@ __device__ __forceinline__ void rough1_item(const RoughJob* __restrict__ jobs, i
     size_t lo, hi;
     chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
     const T* h = reinterpret_cast<const T*>(jb.h);
-    // min and max on the order-preserving keys (exact, on the integer ALU),
-    // leaving the sum as the one FP64 operation per cell
-    double s = 0.0;
-    unsigned long long kmn = ~0ull, kmx = 0ull;
+    // min and max on the order-preserving keys (exact, on the integer ALU);
+    // the sum of z - ref (ref: the map's first cell), each difference one
+    // FP64 subtraction split into a float pair, summed in double-float on the
+    // FP32 pipes (the split's 2^-47 is then relative to the difference, not
+    // to z: maps far from zero keep their texture's precision)
+    const double ref = (double)h[0];
+    float2 s = make_float2(0.f, 0.f);
+    // keys as (high, low) 32-bit words, compared lexicographically
+    unsigned mn_h = ~0u, mn_l = ~0u, mx_h = 0u, mx_l = 0u;
 #pragma unroll 4
     for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double z = (double)h[i];
-        s += z;
-        const unsigned long long k = enc64((unsigned long long)__double_as_longlong(z));
-        kmn = k < kmn ? k : kmn;
-        kmx = k > kmx ? k : kmx;
+        s = df_add(s, split_double(z - ref));
+        const unsigned zh = (unsigned)__double2hiint(z), zl = (unsigned)__double2loint(z);
+        const bool neg = (zh >> 31) != 0u;
+        const unsigned kh = neg ? ~zh : (zh | 0x80000000u), kl = neg ? ~zl : zl;
+        if (kh < mn_h || (kh == mn_h && kl < mn_l)) { mn_h = kh; mn_l = kl; }
+        if (kh > mx_h || (kh == mx_h && kl > mx_l)) { mx_h = kh; mx_l = kl; }
     }
-    s = block_reduce<0>(s, sh);
+    const unsigned long long kmn = ((unsigned long long)mn_h << 32) | mn_l;
+    const unsigned long long kmx = ((unsigned long long)mx_h << 32) | mx_l;
+    const double sum = block_sum_df(s, sh);
     double mn = kmn == ~0ull ? 1e300 : __longlong_as_double((long long)dec64(kmn));
     double mx = kmx == 0ull ? -1e300 : __longlong_as_double((long long)dec64(kmx));
     mn = block_reduce<1>(mn, sh);
     mx = block_reduce<2>(mx, sh);
     if (threadIdx.x == 0) {
-        part[3 * (size_t)b] = s;
+        part[3 * (size_t)b] = sum;
         part[3 * (size_t)b + 1] = mn;
         part[3 * (size_t)b + 2] = mx;
     }
-    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, 0.0, sh);
+    job_mean_if_last(jobs, chunk_base, part, n_jobs, j, sync, ref, sh);
 }
 
 // Mean of job j from its chunk sums, in chunk order (identical in every block).
@@ -1743,23 +1786,23 @@ __device__ __forceinline__ void rough2_item(const RoughJob* __restrict__ jobs, i
     size_t lo, hi;
     chunk_range<T>(jb, b - chunk_base[j], &lo, &hi);
     const T* h = reinterpret_cast<const T*>(jb.h);
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-#pragma unroll 4
+    // |d|, d^2, d^3, d^4 of d = z - mu (one FP64 subtraction, split into a
+    // float pair) in double-float on the FP32 pipes
+    float2 v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 2
     for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double d = (double)h[i] - mu;
-        const double d2 = d * d;
-        v0 += fabs(d);
-        v1 += d2;
-        v2 += d2 * d;
-        v3 += d2 * d2;
+        const float2 d = split_double((double)h[i] - mu);
+        const float2 d2 = df_mul(d, d);
+        v[0] = df_add(v[0], d.x < 0.f ? make_float2(-d.x, -d.y) : d);
+        v[1] = df_add(v[1], d2);
+        v[2] = df_add(v[2], df_mul(d2, d));
+        v[3] = df_add(v[3], df_mul(d2, d2));
     }
-    v0 = block_reduce<0>(v0, sh);
-    v1 = block_reduce<0>(v1, sh);
-    v2 = block_reduce<0>(v2, sh);
-    v3 = block_reduce<0>(v3, sh);
+    double vs[4];
+    block_sum_df4(v, sh, vs);
     if (threadIdx.x == 0) {
         double* o = part2 + 4 * (size_t)b;
-        o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
+        o[0] = vs[0]; o[1] = vs[1]; o[2] = vs[2]; o[3] = vs[3];
     }
     // the block that finishes a job's last item combines the job
     finish2(jobs, n_jobs, chunk_base, part, part2, sync, total_chunks, per_job, j, sh);
@@ -1771,8 +1814,8 @@ __device__ __forceinline__ void rough2_item(const RoughJob* __restrict__ jobs, i
 // 1e-4 target), the leaves and the block sums kept as double-float pairs.
 // Pass 1 sums z - ref about the map's first cell, so its leaves carry
 // deviations only; min and max are exact in FP32. The mean is used as a
-// float pair so the deviations keep full FP32 precision. FP64 maps keep FP64
-// throughout.
+// float pair so the deviations keep full FP32 precision. (FP64 maps take
+// their cells as float pairs and double-float terms throughout.)
 __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 __device__ __forceinline__ void rough1_f32_item(const RoughJob* __restrict__ jobs, int n_jobs,
@@ -1924,7 +1967,7 @@ __global__ void __launch_bounds__(256, kRoughBlocksPerSm) rough2_kernel(const Ro
                                                      const int* __restrict__ chunk_base, const double* part,
                                                      double* part2, void* sync, int total_chunks, int per_job,
                                                      int n_items) {
-    __shared__ double sh[32];
+    __shared__ double sh[128];
     const int n_prof = n_items - total_chunks;
     for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
         const int item = b < n_prof ? total_chunks + b : b - n_prof;

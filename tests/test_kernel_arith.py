@@ -116,3 +116,40 @@ def test_planner_sinusoids_equal_the_pose():
         pose = np.cos(th) * u + np.sin(th) * v + w
         sinus = w + amp * np.cos(dth * (m - mph))
         assert np.abs(pose - sinus).max() <= 1e-9 * max(amp, 1.0)
+
+
+def split_double(z):
+    """Model of the kernels' split of a double into a float pair from its
+    bits: hi keeps the top 24 significant bits (truncated), lo the other 29
+    rounded to a float; magnitudes outside [2^-60, 2^100] (and zero) use the
+    rounded conversions."""
+    z = np.asarray(z, dtype=np.float64)
+    b = z.view(np.uint64)
+    e = ((b >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64) - 1023
+    sign = (b >> np.uint64(63)).astype(np.uint32) << np.uint32(31)
+    m = b & np.uint64(0xFFFFFFFFFFFFF)
+    hi_bits = sign | ((np.clip(e, -126, 127) + 127).astype(np.uint32) << np.uint32(23)) | \
+        (m >> np.uint64(29)).astype(np.uint32)
+    hi = hi_bits.view(np.float32)
+    rem = (m & np.uint64(0x1FFFFFFF)).astype(np.float64)
+    lo = (rem * np.ldexp(1.0, e - 52)).astype(np.float32) * np.where(sign != 0, -1, 1).astype(np.float32)
+    fb = (e < -60) | (e > 100)
+    hi_f = z.astype(np.float32)
+    lo_f = (z - hi_f.astype(np.float64)).astype(np.float32)
+    return np.where(fb, hi_f, hi), np.where(fb, lo_f, lo)
+
+
+def test_split_double_is_a_faithful_float_pair():
+    """FP64 maps' moments run in double-float arithmetic on cells split into
+    float pairs: hi + lo must be within 2^-47 |z| of z, with lo small
+    against hi (so the pair is normalised), for heights of every scale a
+    float can hold."""
+    rng = np.random.default_rng(47)
+    z = np.concatenate([rng.normal(0.0, 1.0, 10**5) * 10.0 ** rng.uniform(-18, 30, 10**5),
+                        [0.0, -0.0, 1.0, -1.0, 2.0 ** -60, 2.0 ** 100, 1e-300, -1e35, 0.1, -0.2]])
+    hi, lo = split_double(z)
+    back = hi.astype(np.float64) + lo.astype(np.float64)
+    err = np.abs(back - z)
+    assert np.all(err <= 2.0 ** -47 * np.abs(z) + 1e-300 * (np.abs(z) < 1e-290)), err.max()
+    nz = (z != 0) & np.isfinite(hi)
+    assert np.all(np.abs(lo[nz]) <= 2.0 ** -22 * np.abs(hi[nz]))
