@@ -83,6 +83,7 @@ struct Surface {
     float fs_hi, fs_lo;             // fs as an unevaluated float pair (fs_hi + fs_lo)
     float fs_f, inv_fs_f, dth_f, inv_dth_f, inv_pitch_f;
     float fsc_hi, fsc_lo, fsc_f;    // feed per step in cells (fs / pitch), as a float pair and rounded
+    float pitch_f;                  // pitch (FP32 enumeration and error bounds)
     float guard_extra;              // FP32 rounding of the bin scaling, in cells
 };
 

@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         sf->dth_f = (float)dth;
         sf->inv_dth_f = (float)(1.0 / dth);
         sf->inv_pitch_f = (float)(1.0 / sf->pitch);
+        sf->pitch_f = (float)sf->pitch;
         const double fsc = fs / sf->pitch;
         sf->fsc_hi = (float)fsc;
         sf->fsc_lo = (float)(fsc - (double)sf->fsc_hi);
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         const int j = g * 32 + lane;
         float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
         if (j < E) {
-            const PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), (float)sf->pitch);
+            const PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), sf->pitch_f);
             zmin = geo.wz - geo.amp_z;
             ArcF za;
             ArcI ia[kMaxArcs];
@@ -496,7 +497,7 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         t4[2] = tp[2];
         const float4 t3 = tp[3];
         PointGeom geo;
-        const float pitch = (float)sf.pitch;  // the x, y rows are in cells
+        const float pitch = sf.pitch_f;  // the x, y rows are in cells
         geo.wx = t4[0].z * pitch;
         geo.wy = t4[1].z * pitch;
         geo.wz = t4[2].x;
@@ -526,7 +527,7 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         const float u24 = 5.9604644775390625e-8f;
         const float amp_xy = fmaxf(geo.amp_x, geo.amp_y);
         const float pt_err = 6.f * amp_xy + 3.f * (fabsf(geo.wx) + fabsf(geo.wy) + fabsf(geo.wz)) +
-                             3.f * (float)max(sf.tile_x, sf.tile_y) * (float)sf.pitch;
+                             3.f * (float)max(sf.tile_x, sf.tile_y) * pitch;
         pt.x = sf.zrel_f + geo.wz;                                                          // zb
         pt.y = 1.5f * u24 * (5.f * geo.amp_z + 4.f * (fabsf(sf.zrel_f) + fabsf(geo.wz)));  // eps_z
         for (int a = 0; a < n; ++a) {
