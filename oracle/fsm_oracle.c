@@ -120,6 +120,8 @@ static int valid(const orc_tool* t, const orc_process* p) {
     if (p->surface != ORC_FLOOR && p->surface != ORC_WALL) return 0;
     if (p->surface == ORC_WALL && p->n_passes != 1) return 0;
     if (p->pass_mode != ORC_ONE_WAY && p->pass_mode != ORC_ZIGZAG) return 0;
+    if (!isfinite(p->feed_dir_deg)) return 0;
+    if (p->surface == ORC_WALL && p->feed_dir_deg != 0.0) return 0;
     return 1;
 }
 
@@ -321,7 +323,15 @@ static mat4 step_matrix(const orc_tool* t, const orc_process* p, const mat4* A,
     double yc = p->pass_y0 + (double)pass * p->ae;
     mat4 tsw = m_translate(xc, yc, z_ref);
     mat4 tts = m_tool_to_spindle(theta);
-    return m_mul(m_mul(tsw, *A), tts);
+    mat4 T = m_mul(m_mul(tsw, *A), tts);
+    if (p->feed_dir_deg != 0.0) {
+        /* feed direction: the chain above, turned about the vertical through
+         * the start of pass 0 */
+        mat4 F = m_mul(m_mul(m_translate(p->pass_x0, p->pass_y0, 0.0), m_rot_z(p->feed_dir_deg * DEG)),
+                       m_translate(-p->pass_x0, -p->pass_y0, 0.0));
+        T = m_mul(F, T);
+    }
+    return T;
 }
 
 int orc_pose(const orc_tool* t, const orc_process* p, int64_t s, int K, int j,

@@ -97,6 +97,13 @@ typedef struct {
      * passes run back along -X over the same stretch (step n of an odd pass
      * is where step steps_per_pass-1-n of an even pass is) */
     int32_t pass_mode;
+    /* (extension; the paper feeds along one axis) direction of the feed in
+     * the XY plane, degrees counter-clockwise from +X: the whole tool path
+     * and tool of the feed_dir_deg = 0 process, orientation included, turned
+     * by this angle about the vertical through (pass_x0, pass_y0). Passes
+     * then run along (cos, sin) and step over along (-sin, cos). Floors
+     * only (0 for a wall). */
+    double feed_dir_deg;
 } orc_process;
 
 enum { ORC_ONE_WAY = 0, ORC_ZIGZAG = 1 };

@@ -40,6 +40,7 @@ class OrcProcess(C.Structure):
         ("x0", C.c_double), ("y0", C.c_double), ("pitch", C.c_double),
         ("nx", C.c_int32), ("ny", C.c_int32), ("z_ref_override", C.c_double),
         ("surface", C.c_int32), ("wall_y", C.c_double), ("pass_mode", C.c_int32),
+        ("feed_dir_deg", C.c_double),
     ]
 
 
@@ -121,6 +122,7 @@ def make_process(proc, z_ref=None) -> OrcProcess:
     p.surface = {"floor": 0, "wall": 1}[proc.surface]
     p.wall_y = proc.wall_y
     p.pass_mode = {"one_way": 0, "zigzag": 1}[proc.pass_mode]
+    p.feed_dir_deg = proc.feed_dir_deg
     return p
 
 

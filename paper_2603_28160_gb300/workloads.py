@@ -91,6 +91,7 @@ class ProcessSpec:
     surface: str = "floor"        # "floor" (grid x, y; height z) or "wall" (+Y side wall:
     wall_y: float = 0.0           # grid x, z; height -y; un-machined at y = wall_y)
     pass_mode: str = "one_way"    # "one_way" or "zigzag" (odd passes run back along -X)
+    feed_dir_deg: float = 0.0     # feed direction: the path and tool turned about (pass_x0, pass_y0)
 
     def replace(self, **kw) -> "ProcessSpec":
         return dataclasses.replace(self, **kw)
