@@ -131,10 +131,19 @@ typedef struct {
  *   pass_mode FSM_PASS_ONE_WAY: every pass runs along +X from pass_x0;
  *   FSM_PASS_ZIGZAG: odd passes run back along -X over the same stretch
  *   (their step n is where step steps_per_pass-1-n of an even pass is).
+ *   feed_dir_deg (an extension; the paper feeds along one axis): the feed
+ *   direction in the XY plane, degrees counter-clockwise from +X. The tool
+ *   path and the tool of the feed_dir_deg = 0 process (lead, tilt and
+ *   spindle phase included) are turned by this angle about the vertical
+ *   through (pass_x0, pass_y0): passes run along (cos, sin) and step over
+ *   along (-sin, cos); the grid stays axis-aligned. A multiple of 360 is the
+ *   +X feed itself. Floors only. Surfaces fed off the X axis take the item
+ *   form of the sweep (FSM_FORM_PHASE is rejected for them).
  * Validation: fz, ap, pitch > 0; 360/rot_step_deg integral; rot_sense = +-1;
  * n_passes >= 1 (== 1 for a wall); steps_per_pass >= 1;
- * n_passes*steps_per_pass < 2^31; 1 <= nx, ny <= 65535*256; finite values.
- * rpm only labels time. */
+ * n_passes*steps_per_pass < 2^31; 1 <= nx, ny <= 65535*256; finite values;
+ * feed_dir_deg a multiple of 360 for a wall. rpm only labels time.
+ * feed_dir_deg was added after `reserved`; zero it for the +X feed. */
 typedef struct {
     double fz;
     double rpm;
@@ -160,6 +169,7 @@ typedef struct {
     double wall_y;
     int32_t pass_mode;
     int32_t reserved;
+    double feed_dir_deg;
 } fsm_process_desc;
 
 /* Optional launch overrides, counters and timing for the prediction calls.

@@ -78,7 +78,8 @@ static fsm_status check_tool(const fsm_tool_desc* t) {
 static fsm_status check_process(const fsm_process_desc* p) {
     if (!p) return fail(FSM_E_INVALID, "process descriptor is NULL");
     const double vals[] = {p->fz, p->rpm, p->rot_step_deg, p->phase0_deg, p->ap, p->lead_deg, p->tilt_deg,
-                           p->ae, p->pass_x0, p->pass_y0, p->stock_z, p->x0, p->y0, p->pitch, p->wall_y};
+                           p->ae, p->pass_x0, p->pass_y0, p->stock_z, p->x0, p->y0, p->pitch, p->wall_y,
+                           p->feed_dir_deg};
     for (double v : vals)
         if (!finite(v)) return fail(FSM_E_INVALID, "non-finite process value");
     if (!(p->fz > 0.0)) return fail(FSM_E_INVALID, "fz must be > 0");
@@ -101,6 +102,8 @@ static fsm_status check_process(const fsm_process_desc* p) {
         return fail(FSM_E_INVALID, "a wall map takes a single pass");
     if (p->pass_mode != FSM_PASS_ONE_WAY && p->pass_mode != FSM_PASS_ZIGZAG)
         return fail(FSM_E_INVALID, "unknown pass_mode");
+    if (p->surface == FSM_SURFACE_WALL && feed_tilted(*p))
+        return fail(FSM_E_INVALID, "a wall map takes the +X feed (feed_dir_deg a multiple of 360)");
     return FSM_OK;
 }
 
@@ -170,6 +173,23 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
             s.tile_x = w;
         }
     }
+    // surfaces fed off the X axis: a square tile of the same cell budget (a
+    // tile's extent along and across a tilted feed, which bounds the steps
+    // and phases enumerated for it, grows with its longer side)
+    if (group && n_group > 0) {
+        bool all_tilted = false;
+        for (int i = 0; i < n_group; ++i)
+            if (group[i]->precision == p.precision) {
+                all_tilted = feed_tilted(*group[i]);
+                if (!all_tilted) break;
+            }
+        if (all_tilted) {
+            const int cells = s.tile_x * s.tile_y;
+            const int side = std::max(4, (int)floor(sqrt((double)cells)) & ~3);
+            s.tile_x = side;
+            s.tile_y = std::max(1, cells / side);
+        }
+    }
     if (o) {
         if (o->tile_x > 0) s.tile_x = o->tile_x;
         if (o->tile_y > 0) s.tile_y = o->tile_y;
@@ -216,6 +236,8 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
     s->surface = p.surface;
     s->wall_y = p.wall_y;
     s->pass_mode = p.pass_mode;
+    s->feed_dir_deg = p.feed_dir_deg;
+    s->tilted = feed_tilted(p) ? 1 : 0;
     s->x0 = p.x0;
     s->y0 = p.y0;
     s->pitch = p.pitch;
@@ -345,7 +367,7 @@ fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* sm
         return fail(FSM_E_INVALID, "block_threads must be a multiple of 32 in 64..512");
     if (sh.tile_x < 4 || sh.tile_y < 1 || (sh.tile_x & 3)) return fail(FSM_E_INVALID, "tile_x must be a multiple of 4");
     *smem = sweep_smem_bytes(precision, sh.tile_x, sh.tile_y, sh.threads);
-    if (*smem + 1024 > ctx->smem_optin) return fail(FSM_E_INVALID, "tile does not fit in shared memory");
+    if (*smem + sweep_static_bytes() > ctx->smem_optin) return fail(FSM_E_INVALID, "tile does not fit in shared memory");
     // the occupancy queries cost host time on every call: cached per context
     const std::array<long long, 3> key = {precision, sh.threads, (long long)*smem};
     int b = -1;
@@ -371,10 +393,10 @@ fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* sm
 
 std::string tune_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
     char buf[256];
-    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%.6g/%d/%d/%.6g", p.surface, p.precision, t.kind, t.n_teeth,
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%.6g/%d/%d/%.6g/%d", p.surface, p.precision, t.kind, t.n_teeth,
              t.n_edge + ((t.kind == FSM_TOOL_FLAT || t.kind == FSM_TOOL_TORUS) ? t.n_end : 0),
              (int)steps_per_rev(p.rot_step_deg), t.diameter,
-             p.nx, p.ny, p.pitch);
+             p.nx, p.ny, p.pitch, feed_tilted(p) ? 1 : 0);
     return buf;
 }
 
@@ -402,16 +424,20 @@ fsm_status check_fp32_band(const fsm_tool_desc& t, const fsm_process_desc& p, co
     return FSM_OK;
 }
 
-fsm_status check_opts(const fsm_predict_opts* o) {
+fsm_status check_opts(const fsm_predict_opts* o, const fsm_process_desc* const* procs, int n) {
     if (o && o->sweep_form != FSM_FORM_AUTO && o->sweep_form != FSM_FORM_ITEM && o->sweep_form != FSM_FORM_PHASE)
         return fail(FSM_E_INVALID, "sweep_form must be FSM_FORM_AUTO, FSM_FORM_ITEM or FSM_FORM_PHASE");
+    if (o && o->sweep_form == FSM_FORM_PHASE)
+        for (int i = 0; i < n; ++i)
+            if (feed_tilted(*procs[i]))
+                return fail(FSM_E_INVALID, "FSM_FORM_PHASE needs the +X feed (feed_dir_deg a multiple of 360)");
     return FSM_OK;
 }
 
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st) {
-    if (fsm_status rc0 = check_opts(opts)) return rc0;
     const fsm_process_desc* self = &p;
+    if (fsm_status rc0 = check_opts(opts, &self, 1)) return rc0;
     const fsm_tool_desc* self_tool = &t;
     Shape sh = pick_shape(p, opts, &self, 1, ctx->sm_count, &self_tool);
     fsm_predict_opts tuned_opts;
@@ -456,7 +482,7 @@ fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_d
     // tiles are handed out by a device counter that the planning kernel zeroed
     e = launch_sweep_shaped(p.precision, d_s, 1, nullptr, tiles, s.tile_queue,
                             opts ? (long long*)opts->d_counters : nullptr, grid, sh.threads, smem, st,
-                            phase_form_pays(t, p, sh.tile_x, s.form));
+                            phase_form_pays(t, p, sh.tile_x, s.form), feed_tilted(p));
     if (opts && opts->sweep_events[1]) cudaEventRecord((cudaEvent_t)opts->sweep_events[1], st);
     cudaError_t e2 = cudaFreeAsync(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");

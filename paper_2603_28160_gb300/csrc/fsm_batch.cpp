@@ -30,6 +30,7 @@ struct BatchLayout {
            off_cb32 = 0, off_part64 = 0, off_part32 = 0, off_tables = 0, total = 0;
     bool rough = false;
     bool phase_form32 = false, phase_form64 = false;  // some surface's runs come back for many revolutions
+    bool tilt32 = false, tilt64 = false;              // some surface is fed off the X axis
     int plan_work = 0;  // largest (edge points + phases) of a surface, for the planning grid
     long long* counters = nullptr;
     void* events[2] = {nullptr, nullptr};
@@ -43,7 +44,7 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
                        fsm_roughness_out* d_rough, const fsm_predict_opts* opts, char* base, BatchLayout* L,
                        const TableRef* trefs = nullptr) {
     if (n < 1) return fail(FSM_E_INVALID, "batch size must be >= 1");
-    if (fsm_status rc0 = check_opts(opts)) return rc0;
+    if (fsm_status rc0 = check_opts(opts, procs, n)) return rc0;
     const int form = opts ? opts->sweep_form : FSM_FORM_AUTO;
     std::vector<int> order;
     order.reserve(n);
@@ -67,6 +68,7 @@ fsm_status build_batch(fsm_ctx* ctx, int n, const fsm_tool_desc* const* tools,
         const bool f64 = procs[i]->precision == FSM_FP64;
         if (phase_form_pays(*tools[i], *procs[i], f64 ? L->sh64.tile_x : L->sh32.tile_x, form))
             (f64 ? L->phase_form64 : L->phase_form32) = true;
+        if (feed_tilted(*procs[i])) (f64 ? L->tilt64 : L->tilt32) = true;
     }
     L->counters = opts ? (long long*)opts->d_counters : nullptr;
     if (opts) {
@@ -172,13 +174,13 @@ fsm_status run_batch(fsm_ctx* ctx, const BatchLayout& L, char* base, cudaStream_
     if (L.n64) {
         const int grid = std::min(L.tiles64, ctx->sm_count * L.bps64);
         e = launch_sweep_shaped(FSM_FP64, d_surf, L.n64, (const int*)(base + L.off_tb64), L.tiles64, q, L.counters,
-                                grid, L.sh64.threads, L.smem64, st, L.phase_form64);
+                                grid, L.sh64.threads, L.smem64, st, L.phase_form64, L.tilt64);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel (FP64)");
     }
     if (L.n32) {
         const int grid = std::min(L.tiles32, ctx->sm_count * L.bps32);
         e = launch_sweep_shaped(FSM_FP32, d_surf + L.n64, L.n32, (const int*)(base + L.off_tb32), L.tiles32, q + 1,
-                                L.counters, grid, L.sh32.threads, L.smem32, st, L.phase_form32);
+                                L.counters, grid, L.sh32.threads, L.smem32, st, L.phase_form32, L.tilt32);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel (FP32)");
     }
     if (L.events[1]) cudaEventRecord((cudaEvent_t)L.events[1], st);

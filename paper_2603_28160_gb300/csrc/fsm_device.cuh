@@ -54,6 +54,9 @@ struct Surface {
     int32_t nx, ny, precision, E;    // E = points per tooth
     int32_t surface, pass_mode;      // FSM_SURFACE_*, FSM_PASS_*
     double wall_y;
+    double feed_dir_deg;             // feed direction (degrees from +X)
+    int32_t tilted;                  // feed_dir_deg is not a multiple of 360
+    int32_t pad0;
     // ---- launch geometry (inputs) ----
     int32_t tile_x, tile_y, ntx, nty;
     int32_t form;             // FSM_FORM_* of the sweep's phase 2
@@ -85,6 +88,14 @@ struct Surface {
     float fsc_hi, fsc_lo, fsc_f;    // feed per step in cells (fs / pitch), as a float pair and rounded
     float pitch_f;                  // pitch (FP32 enumeration and error bounds)
     float guard_extra;              // FP32 rounding of the bin scaling, in cells
+    // feed direction (tilted surfaces): the path of the +X process turned
+    // about (pass_x0, pass_y0); pass p, position index k sits at
+    // (pass_x0 + k fsx + p aex, pass_y0 + k fsy + p aey)
+    double feed_c, feed_s;          // cos, sin of the feed direction
+    double fsx, fsy, aex, aey;      // feed per step and step-over per pass, map x and y
+    float feed_cf, feed_sf;
+    float fscx_hi, fscx_lo, fscx_f; // fsx / pitch (cells per step) as a float pair and rounded
+    float fscy_hi, fscy_lo, fscy_f; // fsy / pitch
 };
 
 // ---------------------------------------------------------------------------
@@ -273,7 +284,18 @@ FSM_HD PointGeom load_geom(const float4* t4, float pitch) {
     return g;
 }
 
-// Tile/pass frame for the enumeration, all in FP32 relative to the tile:
+// A tilted surface's tables hold map-frame x, y rows but feed-frame
+// sinusoids: turn the point's constant offset (map frame) into the feed
+// frame (along, across the feed) with the direction's cos c and sin s.
+FSM_HD void to_feed_frame(PointGeom& g, float c, float s) {
+    const float a = c * g.wx + s * g.wy;
+    const float b = c * g.wy - s * g.wx;
+    g.wx = a;
+    g.wy = b;
+}
+
+// Tile/pass frame for the enumeration, all in FP32 relative to the tile
+// (a tilted surface's in the feed frame: x along the feed, y across it):
 //   y band  [ylo, yhi]   of P_y (tile rows minus the pass's y, with margin)
 //   z limit zhi          of P_z (stock - z_ref, with margin)
 //   x:      pass step n lands P_x + dx0 + n*fs in [xlo, xhi]

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stddef.h>
 
 #include "../../include/fsm.h"
@@ -18,14 +19,19 @@ namespace fsm {
 cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, int max_work, int sm_count, cudaStream_t st);
 
 size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads);
+size_t sweep_static_bytes();  // static shared memory of the sweep kernels
 int sweep_blocks_per_sm(int precision, int threads, size_t smem);
 cudaError_t sweep_allow_smem(size_t max_bytes);
 // phase_form: surfaces whose runs come back for many revolutions share
-// per-phase work (see phase_form_pays).
+// per-phase work (see phase_form_pays); tilt: some surface is fed off the X
+// axis (every task then takes the item form).
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,
-                                cudaStream_t st, bool phase_form);
+                                cudaStream_t st, bool phase_form, bool tilt);
+
+// A feed direction off the X axis (not a multiple of 360 degrees).
+inline bool feed_tilted(const fsm_process_desc& p) { return fmod(p.feed_dir_deg, 360.0) != 0.0; }
 
 // Whether the sweep is launched in the instantiation that chooses between
 // the item and the phase form per task (otherwise every task takes the item
@@ -38,6 +44,7 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
 // item (ball raster FP64 4.55 -> 3.57 ms with 512x32 tiles, 8 mm floor
 // 79.6 -> 55.0 ms).
 inline bool phase_form_pays(const fsm_tool_desc& t, const fsm_process_desc& p, int tile_x, int form = 0) {
+    if (feed_tilted(p)) return false;
     if (form == FSM_FORM_PHASE) return true;
     if (form == FSM_FORM_ITEM) return false;
     if (p.precision == FSM_FP64) return true;

@@ -186,10 +186,6 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
             v[d] = A[3 * d + 1] * qx - A[3 * d] * qy;
             w[d] = A[3 * d + 2] * qz;
         }
-        double* t64 = sf.tool64;
-        t64[0 * NE + idx] = u[0]; t64[1 * NE + idx] = u[1]; t64[2 * NE + idx] = u[2];
-        t64[3 * NE + idx] = v[0]; t64[4 * NE + idx] = v[1]; t64[5 * NE + idx] = v[2];
-        t64[6 * NE + idx] = w[0]; t64[7 * NE + idx] = w[1]; t64[8 * NE + idx] = w[2];
         float amp[3], mph[3];
         double a64[3];
         for (int d = 0; d < 3; ++d) {
@@ -203,6 +199,34 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
             amp[d] = (float)a;
             mph[d] = (float)m;
         }
+        // lowest workpiece z of the point over a turn (exact FP64; min is
+        // order-free): the map height on a floor, the map y on a wall; reach
+        // along and across the feed
+        const int dz = sf.surface == 1 ? 1 : 2;
+        zlo = fmin(zlo, w[dz] - a64[dz]);
+        rx = fmaxf(rx, (float)(fabs(w[0]) + a64[0]));
+        ry = fmaxf(ry, (float)(fabs(w[1]) + a64[1]));
+        // The sinusoids above are the feed frame's (the +X process); a
+        // tilted surface's x and y rows are turned into the map frame.
+        if (sf.tilted) {
+            double fsn, fc;
+            sincos(deg2rad(sf.feed_dir_deg), &fsn, &fc);
+            double x = u[0], y = u[1];
+            u[0] = fc * x - fsn * y;
+            u[1] = fsn * x + fc * y;
+            x = v[0];
+            y = v[1];
+            v[0] = fc * x - fsn * y;
+            v[1] = fsn * x + fc * y;
+            x = w[0];
+            y = w[1];
+            w[0] = fc * x - fsn * y;
+            w[1] = fsn * x + fc * y;
+        }
+        double* t64 = sf.tool64;
+        t64[0 * NE + idx] = u[0]; t64[1 * NE + idx] = u[1]; t64[2 * NE + idx] = u[2];
+        t64[3 * NE + idx] = v[0]; t64[4 * NE + idx] = v[1]; t64[5 * NE + idx] = v[2];
+        t64[6 * NE + idx] = w[0]; t64[7 * NE + idx] = w[1]; t64[8 * NE + idx] = w[2];
         // x and y rows in cells, so the sweep bins without a scaling step
         float4* t32 = sf.tool32 + 4 * (size_t)idx;
         const double ip = 1.0 / sf.pitch;
@@ -210,12 +234,6 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         t32[1] = make_float4((float)(u[1] * ip), (float)(v[1] * ip), (float)(w[1] * ip), (float)v[2]);
         t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
         t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
-        // lowest workpiece z of the point over a turn (exact FP64; min is
-        // order-free): the map height on a floor, the map y on a wall
-        const int dz = sf.surface == 1 ? 1 : 2;
-        zlo = fmin(zlo, w[dz] - a64[dz]);
-        rx = fmaxf(rx, (float)(fabs(w[0]) + a64[0]));
-        ry = fmaxf(ry, (float)(fabs(w[1]) + a64[1]));
     }
     // phase table, two turns (entry m + S repeats entry m)
     for (int m = first; m < S; m += stride) {
@@ -289,6 +307,23 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         sf->fsc_hi = (float)fsc;
         sf->fsc_lo = (float)(fsc - (double)sf->fsc_hi);
         sf->fsc_f = (float)fsc;
+        double fsn = 0.0, fc = 1.0;
+        if (sf->tilted) sincos(deg2rad(sf->feed_dir_deg), &fsn, &fc);
+        sf->feed_c = fc;
+        sf->feed_s = fsn;
+        sf->feed_cf = (float)fc;
+        sf->feed_sf = (float)fsn;
+        sf->fsx = fs * fc;
+        sf->fsy = fs * fsn;
+        sf->aex = -sf->ae * fsn;
+        sf->aey = sf->ae * fc;
+        const double fcx = sf->fsx / sf->pitch, fcy = sf->fsy / sf->pitch;
+        sf->fscx_hi = (float)fcx;
+        sf->fscx_lo = (float)(fcx - (double)sf->fscx_hi);
+        sf->fscx_f = (float)fcx;
+        sf->fscy_hi = (float)fcy;
+        sf->fscy_lo = (float)(fcy - (double)sf->fscy_hi);
+        sf->fscy_f = (float)fcy;
         // the bin scaling x_l * (1/pitch) rounds twice, relative to |x_l / pitch|
         const double u24 = 5.9604644775390625e-8;
         sf->guard_extra = (float)(3.0 * u24 * (double)max(sf->tile_x, sf->tile_y) + 1e-6);
@@ -309,7 +344,8 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
         const int j = g * 32 + lane;
         float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
         if (j < E) {
-            const PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), sf->pitch_f);
+            PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), sf->pitch_f);
+            if (sf->tilted) to_feed_frame(geo, sf->feed_cf, sf->feed_sf);
             zmin = geo.wz - geo.amp_z;
             ArcF za;
             ArcI ia[kMaxArcs];
@@ -388,11 +424,22 @@ constexpr int kTaskBits = 4096;
 
 struct TileShared {
     uint32_t accept[kTaskBits / 32];          // task t may have runs here (group reject passed)
-    float ylo[kPassCache], yhi[kPassCache];  // mm, for the enumeration
-    float dy[kPassCache];                     // pass line - tile origin y, in cells
+    float ylo[kPassCache], yhi[kPassCache];  // mm, for the enumeration (tilted: across the feed)
+    float dy[kPassCache];                     // pass line - tile origin y, in cells (tilted: pass start y, hi)
+    float dy_lo[kPassCache];                  // tilted: pass start y - tile origin y, lo part (cells)
+    float dxp_hi[kPassCache], dxp_lo[kPassCache];  // tilted: pass start x - tile origin x (cells)
     float dx_hi, dx_lo;  // pass_x0 - tile origin x in cells, as a float pair
-    float xlo, xhi;      // tile x extent relative to pass_x0, margins included
+    float xlo, xhi;      // tile x extent relative to pass_x0, margins included (tilted: along the feed)
     float zhi;           // stock - z_ref + margin
+};
+
+// One pass seen from a tile: the enumeration's y band (mm; across the feed
+// on a tilted surface) and the pass in tile-local cells -- its line's y on a
+// +X feed; its start (x, y) as float pairs on a tilted feed.
+struct PassFrame {
+    float ylo, yhi;
+    float dy;                   // +X feed: pass line y; tilted: start y (hi part)
+    float dy_lo, dx_hi, dx_lo;  // tilted: start y (lo part), start x (pair)
 };
 
 template <typename Cell>
@@ -423,13 +470,23 @@ __device__ __forceinline__ Vec9 load_vec9(const double* t64, int NE, int idx) {
 // records) goes through these functions, with each rounding step spelled
 // out, so a point is assigned to the same cell wherever it is re-binned.
 __device__ __forceinline__ bool pass_reversed(const Surface& sf, int p) { return sf.pass_mode == 1 && (p & 1); }
-// tool reference x at local step n of pass p (a zig-zag return pass runs back)
+// tool reference x, y at local step n of pass p (a zig-zag return pass runs
+// back); a tilted surface's path is the +X path turned about (pass_x0, pass_y0)
 __device__ __forceinline__ double path_x(const Surface& sf, int p, int32_t n) {
     const int32_t k = pass_reversed(sf, p) ? sf.steps_per_pass - 1 - n : n;
+    if (sf.tilted) return __dadd_rn(sf.pass_x0, __fma_rn((double)k, sf.fsx, __dmul_rn((double)p, sf.aex)));
     return __dadd_rn(sf.pass_x0, __dmul_rn((double)k, sf.fs));
 }
+// the pass line's y on a +X feed
 __device__ __forceinline__ double path_y(const Surface& sf, int p) {
     return __dadd_rn(sf.path_y0, __dmul_rn((double)p, sf.path_dy));
+}
+__device__ __forceinline__ double path_y(const Surface& sf, int p, int32_t n) {
+    if (sf.tilted) {
+        const int32_t k = pass_reversed(sf, p) ? sf.steps_per_pass - 1 - n : n;
+        return __dadd_rn(sf.pass_y0, __fma_rn((double)k, sf.fsy, __dmul_rn((double)p, sf.aey)));
+    }
+    return path_y(sf, p);
 }
 __device__ __forceinline__ Pose64 pose64(const Vec9& v, double2 cs, double xc, double yc, double zr) {
     Pose64 P;
@@ -442,9 +499,50 @@ __device__ __forceinline__ long long bin64(double coord, double origin, double i
     return (long long)floor(__dmul_rn(__dsub_rn(coord, origin), inv_pitch));
 }
 
+// Tilted surfaces: the tile's extent along (a) and across (b) the feed,
+// relative to (pass_x0, pass_y0), and the start of pass p in tile-local
+// cells as float pairs.
 template <typename Cell>
+__device__ __forceinline__ void tile_feed_extent(const Surface& sf, const TileCtx<Cell>& tc, double* amin,
+                                                 double* amax, double* bmin, double* bmax) {
+    const double c = sf.feed_c, s = sf.feed_s;
+    const double x0 = tc.X0 - sf.pass_x0, x1 = x0 + (double)tc.txc * sf.pitch;
+    const double y0 = tc.Y0 - sf.pass_y0, y1 = y0 + (double)tc.tyc * sf.pitch;
+    *amin = fmin(x0 * c, x1 * c) + fmin(y0 * s, y1 * s);
+    *amax = fmax(x0 * c, x1 * c) + fmax(y0 * s, y1 * s);
+    *bmin = fmin(y0 * c, y1 * c) - fmax(x0 * s, x1 * s);
+    *bmax = fmax(y0 * c, y1 * c) - fmin(x0 * s, x1 * s);
+}
+template <typename Cell>
+__device__ __forceinline__ void pass_start_cells(const Surface& sf, const TileCtx<Cell>& tc, int p, float* dx_hi,
+                                                 float* dx_lo, float* dy_hi, float* dy_lo) {
+    const double dx = (__dadd_rn(sf.pass_x0, __dmul_rn((double)p, sf.aex)) - tc.X0) * sf.inv_pitch;
+    const double dy = (__dadd_rn(sf.pass_y0, __dmul_rn((double)p, sf.aey)) - tc.Y0) * sf.inv_pitch;
+    *dx_hi = (float)dx;
+    *dx_lo = (float)(dx - (double)*dx_hi);
+    *dy_hi = (float)dy;
+    *dy_lo = (float)(dy - (double)*dy_hi);
+}
+
+template <bool kTilt, typename Cell>
 __device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCtx<Cell>& tc, TileShared& ts) {
     const int np = min(sf.n_passes, kPassCache);
+    if (kTilt && sf.tilted) {
+        double amin, amax, bmin, bmax;
+        tile_feed_extent(sf, tc, &amin, &amax, &bmin, &bmax);
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            ts.ylo[p] = (float)(bmin - (double)p * sf.ae) - kMarginMm;
+            ts.yhi[p] = (float)(bmax - (double)p * sf.ae) + kMarginMm;
+            pass_start_cells(sf, tc, p, &ts.dxp_hi[p], &ts.dxp_lo[p], &ts.dy[p], &ts.dy_lo[p]);
+        }
+        if (threadIdx.x == 0) {
+            ts.dx_hi = ts.dx_lo = 0.f;
+            ts.xlo = (float)amin - kMarginMm;
+            ts.xhi = (float)amax + kMarginMm;
+            ts.zhi = (float)(sf.stock - sf.z_ref) + kMarginMm;
+        }
+        return;
+    }
     const double y1 = tc.Y0 + (double)tc.tyc * sf.pitch;
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
         const double yc = path_y(sf, p);
@@ -462,34 +560,47 @@ __device__ __forceinline__ void fill_tile_shared(const Surface& sf, const TileCt
     }
 }
 
-// y band of pass p relative to the pass line, and the pass line relative to the tile
-template <typename Cell>
+// y band of pass p relative to the pass line, and the pass relative to the tile
+template <bool kTilt, typename Cell>
 __device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<Cell>& tc, const TileShared& ts,
-                                          int p, float* ylo, float* yhi, float* dy) {
+                                          int p, PassFrame& pf) {
     if (p < kPassCache) {
-        *ylo = ts.ylo[p];
-        *yhi = ts.yhi[p];
-        *dy = ts.dy[p];
+        pf.ylo = ts.ylo[p];
+        pf.yhi = ts.yhi[p];
+        pf.dy = ts.dy[p];
+        if (kTilt && sf.tilted) {
+            pf.dy_lo = ts.dy_lo[p];
+            pf.dx_hi = ts.dxp_hi[p];
+            pf.dx_lo = ts.dxp_lo[p];
+        }
+    } else if (kTilt && sf.tilted) {
+        double amin, amax, bmin, bmax;
+        tile_feed_extent(sf, tc, &amin, &amax, &bmin, &bmax);
+        pf.ylo = (float)(bmin - (double)p * sf.ae) - kMarginMm;
+        pf.yhi = (float)(bmax - (double)p * sf.ae) + kMarginMm;
+        pass_start_cells(sf, tc, p, &pf.dx_hi, &pf.dx_lo, &pf.dy, &pf.dy_lo);
     } else {
         const double yc = path_y(sf, p);
-        *ylo = (float)(tc.Y0 - yc) - kMarginMm;
-        *yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
-        *dy = (float)((yc - tc.Y0) * sf.inv_pitch);
+        pf.ylo = (float)(tc.Y0 - yc) - kMarginMm;
+        pf.yhi = (float)(tc.Y0 + (double)tc.tyc * sf.pitch - yc) + kMarginMm;
+        pf.dy = (float)((yc - tc.Y0) * sf.inv_pitch);
     }
 }
 
 // Phase 1 of a warp task: lane = edge point j = 32 g + lane of tooth K. Each
 // lane enumerates its runs for pass p and stores them with their iteration
-// bookkeeping, its FP32 anchor and guard band. t4 and pt (zb, eps_z) stay
-// in the lane's registers for phase 2. Returns whether any lane has work.
-__device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& ts, float ylo, float yhi, int K,
-                                          int g, int p, WarpScratch& ws, float4 (&t4)[3], float2& pt) {
+// bookkeeping, its FP32 anchor and guard band. t4 and zb (the FP32 height
+// base z_ref - stock + w_z) stay in the lane's registers for phase 2.
+// Returns whether any lane has work.
+template <bool kTilt>
+__device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& ts, const PassFrame& pf, int K,
+                                          int g, int p, WarpScratch& ws, float4 (&t4)[3], float& zb) {
     const int lane = threadIdx.x & 31;
     const int E = sf.E;
     const int j = g * 32 + lane;
     int nr = 0;
     t4[0] = t4[1] = t4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    pt = make_float2(0.f, 0.f);
+    zb = 0.f;
     if (j < E) {
         const float4* tp = sf.tool32 + 4 * (size_t)(K * E + j);
         t4[0] = tp[0];
@@ -507,9 +618,19 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         geo.mph_z = t3.x;
         geo.amp_x = t3.y;
         geo.mph_x = t3.z;
+        // FP32 error bounds of z and of the tile-local x, y for this point
+        // (error model in the precision-scheme documentation), 1.5x margin;
+        // on a tilted surface the map-frame x and y sinusoids are mixtures
+        // of the tabulated feed-frame ones (amplitude at most their sum)
+        const float u24 = 5.9604644775390625e-8f;
+        const bool tilted = kTilt && sf.tilted;
+        const float amp_xy = tilted ? geo.amp_x + geo.amp_y : fmaxf(geo.amp_x, geo.amp_y);
+        const float pt_err = 6.f * amp_xy + 3.f * (fabsf(geo.wx) + fabsf(geo.wy) + fabsf(geo.wz)) +
+                             3.f * (float)max(sf.tile_x, sf.tile_y) * pitch;
+        if (tilted) to_feed_frame(geo, sf.feed_cf, sf.feed_sf);
         TileFrame f;
-        f.ylo = ylo;
-        f.yhi = yhi;
+        f.ylo = pf.ylo;
+        f.yhi = pf.yhi;
         f.zhi = ts.zhi;
         f.xlo = ts.xlo;
         f.xhi = ts.xhi;
@@ -522,14 +643,7 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         f.reversed = pass_reversed(sf, p) ? 1 : 0;
         Run runs[kMaxArcs];
         const int n = point_runs(geo, f, runs);
-        // FP32 error bounds of z and of the tile-local x, y for this point
-        // (error model in the precision-scheme documentation), 1.5x margin
-        const float u24 = 5.9604644775390625e-8f;
-        const float amp_xy = fmaxf(geo.amp_x, geo.amp_y);
-        const float pt_err = 6.f * amp_xy + 3.f * (fabsf(geo.wx) + fabsf(geo.wy) + fabsf(geo.wz)) +
-                             3.f * (float)max(sf.tile_x, sf.tile_y) * pitch;
-        pt.x = sf.zrel_f + geo.wz;                                                          // zb
-        pt.y = 1.5f * u24 * (5.f * geo.amp_z + 4.f * (fabsf(sf.zrel_f) + fabsf(geo.wz)));  // eps_z
+        zb = sf.zrel_f + geo.wz;
         for (int a = 0; a < n; ++a) {
             const RunIter it = run_iter(runs[a], sf.S);
             if (it.total <= 0) continue;
@@ -543,7 +657,10 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
             r.len_last = it.len_last;
             const int32_t sA = it.occ0 + it.first_off;
             const int32_t nA = f.reversed ? f.n_steps - 1 - (sA - f.s0) : sA - f.s0;
-            r.dxA = df_affine(ts.dx_hi, ts.dx_lo, nA, sf.fsc_hi, sf.fsc_lo);  // cells
+            if (tilted)
+                r.dxA = df_affine(pf.dx_hi, pf.dx_lo, nA, sf.fscx_hi, sf.fscx_lo);  // cells
+            else
+                r.dxA = df_affine(ts.dx_hi, ts.dx_lo, nA, sf.fsc_hi, sf.fsc_lo);  // cells
             const float span_mm = (float)(runs[a].s_hi - runs[a].s_lo) * sf.fs_f;
             r.g_cells = 1.5f * u24 * (pt_err + 2.f * span_mm) * sf.inv_pitch_f + sf.guard_extra;
         }
@@ -591,10 +708,23 @@ __device__ __forceinline__ double height64(double2 cs, double uz, double vz, dou
     return __dadd_rn(zr, __fma_rn(cs.x, uz, __fma_rn(cs.y, vz, wz)));
 }
 
+// FP32 height of an FP32 map's point relative to the stock: the FP32 pose's
+// z with the operations of the sweep's walks, so a point stores the same
+// value whether its cell was decided in FP32 or re-binned in FP64.
+__device__ __forceinline__ float height32(const Surface& sf, int m, int idx) {
+    const float4* t = sf.tool32 + 4 * (size_t)idx;
+    const float uz = t[0].w, vz = t[1].w, zb = sf.zrel_f + t[2].x;
+    const float2 c = sf.ph32[m];
+    return fmaf(c.x, uz, fmaf(c.y, vz, zb));
+}
+
 // Re-bin queued points in FP64 (lanes < count take one entry each). Takes
 // the tile by value and returns this lane's (re-binned, atomics, cutting)
 // counts, so the caller's counters stay in registers; cutting is counted
-// here for FP64 maps only (FP32 maps count it from the FP32 pose).
+// here for FP64 maps only (FP32 maps count it from the FP32 pose). The FP64
+// pose decides the cell; the height is the map's own: FP64 for FP64 maps,
+// the FP32 pose's for FP32 maps (so an FP32 map does not depend on which
+// points were ambiguous, i.e. on the tile shape).
 template <bool F64>
 __device__ __noinline__ uint4 rebin_flush(const Surface& sf, CellOf<F64>* cells, int tx, int ty, int txc, int tyc,
                                           WarpScratch& ws, int p, int count) {
@@ -604,14 +734,17 @@ __device__ __noinline__ uint4 rebin_flush(const Surface& sf, CellOf<F64>* cells,
         const int NE = sf.n_teeth * sf.E;
         const int s = ws.q_s[lane], m = ws.q_m[lane], idx = ws.q_idx[lane];
         const Vec9 v = load_vec9(sf.tool64, NE, idx);
-        const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, p, s - p * sf.steps_per_pass), path_y(sf, p), sf.z_ref);
+        const int32_t n = s - p * sf.steps_per_pass;
+        const Pose64 P = pose64(v, sf.ph64[m], path_x(sf, p, n), path_y(sf, p, n), sf.z_ref);
         c.x = 1u;
-        if (P.z < sf.stock) {
+        float z32 = 0.f;
+        if constexpr (!F64) z32 = height32(sf, m, idx);
+        if (F64 ? P.z < sf.stock : z32 < 0.f) {
             const long long ig = bin64(P.x, sf.x0, sf.inv_pitch) - (long long)tx * sf.tile_x;
             const long long kg = bin64(P.y, sf.y0, sf.inv_pitch) - (long long)ty * sf.tile_y;
             if (ig >= 0 && ig < txc && kg >= 0 && kg < tyc) {
                 CellOf<F64>* cell = cells + (int)kg * sf.tile_x + (int)ig;
-                const auto e = F64 ? (CellOf<F64>)cell_key(P.z) : (CellOf<F64>)cell_key((float)(P.z - sf.stock));
+                const auto e = F64 ? (CellOf<F64>)cell_key(P.z) : (CellOf<F64>)cell_key(z32);
                 if (e < *cell) {
                     atomicMin(cell, e);
                     c.y = 1u;
@@ -672,23 +805,23 @@ __device__ __forceinline__ void rebin_push(const Surface& sf, const TileCtx<Cell
 // Ambiguous points of FP32 maps (within the guard band of a cell boundary)
 // wait in a per-warp queue and are checked 32 at a time against the cells
 // they may belong to: their own and the neighbours across the near
-// boundaries, clamped to the tile. Those whose height, lowered by the FP32
-// error bound, is below one of them go on to FP64 re-binning. Cell values
-// only decrease, so a check made later than the point's evaluation skips no
-// point that could still lower a cell. (FP64 maps re-bin every ambiguous
-// point: their cells hold FP64 heights.)
+// boundaries, clamped to the tile. Those whose FP32 height -- the value a
+// re-binned point stores -- is below one of them go on to FP64 re-binning.
+// Cell values only decrease, so a check made later than the point's
+// evaluation skips no point that could still lower a cell. (FP64 maps
+// re-bin every ambiguous point: their cells hold FP64 heights.)
 constexpr int kAmbCap = 64;
 struct AmbQueue {
     uint32_t ik[kAmbCap];   // (i + 1) | (k + 1) << 16: tile-local cell of the FP32 pose
     uint32_t mdd[kAmbCap];  // phase index | (dx + 1) << 28 | (dy + 1) << 30: the near boundaries
-    uint32_t elo[kAmbCap];  // encoding of z - eps_z
+    uint32_t elo[kAmbCap];  // cell key of the point's FP32 height
     int32_t s[kAmbCap], idx[kAmbCap];
 };
 
 // Queue this lane's point if `want` (warp-cooperative; i in [-1, txc] and
 // k in [-1, tyc], the cells that can have a neighbour in the tile).
 __device__ __forceinline__ void amb_push(AmbQueue& aq, bool want, int i, int k, float rx, float ry, float g,
-                                         float z, float eps_z, int32_t s, int32_t m, int idx, int& an) {
+                                         float z, int32_t s, int32_t m, int idx, int& an) {
     const int lane = threadIdx.x & 31;
     const unsigned bal = __ballot_sync(0xffffffffu, want);
     if (want) {
@@ -697,7 +830,7 @@ __device__ __forceinline__ void amb_push(AmbQueue& aq, bool want, int i, int k, 
         const int dy = ry < g ? -1 : (ry > 1.f - g ? 1 : 0);
         aq.ik[pos] = (uint32_t)(i + 1) | ((uint32_t)(k + 1) << 16);
         aq.mdd[pos] = (uint32_t)m | ((uint32_t)(dx + 1) << 28) | ((uint32_t)(dy + 1) << 30);
-        aq.elo[pos] = enc32(__float_as_uint(z - eps_z));
+        aq.elo[pos] = cell_key(z);
         aq.s[pos] = s;
         aq.idx[pos] = idx;
     }
@@ -757,12 +890,12 @@ __host__ __device__ constexpr size_t sweep_scratch_bytes(int precision, int thre
 template <bool F64>
 __device__ __forceinline__ void push_ambiguous(const Surface& sf, const TileCtx<CellOf<F64>>& tc, WarpScratch& ws,
                                                AmbQueue* aq, int p, bool want, int i, int k, float rx, float ry,
-                                               float g, float z, float eps_z, int32_t s, int32_t m, int idx,
+                                               float g, float z, int32_t s, int32_t m, int idx,
                                                int& an, int& qn, Counters& cnt) {
     if constexpr (F64) {
         rebin_push<true>(sf, tc, ws, p, want, s, m, idx, qn, cnt);
     } else {
-        amb_push(*aq, want, i, k, rx, ry, g, z, eps_z, s, m, idx, an);
+        amb_push(*aq, want, i, k, rx, ry, g, z, s, m, idx, an);
         if (an >= 32) {
             amb_flush(sf, tc, ws, *aq, p, an, qn, cnt);
             an -= 32;
@@ -818,16 +951,22 @@ constexpr int kItemLanes = 8;
 #define FSM_ITEM_CHAINS 2
 #endif
 constexpr int kItemChains = FSM_ITEM_CHAINS;  // items per lane and iteration (independent chains)
-template <bool F64, int U = kItemChains>
-__device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
-                                            int g, int p, WarpScratch& ws, AmbQueue* aq, const float4 (&t4)[3],
-                                            float2 pt, Counters& cnt) {
+// kTilt: the surface is fed off the X axis; y then moves by fsy per step
+// from the run's own anchor, exactly as x does.
+template <bool F64, int U = kItemChains, bool kTilt = false>
+__device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<CellOf<F64>>& tc, const PassFrame& pf,
+                                            int K, int g, int p, WarpScratch& ws, AmbQueue* aq,
+                                            const float4 (&t4)[3], float zb_lane, Counters& cnt) {
     using Cell = CellOf<F64>;
     constexpr int L = kItemLanes;
     const int lane = threadIdx.x & 31;
     const int hl = lane & (L - 1), grp = lane / L;
     const int S = sf.S;
-    const float fs32 = pass_reversed(sf, p) ? -sf.fsc_f : sf.fsc_f;  // cells per step; back on a return pass
+    const bool back = pass_reversed(sf, p);
+    // cells per step; back on a return pass
+    const float fs32 = kTilt ? (back ? -sf.fscx_f : sf.fscx_f) : (back ? -sf.fsc_f : sf.fsc_f);
+    const float fsy32 = kTilt ? (back ? -sf.fscy_f : sf.fscy_f) : 0.f;
+    const float dyp = pf.dy;
     const float2* __restrict__ ph32 = sf.ph32;
     const double2* __restrict__ ph64 = sf.ph64;
     const int NE = sf.n_teeth * sf.E;
@@ -854,7 +993,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
         const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
-        const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
+        const float zb = __shfl_sync(0xffffffffu, zb_lane, o);
         const int idx = K * sf.E + g * 32 + o;
         double uz64 = 0.0, vz64 = 0.0, wz64 = 0.0;
         if constexpr (F64) {
@@ -867,6 +1006,11 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         for (int o2 = L; o2 < 32; o2 <<= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o2));
         const int32_t sA = r.occ0 + r.first_off;
         const float gc = r.g_cells;
+        float dyA = dyp;  // tilted: the pass's y at the run's first step, in cells
+        if constexpr (kTilt) {
+            const int32_t n0 = sA - p * sf.steps_per_pass;
+            dyA = df_affine(pf.dy, pf.dy_lo, back ? sf.steps_per_pass - 1 - n0 : n0, sf.fscy_hi, sf.fscy_lo);
+        }
         // Cells of a point whose FP32 cell is ambiguous lie within M cells of
         // it: M = 1 while the band is under a cell (the host keeps FP32 maps'
         // bands under half a cell); FP64 maps at very fine pitch widen it, and
@@ -920,7 +1064,8 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
                 cnt.evaluated += (unsigned)v;
                 const float z = fmaf(c.x, uz, fmaf(c.y, vz, zb));
                 const float fx = fmaf((float)ds[k], fs32, r.dxA) + fmaf(c.x, ux, fmaf(c.y, vx, wx));
-                const float fy = dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
+                const float fy = kTilt ? fmaf((float)ds[k], fsy32, dyA) + fmaf(c.x, uy, fmaf(c.y, vy, wy))
+                                       : dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
                 // floor by one conversion each, the fraction by subtraction
                 const int ix = __float2int_rd(fx), ky = __float2int_rd(fy);
                 const float rx = fx - __int2float_rn(ix), ry = fy - __int2float_rn(ky);
@@ -956,7 +1101,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
             if (__any_sync(0xffffffffu, push_any)) {
 #pragma unroll
                 for (int k = 0; k < U; ++k)
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pk[k], ik[k], kk[k], rxk[k], ryk[k], gc, zk[k], eps_z,
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pk[k], ik[k], kk[k], rxk[k], ryk[k], gc, zk[k],
                                         sA + ds[k], mi[k], idx, an, qn, cnt);
             }
         }
@@ -978,7 +1123,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
 template <bool F64>
 __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<CellOf<F64>>& tc, float dyp, int K,
                                              int g, int p, WarpScratch& ws, AmbQueue* aq, const float4 (&t4)[3],
-                                             float2 pt, Counters& cnt) {
+                                             float zb_lane, Counters& cnt) {
     using Cell = CellOf<F64>;
     const int lane = threadIdx.x & 31;
     constexpr int L = kItemLanes;
@@ -1015,7 +1160,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
         const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
         const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
-        const float zb = __shfl_sync(0xffffffffu, pt.x, o), eps_z = __shfl_sync(0xffffffffu, pt.y, o);
+        const float zb = __shfl_sync(0xffffffffu, zb_lane, o);
         const int idx = K * sf.E + g * 32 + o;
         double uz64 = 0.0, vz64 = 0.0, wz64 = 0.0;
         if constexpr (F64) {
@@ -1106,9 +1251,9 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
                 const bool pa = va && amb_a && ia >= -M && ia <= txc - 1 + M;
                 const bool pb = vb && amb_b && ib >= -M && ib <= txc - 1 + M;
                 if (__any_sync(0xffffffffu, pa || pb)) {
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ky, rxa, ry, gc, z, eps_z, sA + (int32_t)ds, m,
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ky, rxa, ry, gc, z, sA + (int32_t)ds, m,
                                         idx, an, qn, cnt);
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pb, ib, ky, rxb, ry, gc, z, eps_z, sA + (int32_t)dsb, m,
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pb, ib, ky, rxb, ry, gc, z, sA + (int32_t)dsb, m,
                                         idx, an, qn, cnt);
                 }
                 ds = dsb + fS;
@@ -1131,7 +1276,10 @@ __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) 
 // (tile_base[s] = first tile of surface s); CTAs take tiles in a static
 // stride, or from *queue when it is not NULL. Inside a tile, warps take
 // (pass, tooth, 32-point group) tasks from a shared counter.
-template <bool FP64, bool kCount, bool kPhases>
+// kTilt: the launch may hold surfaces fed off the X axis (taken item by
+// item, with y stepping along the feed); the others run as in the plain
+// instantiation.
+template <bool FP64, bool kCount, bool kPhases, bool kTilt = false>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
                                                        const int* __restrict__ tile_base, int total_tiles,
                                                        int* queue, long long* counters) {
@@ -1174,7 +1322,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
         if constexpr (FP64) init = (Cell)enc64((unsigned long long)__double_as_longlong(sf.stock));
         else init = (Cell)enc32(__float_as_uint(0.0f));  // FP32 cells hold heights relative to the stock
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cells[c] = init;
-        fill_tile_shared(sf, tc, ts);
+        fill_tile_shared<kTilt>(sf, tc, ts);
         __syncthreads();
 
         const int G = (sf.E + 31) / 32;
@@ -1189,10 +1337,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             if (t < n_bits) {
                 const int p = t / (sf.n_teeth * G);
                 const int rem = t - p * sf.n_teeth * G;
-                float ylo, yhi, dyp;
-                pass_band(sf, tc, ts, p, &ylo, &yhi, &dyp);
+                PassFrame pf;
+                pass_band<kTilt>(sf, tc, ts, p, pf);
                 const float4 gb = sf.groups[rem];  // rem = K * G + g
-                ok = !(gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi);
+                ok = !(gb.y < pf.ylo || gb.x > pf.yhi || gb.z >= ts.zhi);
             }
             const unsigned bits = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) ts.accept[w0 >> 5] = bits;
@@ -1200,7 +1348,11 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
         __syncthreads();
         const double tile_x1 = tc.X0 + (double)tc.txc * sf.pitch;
         const double pass_x1 = sf.pass_x0 + (double)(sf.steps_per_pass - 1) * sf.fs;
-        const bool x_miss = (pass_x1 + sf.reach_x < tc.X0 - 1e-3) || (sf.pass_x0 - sf.reach_x > tile_x1 + 1e-3);
+        bool x_miss = (pass_x1 + sf.reach_x < tc.X0 - 1e-3) || (sf.pass_x0 - sf.reach_x > tile_x1 + 1e-3);
+        if (kTilt && sf.tilted) {  // along the feed: the tile's extent against the passes' reach
+            const double len = (double)(sf.steps_per_pass - 1) * sf.fs;
+            x_miss = ((double)ts.xlo > len + sf.reach_x + 1e-3) || ((double)ts.xhi < -sf.reach_x - 1e-3);
+        }
         while (!x_miss) {
             int task = 0;
             if (lane == 0) task = atomicAdd(&s_task, 1);
@@ -1210,15 +1362,15 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             const int rem = task - p * sf.n_teeth * G;
             const int K = rem / G, g = rem - K * G;
             if (task < kTaskBits && !((ts.accept[task >> 5] >> (task & 31)) & 1u)) continue;  // warp-uniform
-            float ylo, yhi, dyp;
-            pass_band(sf, tc, ts, p, &ylo, &yhi, &dyp);
+            PassFrame pf;
+            pass_band<kTilt>(sf, tc, ts, p, pf);
             if (task >= kTaskBits) {
                 const float4 gb = sf.groups[K * G + g];
-                if (gb.y < ylo || gb.x > yhi || gb.z >= ts.zhi) continue;  // warp-uniform
+                if (gb.y < pf.ylo || gb.x > pf.yhi || gb.z >= ts.zhi) continue;  // warp-uniform
             }
             float4 t4[3];
-            float2 pt;
-            if (!warp_runs(sf, ts, ylo, yhi, K, g, p, ws, t4, pt)) continue;
+            float zb;
+            if (!warp_runs<kTilt>(sf, ts, pf, K, g, p, ws, t4, zb)) continue;
             AmbQueue* aq = FP64 ? nullptr : aqs + warp;
             // runs that come back for many revolutions share their per-phase
             // work (phase form); others are walked item by item
@@ -1241,9 +1393,11 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             }
             if (sf.form_tasks && lane == 0) atomicAdd(sf.form_tasks + (by_phase ? 1 : 0), 1ull);
             if (by_phase)
-                sweep_phases<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
+                sweep_phases<FP64>(sf, tc, pf.dy, K, g, p, ws, aq, t4, zb, cnt);
+            else if (kTilt && sf.tilted)
+                sweep_items<FP64, kItemChains, kTilt>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
             else
-                sweep_items<FP64>(sf, tc, dyp, K, g, p, ws, aq, t4, pt, cnt);
+                sweep_items<FP64>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
             __syncwarp();
         }
         __syncthreads();
@@ -2136,7 +2290,7 @@ __global__ void __launch_bounds__(256) traj_record_kernel(const Surface* __restr
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_steps; s += gridDim.x * blockDim.x) {
         const int p = s / spp;
         const int m = s % S;
-        const double xc = path_x(sf, p, s - p * spp), yc = path_y(sf, p);
+        const double xc = path_x(sf, p, s - p * spp), yc = path_y(sf, p, s - p * spp);
         const double2 cs = __ldg(sf.ph64 + m);
         fsm_traj_point* o = out + (size_t)s * N;
         for (int K = 0; K < N; ++K) {
@@ -2187,13 +2341,29 @@ size_t sweep_smem_bytes(int precision, int tile_x, int tile_y, int threads) {
     return sweep_scratch_bytes(precision, threads) + cell * (size_t)tile_x * (size_t)tile_y;
 }
 
+size_t sweep_static_bytes() { return sizeof(TileShared) + 2 * sizeof(int); }
+
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,
-                                cudaStream_t st, bool phase_form) {
-    // counting and the FP32 phase form are separate instantiations: without
-    // them the counters are dead code and the item loop has the SM to itself
-    if (precision == 0 && phase_form) {
+                                cudaStream_t st, bool phase_form, bool tilt) {
+    // counting, the FP32 phase form and tilted feeds are separate
+    // instantiations: without them the counters are dead code and the item
+    // loop has the SM to itself
+    if (tilt) {
+        if (precision == 0 && d_counters)
+            sweep_kernel<true, true, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                               total_tiles, d_queue, d_counters);
+        else if (precision == 0)
+            sweep_kernel<true, false, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                                total_tiles, d_queue, nullptr);
+        else if (d_counters)
+            sweep_kernel<false, true, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                                total_tiles, d_queue, d_counters);
+        else
+            sweep_kernel<false, false, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+                                                                                 total_tiles, d_queue, nullptr);
+    } else if (precision == 0 && phase_form) {
         if (d_counters)
             sweep_kernel<true, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base, total_tiles,
                                                                         d_queue, d_counters);
@@ -2245,28 +2415,42 @@ cudaError_t sweep_allow_smem(size_t max_bytes) {
     if ((e = allow_dynamic_smem(sweep_kernel<false, true, false>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, false, false>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, true, true>, max_bytes)) != cudaSuccess) return e;
-    return allow_dynamic_smem(sweep_kernel<false, false, true>, max_bytes);
+    if ((e = allow_dynamic_smem(sweep_kernel<false, false, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, true, false, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, false, false, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<false, true, false, true>, max_bytes)) != cudaSuccess) return e;
+    return allow_dynamic_smem(sweep_kernel<false, false, false, true>, max_bytes);
 }
 
-// Resident CTAs per SM: the smaller of the counting and plain instantiations.
+// Resident CTAs per SM: the smallest over the instantiations of a precision.
 int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
-    int a = 0, b = 0;
-    cudaError_t e1, e2;
-    int c = 1 << 20, d = 1 << 20;
-    cudaError_t e3 = cudaSuccess, e4 = cudaSuccess;
+    int r[6] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e[6];
     if (precision == 0) {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<true, true, false>, threads, smem);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<true, false, false>, threads, smem);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, sweep_kernel<true, true, true>, threads, smem);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, sweep_kernel<true, false, true>, threads, smem);
+        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 0, sweep_kernel<true, true, false>, threads, smem);
+        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 1, sweep_kernel<true, false, false>, threads, smem);
+        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 2, sweep_kernel<true, true, true>, threads, smem);
+        e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 3, sweep_kernel<true, false, true>, threads, smem);
+        e[4] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 4, sweep_kernel<true, true, false, true>, threads,
+                                                             smem);
+        e[5] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 5, sweep_kernel<true, false, false, true>, threads,
+                                                             smem);
     } else {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_kernel<false, true, false>, threads, smem);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_kernel<false, false, false>, threads, smem);
-        e3 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, sweep_kernel<false, true, true>, threads, smem);
-        e4 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, sweep_kernel<false, false, true>, threads, smem);
+        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 0, sweep_kernel<false, true, false>, threads, smem);
+        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 1, sweep_kernel<false, false, false>, threads, smem);
+        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 2, sweep_kernel<false, true, true>, threads, smem);
+        e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 3, sweep_kernel<false, false, true>, threads, smem);
+        e[4] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 4, sweep_kernel<false, true, false, true>, threads,
+                                                             smem);
+        e[5] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 5, sweep_kernel<false, false, false, true>,
+                                                             threads, smem);
     }
-    const bool ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess;
-    return ok ? min(min(a, b), min(c, d)) : 0;
+    int b = 1 << 20;
+    for (int k = 0; k < 6; ++k) {
+        if (e[k] != cudaSuccess) return 0;
+        b = min(b, r[k]);
+    }
+    return b;
 }
 
 __global__ void rough_setup_one_kernel(RoughJob jb, int chunks, RoughJob* d_job, int* d_base) {

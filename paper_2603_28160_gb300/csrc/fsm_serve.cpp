@@ -32,6 +32,7 @@
 
 #include "../../include/fsm.h"
 #include "fsm_host.h"
+#include "fsm_internal.h"
 
 namespace fsm {
 
@@ -108,7 +109,7 @@ struct Server {
 
 // Inputs of the planned tables (plan_kernel, plan_finish_kernel's group
 // bounds): the tool, and the process fields that shape the edge points,
-// their orientation and the phase table. Feed, step-over, path, grid and
+// their orientation (feed direction included) and the phase table. Feed, step-over, path, grid and
 // precision do not enter them (except a round insert's edge length, which
 // depends on fz, and a wall's stock offset).
 static std::string table_key(const fsm_tool_desc& t, const fsm_process_desc& p) {
@@ -124,7 +125,8 @@ static std::string table_key(const fsm_tool_desc& t, const fsm_process_desc& p) 
     const double v[] = {t.runout_mm, t.runout_phase_deg, t.insert_radius, t.rake_f_deg, t.rake_p_deg, t.eps_r_mm,
                         t.eps_a_mm, t.corner_radius, p.ap, p.lead_deg, p.tilt_deg, p.rot_step_deg, p.phase0_deg,
                         t.kind == FSM_TOOL_INSERT ? p.fz : 0.0,
-                        p.surface == FSM_SURFACE_WALL ? p.wall_y - p.pass_y0 : 0.0};
+                        p.surface == FSM_SURFACE_WALL ? p.wall_y - p.pass_y0 : 0.0,
+                        feed_tilted(p) ? fmod(p.feed_dir_deg, 360.0) : 0.0};
     put(v, sizeof v);
     put(&p.rot_sense, sizeof p.rot_sense);
     put(&p.surface, sizeof p.surface);

@@ -42,7 +42,8 @@ class ProcessDesc(C.Structure):
                 ("pass_x0", C.c_double), ("pass_y0", C.c_double), ("steps_per_pass", C.c_int64),
                 ("stock_z", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("pitch", C.c_double),
                 ("nx", C.c_int32), ("ny", C.c_int32), ("precision", C.c_int32), ("surface", C.c_int32),
-                ("wall_y", C.c_double), ("pass_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("wall_y", C.c_double), ("pass_mode", C.c_int32), ("reserved", C.c_int32),
+                ("feed_dir_deg", C.c_double)]
 
 
 class PredictOpts(C.Structure):
@@ -176,6 +177,7 @@ def process_desc(p: ProcessSpec) -> ProcessDesc:
     d.surface = {"floor": 0, "wall": 1}[p.surface]
     d.wall_y = p.wall_y
     d.pass_mode = {"one_way": 0, "zigzag": 1}[p.pass_mode]
+    d.feed_dir_deg = p.feed_dir_deg
     return d
 
 

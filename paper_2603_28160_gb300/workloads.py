@@ -173,6 +173,49 @@ def raster_ball_d10(precision: str = "fp32", width: float = 5.0, pitch: float = 
     return Workload("raster_ball_d10", tool, proc)
 
 
+def plan_passes_dir(tool: ToolSpec, fz: float, rot_step_deg: float, width_x: float, width_y: float,
+                    centre, n_passes: int, ae: float, ap: float, pitch: float, feed_dir_deg: float):
+    """Tool path of a raster fed along feed_dir_deg: n_passes straight passes
+    ae apart, centred on the patch across the feed and long enough along it
+    that the whole tool clears the patch at both ends. Returns (pass_x0,
+    pass_y0, steps_per_pass): the start of pass 0, about which the +X path is
+    turned."""
+    th = math.radians(feed_dir_deg)
+    c, s = math.cos(th), math.sin(th)
+    along = 0.5 * (width_x * abs(c) + width_y * abs(s))
+    steps_per_rev = int(round(360.0 / rot_step_deg))
+    feed_per_step = tool.n_teeth * fz / steps_per_rev
+    overtravel = 0.5 * tool.diameter + tool.runout_mm + ap + 2.0 * pitch + tool.insert_radius
+    half_steps = int(math.ceil((along + overtravel) / feed_per_step))
+    a0 = -half_steps * feed_per_step
+    b0 = -0.5 * (n_passes - 1) * ae
+    return centre[0] + a0 * c - b0 * s, centre[1] + a0 * s + b0 * c, 2 * half_steps + 1
+
+
+def raster_ball_tilted(precision: str = "fp32", width: float = 5.0, feed_dir_deg: float = 30.0,
+                       pitch: float = 0.001, n_passes: Optional[int] = None, n_edge: int = 200,
+                       rot_step_deg: float = 0.1, pass_mode: str = "one_way") -> Workload:
+    """The ball raster's tool and cutting conditions fed at feed_dir_deg from
+    +X (the lead leans the axis toward the feed): passes ae = 0.3 mm apart
+    along the feed direction, enough of them to cross the square patch
+    (n_passes overrides), on the same axis-aligned grid."""
+    tool = ToolSpec("ball", 10.0, 4, [30.0], runout_mm=0.005, runout_phase_deg=30.0,
+                    n_edge=n_edge)
+    x0, y0, nx, ny = _patch(width, width, pitch)
+    ae = 0.3
+    th = math.radians(feed_dir_deg)
+    if n_passes is None:
+        across = nx * pitch * abs(math.sin(th)) + ny * pitch * abs(math.cos(th))
+        n_passes = int(math.ceil(across / ae)) + 1
+    px, py, spp = plan_passes_dir(tool, 0.08, rot_step_deg, nx * pitch, ny * pitch, (0.0, 0.0), n_passes, ae,
+                                  0.2, pitch, feed_dir_deg)
+    proc = ProcessSpec(fz=0.08, rpm=6000, rot_step_deg=rot_step_deg, ap=0.2, pass_x0=px,
+                       pass_y0=py, steps_per_pass=spp, x0=x0, y0=y0, pitch=pitch, nx=nx,
+                       ny=ny, n_passes=n_passes, ae=ae, lead_deg=15.0, precision=precision,
+                       pass_mode=pass_mode, feed_dir_deg=feed_dir_deg)
+    return Workload("raster_ball_tilted", tool, proc)
+
+
 def floor_flat_d12(seed: int = 2603, precision: str = "fp32", width: float = 20.0,
                    pitch: float = 0.002, rot_step_deg: float = 0.05) -> Workload:
     """Flat end mill D=12, 3 flutes with unequal helix 35/38/41 deg, runout

@@ -84,6 +84,7 @@ int main(void) {
          sizeof(fsm_predict_opts), sizeof(fsm_roughness_out), sizeof(fsm_result),
          offsetof(fsm_process_desc, steps_per_pass), offsetof(fsm_roughness_out, Ra_row),
          sizeof(fsm_traj_point), offsetof(fsm_process_desc, wall_y));
+  printf("%zu\n", offsetof(fsm_process_desc, feed_dir_deg));
   return 0;
 }
 '''
@@ -95,7 +96,8 @@ int main(void) {
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(fsm.ToolDesc), ctypes.sizeof(fsm.ProcessDesc), ctypes.sizeof(fsm.PredictOpts),
             ctypes.sizeof(fsm.RoughnessOut), ctypes.sizeof(fsm.Result), fsm.ProcessDesc.steps_per_pass.offset,
-            fsm.RoughnessOut.Ra_row.offset, fsm.TRAJ_BYTES, fsm.ProcessDesc.wall_y.offset]
+            fsm.RoughnessOut.Ra_row.offset, fsm.TRAJ_BYTES, fsm.ProcessDesc.wall_y.offset,
+            fsm.ProcessDesc.feed_dir_deg.offset]
     assert got == want
 
 

@@ -94,24 +94,62 @@ def test_guard_band_bounds_fp32_binning_error():
     assert worst < 0.7, worst
 
 
-def test_height_bound_covers_fp32_height_error():
-    """The FP32 height relative to the stock, z = fma(c, u_z, fma(s, v_z,
-    z_rel + w_z)), is within eps_z = 1.5 u (5 amp_z + 4 (|z_rel| + |w_z|)) of
-    the float64 value: an ambiguous point whose z - eps_z is not below a
-    candidate cell cannot lower it."""
-    rng = np.random.default_rng(7)
-    n = 1_000_000
-    amp = rng.uniform(0.0, 10.0, n)
-    ph = rng.uniform(0, 2 * np.pi, n)
-    uz, vz = amp * np.cos(ph), amp * np.sin(ph)
-    wz = rng.uniform(-10.0, 10.0, n)
-    zrel = rng.uniform(-15.0, 15.0, n)          # tool reference height - stock
-    th = rng.uniform(0.0, 2 * np.pi, n)
-    c, s = np.cos(th), np.sin(th)
-    zrel32, wz32 = zrel.astype(f32), wz.astype(f32)
-    zb = (zrel32 + wz32).astype(f32)
-    z32 = fma32(c.astype(f32), uz.astype(f32), fma32(s.astype(f32), vz.astype(f32), zb))
-    z64 = zrel + wz + c * uz + s * vz
-    eps = 1.5 * U24 * (5.0 * amp + 4.0 * (np.abs(zrel) + np.abs(wz)))
-    ratio = np.abs(z32.astype(np.float64) - z64) / eps
-    assert ratio.max() < 1.0, ratio.max()
+def test_guard_band_bounds_tilted_fp32_binning_error():
+    """A feed direction phi off the X axis: the x and y rows are the feed
+    frame's turned by phi (the band takes amp_a + amp_b for their
+    amplitude), and y, like x, steps from its own run anchor: y = fma(ds,
+    fsy, dyA) + fma(c, u_y, fma(s, v_y, w_y)) with dyA = the double-float
+    affine step of the pass start's y, fsx = fs cos phi, fsy = fs sin phi."""
+    rng = np.random.default_rng(20260329)
+    worst = 0.0
+    for pitch in (5e-4, 1e-3, 2e-3, 1e-2):
+        for tile_x, tile_y in ((168, 170), (128, 135), (64, 64)):
+            n = 200_000
+            amp = rng.uniform(0.0, 10.0, n)
+            aa, ab = amp * rng.uniform(0.0, 1.0, n), amp * rng.uniform(0.0, 1.0, n)
+            pha, phb = rng.uniform(0, 2 * np.pi, n), rng.uniform(0, 2 * np.pi, n)
+            ua, va, ub, vb = aa * np.cos(pha), aa * np.sin(pha), ab * np.cos(phb), ab * np.sin(phb)
+            wa, wb, wz = rng.uniform(-10.0, 10.0, (3, n))
+            phi = rng.uniform(0.0, 2 * np.pi, n)
+            cf, sf = np.cos(phi), np.sin(phi)
+            ux, uy = cf * ua - sf * ub, sf * ua + cf * ub
+            vx, vy = cf * va - sf * vb, sf * va + cf * vb
+            wx, wy = cf * wa - sf * wb, sf * wa + cf * wb
+            th = rng.uniform(0.0, 2 * np.pi, n)
+            c, s = np.cos(th), np.sin(th)
+            fs = 10.0 ** rng.uniform(-5.0, -2.0, n)
+            fsx, fsy = fs * cf, fs * sf
+            span = np.floor(rng.uniform(0.0, 1.0, n) * np.minimum(1e6, 20.0 / fs))
+            ds = np.floor(rng.uniform(0.0, 1.0, n) * (span + 1))
+            n_a = np.floor(rng.uniform(0.0, 1e6, n)).astype(np.int64)
+            X = rng.uniform(-1.0, tile_x + 1.0, n) * pitch
+            Y = rng.uniform(-1.0, tile_y + 1.0, n) * pitch
+            dx = X - ds * fsx - (c * ux + s * vx + wx) - n_a * fsx  # pass start - tile origin
+            dy = Y - ds * fsy - (c * uy + s * vy + wy) - n_a * fsy
+            c32, s32 = c.astype(f32), s.astype(f32)
+            rows = [(r / pitch).astype(f32) for r in (ux, vx, wx, uy, vy, wy)]
+
+            def pair(v):
+                hi = v.astype(f32)
+                return hi, (v - hi.astype(np.float64)).astype(f32)
+
+            dx_hi, dx_lo = pair(dx / pitch)
+            dy_hi, dy_lo = pair(dy / pitch)
+            fx_hi, fx_lo = pair(fsx / pitch)
+            fy_hi, fy_lo = pair(fsy / pitch)
+            dxa = df_affine(dx_hi, dx_lo, n_a, fx_hi, fx_lo)
+            dya = df_affine(dy_hi, dy_lo, n_a, fy_hi, fy_lo)
+            ds32 = ds.astype(f32)
+            fx = (fma32(ds32, (fsx / pitch).astype(f32), dxa) +
+                  fma32(c32, rows[0], fma32(s32, rows[1], rows[2]))).astype(f32)
+            fy = (fma32(ds32, (fsy / pitch).astype(f32), dya) +
+                  fma32(c32, rows[3], fma32(s32, rows[4], rows[5]))).astype(f32)
+            ex = np.abs(fx.astype(np.float64) - X / pitch)
+            ey = np.abs(fy.astype(np.float64) - Y / pitch)
+            pt_err = 6.0 * (aa + ab) + 3.0 * (np.abs(wx) + np.abs(wy) + np.abs(wz)) + \
+                3.0 * max(tile_x, tile_y) * pitch
+            g = 1.5 * U24 * (pt_err + 2.0 * span * fs) / pitch + 3.0 * U24 * max(tile_x, tile_y) + 1e-6
+            ratio = np.maximum(ex, ey) / g
+            assert ratio.max() < 1.0, (pitch, tile_x, tile_y, ratio.max())
+            worst = max(worst, float(ratio.max()))
+    assert worst < 0.7, worst

@@ -87,10 +87,14 @@ def test_small_parity(ctx, F, oracle_mod, name, prec):
         compare_roughness(r, ro, SA_REL[prec])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("tile", [(8, 8), (36, 20), (128, 32), (256, 64)])
-def test_fp64_tiling_invariance(ctx, F, tile):
-    """FP64 heights do not depend on the tile shape, bit for bit."""
-    w = with_prec(SMALL["ball_raster_ragged"](), "fp64")
+def test_tiling_invariance(ctx, F, tile, prec):
+    """Heights do not depend on the tile shape, bit for bit: a point's cell is
+    its FP64 cell whether FP32 tile-local arithmetic or FP64 re-binning
+    decided it, and its height is the map's own (FP64, or the FP32 pose's)
+    either way."""
+    w = with_prec(SMALL["ball_raster_ragged"](), prec)
     base = gpu_map(ctx, F, w).cpu().numpy()
     H = gpu_map(ctx, F, w, tile=tile).cpu().numpy()
     assert np.array_equal(H, base)

@@ -38,6 +38,10 @@ CASES = {
     "slot_flat_d6": lambda: W.slot_flat_d6(),
     "insert_case2": lambda: W.paper_case(1, length=0.6, width=0.4, pitch=0.004, rot_step_deg=0.25, n_edge=61),
     "raster_ball_reduced": lambda: W.raster_ball_d10(precision="fp64", width=0.3, n_passes=2),
+    # fed at 130 deg from +X, zig-zag: the path and tool turned about the start of pass 0
+    "ball_leaned_fed_130": lambda: Workload("ball_fed_130", _generic_ball().tool,
+                                            _generic_ball().process.replace(feed_dir_deg=130.0,
+                                                                            pass_mode="zigzag")),
     "torus_zigzag": lambda: Workload("torus_zz", ToolSpec("torus", 4.0, 3, [30.0], n_edge=21, n_end=15,
                                                           corner_radius=0.7, runout_mm=0.003),
                                      ProcessSpec(fz=0.05, rpm=1000, rot_step_deg=1.0, ap=0.3, lead_deg=6.0,
