@@ -99,12 +99,11 @@ struct Surface {
 };
 
 // ---------------------------------------------------------------------------
-// Order-preserving integer encodings: a < b as floats <=> enc(a) < enc(b)
+// Order-preserving integer encoding of doubles: a < b <=> enc(a) < enc(b)
 // as unsigned integers, so atomicMin on the encoding keeps the lowest height
-// whatever order the edge points arrive in.
+// whatever order the edge points arrive in (FP64 cells; FP32 cells hold raw
+// bits, see the sweep).
 // ---------------------------------------------------------------------------
-FSM_HD uint32_t enc32(uint32_t bits) { return (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u); }
-FSM_HD uint32_t dec32(uint32_t e) { return (e & 0x80000000u) ? (e & 0x7fffffffu) : ~e; }
 FSM_HD uint64_t enc64(uint64_t bits) {
     return (bits & 0x8000000000000000ull) ? ~bits : (bits | 0x8000000000000000ull);
 }

@@ -689,10 +689,21 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
 template <bool F64>
 using CellOf = typename std::conditional<F64, unsigned long long, uint32_t>::type;
 
-__device__ __forceinline__ uint32_t cell_key(float zrel) { return enc32(__float_as_uint(zrel)); }
+// Cell values. FP32 cells hold the raw bits of a height relative to the
+// stock: a cell starts at -0 and only ever takes heights below the stock
+// (negative), and negative floats order inversely as signed integers, -0
+// (INT_MIN) lowest of all -- so the lowest height is the largest integer
+// and a cell is lowered by a signed atomicMax on the bits, with no encoding.
+// FP64 cells hold the order-preserving encoding of the height (atomicMin).
+constexpr uint32_t kCell32Init = 0x80000000u;  // -0: the stock itself
+__device__ __forceinline__ uint32_t cell_key(float zrel) { return __float_as_uint(zrel); }
 __device__ __forceinline__ unsigned long long cell_key(double z) {
     return enc64((unsigned long long)__double_as_longlong(z));
 }
+__device__ __forceinline__ bool lowers(uint32_t e, uint32_t cell) { return (int32_t)e > (int32_t)cell; }
+__device__ __forceinline__ bool lowers(unsigned long long e, unsigned long long cell) { return e < cell; }
+__device__ __forceinline__ void lower_cell(uint32_t* cell, uint32_t e) { atomicMax((int*)cell, (int)e); }
+__device__ __forceinline__ void lower_cell(unsigned long long* cell, unsigned long long e) { atomicMin(cell, e); }
 
 // Key below which a height is below the stock: z < stock exactly when
 // cell_key(z) < stock_key(stock) (both zeros take the key of -0, the lowest
@@ -745,8 +756,8 @@ __device__ __noinline__ uint4 rebin_flush(const Surface& sf, CellOf<F64>* cells,
             if (ig >= 0 && ig < txc && kg >= 0 && kg < tyc) {
                 CellOf<F64>* cell = cells + (int)kg * sf.tile_x + (int)ig;
                 const auto e = F64 ? (CellOf<F64>)cell_key(P.z) : (CellOf<F64>)cell_key(z32);
-                if (e < *cell) {
-                    atomicMin(cell, e);
+                if (lowers(e, *cell)) {
+                    lower_cell(cell, e);
                     c.y = 1u;
                 }
                 c.z = F64 ? 1u : 0u;
@@ -855,7 +866,7 @@ __device__ __forceinline__ void amb_flush(const Surface& sf, const TileCtx<uint3
         const int i0 = max(min(i, i + dx), 0), i1 = min(max(i, i + dx), tc.txc - 1);
         const int k0 = max(min(k, k + dy), 0), k1 = min(max(k, k + dy), tc.tyc - 1);
         for (int kk = k0; kk <= k1; ++kk)
-            for (int ii = i0; ii <= i1; ++ii) w |= elo < tc.cells[kk * sf.tile_x + ii];
+            for (int ii = i0; ii <= i1; ++ii) w |= lowers(elo, tc.cells[kk * sf.tile_x + ii]);
     }
     __syncwarp();
     const int rest = count > 32 ? count - 32 : 0;
@@ -1086,11 +1097,11 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
                 cnt.cutting += F64 ? (unsigned)upd : (unsigned)in;
                 const int ci = ky * tile_x + ix;
                 const Cell cv = upd ? cells[ci] : (Cell)0;
-                if (upd && e < cv) {
-                    atomicMin(cells + ci, e);
+                if (upd && lowers(e, cv)) {
+                    lower_cell(cells + ci, e);
                     ++cnt.atomics;
                 }
-                pk[k] = cut && amb && ix >= -M && ix <= txc - 1 + M && ky >= -M && ky <= tyc - 1 + M;
+                pk[k] = cut && amb;  // pushed if near the tile (tested below, rarely reached)
                 push_any |= pk[k];
                 ik[k] = ix;
                 kk[k] = ky;
@@ -1100,9 +1111,11 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
             }
             if (__any_sync(0xffffffffu, push_any)) {
 #pragma unroll
-                for (int k = 0; k < U; ++k)
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pk[k], ik[k], kk[k], rxk[k], ryk[k], gc, zk[k],
+                for (int k = 0; k < U; ++k) {
+                    const bool near = ik[k] >= -M && ik[k] <= txc - 1 + M && kk[k] >= -M && kk[k] <= tyc - 1 + M;
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pk[k] && near, ik[k], kk[k], rxk[k], ryk[k], gc, zk[k],
                                         sA + ds[k], mi[k], idx, an, qn, cnt);
+                }
             }
         }
     }
@@ -1239,22 +1252,22 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
                 const int cia = ky * tile_x + ia, cib = ky * tile_x + ib;
                 const Cell cva = upd_a ? cells[cia] : (Cell)0;
                 const Cell cvb = upd_b ? cells[cib] : (Cell)0;
-                if (upd_a && e < cva) {
-                    atomicMin(cells + cia, e);
+                if (upd_a && lowers(e, cva)) {
+                    lower_cell(cells + cia, e);
                     ++cnt.atomics;
                 }
-                if (upd_b && e < cvb) {
-                    atomicMin(cells + cib, e);
+                if (upd_b && lowers(e, cvb)) {
+                    lower_cell(cells + cib, e);
                     ++cnt.atomics;
                 }
                 // (va, vb: ky in [-M, tyc - 1 + M], below the stock)
-                const bool pa = va && amb_a && ia >= -M && ia <= txc - 1 + M;
-                const bool pb = vb && amb_b && ib >= -M && ib <= txc - 1 + M;
+                const bool pa = va && amb_a, pb = vb && amb_b;  // pushed if near the tile (tested below)
                 if (__any_sync(0xffffffffu, pa || pb)) {
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pa, ia, ky, rxa, ry, gc, z, sA + (int32_t)ds, m,
+                    const bool near_a = ia >= -M && ia <= txc - 1 + M, near_b = ib >= -M && ib <= txc - 1 + M;
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pa && near_a, ia, ky, rxa, ry, gc, z, sA + (int32_t)ds, m,
                                         idx, an, qn, cnt);
-                    push_ambiguous<F64>(sf, tc, ws, aq, p, pb, ib, ky, rxb, ry, gc, z, sA + (int32_t)dsb, m,
-                                        idx, an, qn, cnt);
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pb && near_b, ib, ky, rxb, ry, gc, z,
+                                        sA + (int32_t)dsb, m, idx, an, qn, cnt);
                 }
                 ds = dsb + fS;
             }
@@ -1320,7 +1333,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
         const int ncell = sf.tile_x * sf.tile_y;
         Cell init;
         if constexpr (FP64) init = (Cell)enc64((unsigned long long)__double_as_longlong(sf.stock));
-        else init = (Cell)enc32(__float_as_uint(0.0f));  // FP32 cells hold heights relative to the stock
+        else init = (Cell)kCell32Init;  // FP32 cells hold heights relative to the stock
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cells[c] = init;
         fill_tile_shared<kTilt>(sf, tc, ts);
         __syncthreads();
@@ -1422,10 +1435,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                     const int k = c / q, i4 = (c - k * q) << 2;
                     const uint4 e = *reinterpret_cast<const uint4*>(cells + k * sf.tile_x + i4);
                     float4 v;
-                    v.x = st + __uint_as_float(dec32(e.x));
-                    v.y = st + __uint_as_float(dec32(e.y));
-                    v.z = st + __uint_as_float(dec32(e.z));
-                    v.w = st + __uint_as_float(dec32(e.w));
+                    v.x = st + __uint_as_float(e.x);
+                    v.y = st + __uint_as_float(e.y);
+                    v.z = st + __uint_as_float(e.z);
+                    v.w = st + __uint_as_float(e.w);
                     *reinterpret_cast<float4*>(
                         out + (size_t)(tc.ty * sf.tile_y + k) * sf.nx + tc.tx * sf.tile_x + i4) = v;
                 }
@@ -1433,7 +1446,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                 for (int c = threadIdx.x; c < tc.txc * tc.tyc; c += blockDim.x) {
                     const int k = c / tc.txc, i = c - k * tc.txc;
                     out[(size_t)(tc.ty * sf.tile_y + k) * sf.nx + tc.tx * sf.tile_x + i] =
-                        st + __uint_as_float(dec32(cells[k * sf.tile_x + i]));
+                        st + __uint_as_float(cells[k * sf.tile_x + i]);
                 }
             }
         }

@@ -1,10 +1,14 @@
 """Small pieces of the kernels' arithmetic modelled and checked on the CPU.
 
-- The order-preserving cell keys: a < b as floats exactly when key(a) <
-  key(b) as unsigned integers (so atomicMin on keys keeps the lowest height),
-  and the below-the-stock test of FP64 maps, key(z) < key(stock with both
-  zeros taken as -0), decides as z < stock does -- including z or the stock
-  being +0 or -0.
+- The FP64 maps' order-preserving cell keys: a < b as doubles exactly when
+  key(a) < key(b) as unsigned integers (so atomicMin on keys keeps the
+  lowest height), and their below-the-stock test, key(z) < key(stock with
+  both zeros taken as -0), decides as z < stock does -- including z or the
+  stock being +0 or -0.
+- The FP32 maps' raw cells: a cell starts at -0 and takes only heights
+  below the stock (negative floats); among those values, a < b as floats
+  exactly when bits(a) > bits(b) as signed integers, so a signed atomicMax
+  on the raw bits keeps the lowest height.
 - The double-float sums of the FP32 maps' roughness: Knuth's two-sum on the
   high parts is exact and symmetric in its operands (every lane of a
   butterfly reduction ends with the same pair), and a sum of many floats
@@ -18,12 +22,6 @@ def enc64(z):
     b = np.asarray(z, dtype=np.float64).view(np.uint64)
     sign = (b >> np.uint64(63)) == 1
     return np.where(sign, ~b, b | np.uint64(1 << 63))
-
-
-def enc32(z):
-    b = np.asarray(z, dtype=np.float32).view(np.uint32)
-    sign = (b >> np.uint32(31)) == 1
-    return np.where(sign, ~b, b | np.uint32(1 << 31))
 
 
 def stock_key(stock):
@@ -41,9 +39,18 @@ def test_keys_preserve_order():
     both_zero = (a == 0) & (b == 0)
     assert np.array_equal((ka < kb)[~both_zero], lt[~both_zero])
     assert np.array_equal((ka == kb)[~both_zero], eq[~both_zero])
-    a32, b32 = a.astype(f32), b.astype(f32)
-    z32 = (a32 == 0) & (b32 == 0)
-    assert np.array_equal((enc32(a32) < enc32(b32))[~z32], (a32 < b32)[~z32])
+    # FP32 cells: the values a cell can hold are -0 (its start) and negative
+    # floats; their raw bits as int32 order them inversely
+    neg = -np.abs(rng.normal(0, 1e3, 10**5)).astype(f32)
+    neg = np.concatenate([neg, f32([-1e-45, -1.2e-38, -3.4e38, -1.0, -0.0])])
+    neg = neg[(neg < 0) | (np.signbit(neg) & (neg == 0))]
+    x, y = neg, rng.permutation(neg)
+    ix, iy = x.view(np.int32), y.view(np.int32)
+    both_zero = (x == 0) & (y == 0)
+    assert np.array_equal((ix > iy)[~both_zero], (x < y)[~both_zero])
+    # -0, the start value, is below every other value as int32 (any cut lowers it)
+    assert f32(-0.0).view(np.int32) == np.iinfo(np.int32).min
+    assert (ix[x < 0] > np.iinfo(np.int32).min).all()
 
 
 def test_below_the_stock_on_keys_equals_the_fp64_comparison():
