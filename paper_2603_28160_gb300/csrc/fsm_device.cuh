@@ -64,7 +64,7 @@ struct Surface {
     unsigned long long* form_tasks;  // NULL or [2]: tasks walked in the item / phase form
     // ---- tables (device pointers, inputs) ----
     // [N*E][4]: (ux,vx,wx,uz) (uy,vy,wy,vz) (wz,amp_y,mph_y,amp_z) (mph_z,amp_x,mph_x,0); the x and y
-    // rows (ux..wy) are in cells (divided by the pitch), everything else in mm
+    // rows (ux..wy) are in cells (divided by the pitch; wx, wy less half a cell), everything else in mm
     float4* tool32;
     double* tool64;   // [9][N*E]: ux uy uz vx vy vz wx wy wz
     float2* ph32;     // [2S] (cos, sin) of Theta_m, m mod S: two turns, so m0 + offset needs no wrap
@@ -268,11 +268,12 @@ struct PointGeom {
     float wx, wy, wz, amp_x, amp_y, amp_z, mph_x, mph_y, mph_z;
 };
 
-// t4: the point's FP32 table row; pitch: the map pitch (x and y rows are in cells)
+// t4: the point's FP32 table row; pitch: the map pitch (x and y rows are in
+// cells, their constant parts less half a cell)
 FSM_HD PointGeom load_geom(const float4* t4, float pitch) {
     PointGeom g;
-    g.wx = t4[0].z * pitch;
-    g.wy = t4[1].z * pitch;
+    g.wx = (t4[0].z + 0.5f) * pitch;
+    g.wy = (t4[1].z + 0.5f) * pitch;
     g.wz = t4[2].x;
     g.amp_y = t4[2].y;
     g.mph_y = t4[2].z;

@@ -227,11 +227,14 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         t64[0 * NE + idx] = u[0]; t64[1 * NE + idx] = u[1]; t64[2 * NE + idx] = u[2];
         t64[3 * NE + idx] = v[0]; t64[4 * NE + idx] = v[1]; t64[5 * NE + idx] = v[2];
         t64[6 * NE + idx] = w[0]; t64[7 * NE + idx] = w[1]; t64[8 * NE + idx] = w[2];
-        // x and y rows in cells, so the sweep bins without a scaling step
+        // x and y rows in cells, so the sweep bins without a scaling step;
+        // their constant parts less half a cell, so a point's tile-local
+        // coordinate is centred on its cell: the nearest integer is the cell
+        // and the remainder the signed distance from the cell's centre
         float4* t32 = sf.tool32 + 4 * (size_t)idx;
         const double ip = 1.0 / sf.pitch;
-        t32[0] = make_float4((float)(u[0] * ip), (float)(v[0] * ip), (float)(w[0] * ip), (float)u[2]);
-        t32[1] = make_float4((float)(u[1] * ip), (float)(v[1] * ip), (float)(w[1] * ip), (float)v[2]);
+        t32[0] = make_float4((float)(u[0] * ip), (float)(v[0] * ip), (float)(w[0] * ip - 0.5), (float)u[2]);
+        t32[1] = make_float4((float)(u[1] * ip), (float)(v[1] * ip), (float)(w[1] * ip - 0.5), (float)v[2]);
         t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
         t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
     }
@@ -609,8 +612,8 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         const float4 t3 = tp[3];
         PointGeom geo;
         const float pitch = sf.pitch_f;  // the x, y rows are in cells
-        geo.wx = t4[0].z * pitch;
-        geo.wy = t4[1].z * pitch;
+        geo.wx = (t4[0].z + 0.5f) * pitch;
+        geo.wy = (t4[1].z + 0.5f) * pitch;
         geo.wz = t4[2].x;
         geo.amp_y = t4[2].y;
         geo.mph_y = t4[2].z;
@@ -837,8 +840,8 @@ __device__ __forceinline__ void amb_push(AmbQueue& aq, bool want, int i, int k, 
     const unsigned bal = __ballot_sync(0xffffffffu, want);
     if (want) {
         const int pos = an + __popc(bal & ((1u << lane) - 1u));
-        const int dx = rx < g ? -1 : (rx > 1.f - g ? 1 : 0);
-        const int dy = ry < g ? -1 : (ry > 1.f - g ? 1 : 0);
+        const int dx = rx < g - 0.5f ? -1 : (rx > 0.5f - g ? 1 : 0);  // (rx, ry from the cell's centre)
+        const int dy = ry < g - 0.5f ? -1 : (ry > 0.5f - g ? 1 : 0);
         aq.ik[pos] = (uint32_t)(i + 1) | ((uint32_t)(k + 1) << 16);
         aq.mdd[pos] = (uint32_t)m | ((uint32_t)(dx + 1) << 28) | ((uint32_t)(dy + 1) << 30);
         aq.elo[pos] = cell_key(z);
@@ -940,12 +943,13 @@ __device__ __forceinline__ void divmod_small(int32_t v, int32_t len, float inv_l
 
 // Shared FP32 binning of both walks (tile-local, in cells): the point's
 // x offset from the phase table and the x and y rows of its table entry
-// (already divided by the pitch), the pass position from the run's anchor
-// and the steps after the run's first item:
+// (already divided by the pitch, the constant parts less half a cell), the
+// pass position from the run's anchor and the steps after the run's first
+// item:
 //     x = fma(ds, fs, dxA) + fma(cos, ux, fma(sin, vx, wx)),
 //     y = dyp + fma(cos, uy, fma(sin, vy, wy)),
-// cell = (floor x, floor y), ambiguous within the run's guard band gc of a
-// cell boundary.
+// coordinates centred on cells: cell = (rint x, rint y), ambiguous within
+// the run's guard band gc of a cell boundary, |x - rint x| > 1/2 - gc.
 
 // Item form of phase 2: the task's runs are taken four at a time, one per
 // group of L = 8 lanes; each lane evaluates items hl and hl + L of every 2L
@@ -1077,8 +1081,10 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
                 const float fx = fmaf((float)ds[k], fs32, r.dxA) + fmaf(c.x, ux, fmaf(c.y, vx, wx));
                 const float fy = kTilt ? fmaf((float)ds[k], fsy32, dyA) + fmaf(c.x, uy, fmaf(c.y, vy, wy))
                                        : dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
-                // floor by one conversion each, the fraction by subtraction
-                const int ix = __float2int_rd(fx), ky = __float2int_rd(fy);
+                // the cell by one rounding conversion each (coordinates are
+                // centred on cells), the offset from its centre by an exact
+                // subtraction (Sterbenz)
+                const int ix = __float2int_rn(fx), ky = __float2int_rn(fy);
                 const float rx = fx - __int2float_rn(ix), ry = fy - __int2float_rn(ky);
                 Cell e;
                 bool cut;
@@ -1090,8 +1096,8 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
                     e = cell_key(z);
                 }
                 const bool in = cut && (unsigned)ix < (unsigned)txc && (unsigned)ky < (unsigned)tyc;
-                // within gc of a cell boundary: |r - 1/2| > 1/2 - gc on either axis
-                const bool amb = fmaxf(fabsf(rx - 0.5f), fabsf(ry - 0.5f)) > hg;
+                // within gc of a cell boundary: |r| > 1/2 - gc on either axis
+                const bool amb = fmaxf(fabsf(rx), fabsf(ry)) > hg;
                 const bool upd = in && !amb;
                 // FP32 maps count the FP32 cell; FP64 maps count ambiguous points when re-binned
                 cnt.cutting += F64 ? (unsigned)upd : (unsigned)in;
@@ -1191,7 +1197,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
         // x range of the visits, tile-local cells; k increases toward the
         // far end on a forward pass and toward the near end on a return pass
-        const float x_near = -((float)M + 0.5f), x_far = (float)(txc + M) + 0.5f;
+        const float x_near = -((float)M + 1.0f), x_far = (float)(txc + M);  // (centred coordinates)
         const float xk_lo = back ? x_far : x_near, xk_hi = back ? x_near : x_far;
         const float d_first = (float)(r.occ0 - sA);  // steps from the run's first item to phase 0 of its first turn
         const int f0 = r.first_off, f1 = r.first_off + r.len0;
@@ -1208,7 +1214,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             const float z = fmaf(c.x, uz, fmaf(c.y, vz, zb));
             const float px = fmaf(c.x, ux, fmaf(c.y, vx, wx));
             const float fy = dyp + fmaf(c.x, uy, fmaf(c.y, vy, wy));
-            const int ky = __float2int_rd(fy);  // floor: one conversion, the fraction by subtraction
+            const int ky = __float2int_rn(fy);  // the cell: one conversion, its centre's offset by subtraction
             const float ry = fy - __int2float_rn(ky);
             Cell e;
             bool below;
@@ -1233,20 +1239,20 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
             const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_it);
             const bool ky_in = (unsigned)ky < (unsigned)tyc;
-            const float dy = fabsf(ry - 0.5f);
+            const float dy = fabsf(ry);
             float ds = fmaf((float)k0, fS, d0);  // steps after the run's first item (an exact integer)
             for (int kk = 0; kk < n_max; kk += 2) {
                 const bool va = kk < n_it, vb = kk + 1 < n_it;
                 const float dsb = ds + fS;
                 const float fxa = fmaf(ds, fs32, r.dxA) + px;
                 const float fxb = fmaf(dsb, fs32, r.dxA) + px;
-                const int ia = __float2int_rd(fxa), ib = __float2int_rd(fxb);
+                const int ia = __float2int_rn(fxa), ib = __float2int_rn(fxb);
                 const float rxa = fxa - __int2float_rn(ia), rxb = fxb - __int2float_rn(ib);
                 cnt.evaluated += (unsigned)va + (unsigned)vb;
                 const bool in_a = va && ky_in && (unsigned)ia < (unsigned)txc;
                 const bool in_b = vb && ky_in && (unsigned)ib < (unsigned)txc;
-                const bool amb_a = fmaxf(fabsf(rxa - 0.5f), dy) > hg;  // within gc of a cell boundary
-                const bool amb_b = fmaxf(fabsf(rxb - 0.5f), dy) > hg;
+                const bool amb_a = fmaxf(fabsf(rxa), dy) > hg;  // within gc of a cell boundary
+                const bool amb_b = fmaxf(fabsf(rxb), dy) > hg;
                 const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
                 cnt.cutting += F64 ? (unsigned)upd_a + (unsigned)upd_b : (unsigned)in_a + (unsigned)in_b;
                 const int cia = ky * tile_x + ia, cib = ky * tile_x + ib;

@@ -5,7 +5,8 @@ FP32 tile-local coordinates in cells; a point within the guard band of a
 cell boundary is re-binned with the FP64 pose. The maps equal the FP64
 binning only if the band bounds the FP32 error of every point. This test
 models the sweep's FP32 arithmetic for the tile-local x and y of a pose --
-the tool rows and the pass offsets divided by the pitch in float64 and
+the tool rows and the pass offsets divided by the pitch in float64 (the
+rows' constant parts less half a cell, centring coordinates on cells) and
 rounded once, the run anchor from a float pair of the pass offset and of the
 feed per step (double-float affine step), fused multiply-adds of the rounded
 phase table and tool rows -- with each fused multiply-add rounded once
@@ -68,8 +69,9 @@ def test_guard_band_bounds_fp32_binning_error():
             dyp = Y - (c * uy + s * vy + wy)         # pass line - tile origin (y)
             # FP32 inputs as the planner stores them: x and y rows in cells
             c32, s32 = c.astype(f32), s.astype(f32)
-            ux32, vx32, wx32 = (ux / pitch).astype(f32), (vx / pitch).astype(f32), (wx / pitch).astype(f32)
-            uy32, vy32, wy32 = (uy / pitch).astype(f32), (vy / pitch).astype(f32), (wy / pitch).astype(f32)
+            # (the constant parts less half a cell: coordinates centred on cells)
+            ux32, vx32, wx32 = (ux / pitch).astype(f32), (vx / pitch).astype(f32), (wx / pitch - 0.5).astype(f32)
+            uy32, vy32, wy32 = (uy / pitch).astype(f32), (vy / pitch).astype(f32), (wy / pitch - 0.5).astype(f32)
             dc = d / pitch
             d_hi = dc.astype(f32)
             d_lo = (dc - d_hi.astype(np.float64)).astype(f32)
@@ -81,8 +83,8 @@ def test_guard_band_bounds_fp32_binning_error():
             fx = (fma32(ds.astype(f32), fs_hi, dxa) + fma32(c32, ux32, fma32(s32, vx32, wx32))).astype(f32)
             fy = ((dyp / pitch).astype(f32) + fma32(c32, uy32, fma32(s32, vy32, wy32))).astype(f32)
             # the same pose in float64 (the FP64 binning's coordinates, up to float64 rounding)
-            ex = np.abs(fx.astype(np.float64) - X / pitch)
-            ey = np.abs(fy.astype(np.float64) - Y / pitch)
+            ex = np.abs(fx.astype(np.float64) - (X / pitch - 0.5))
+            ey = np.abs(fy.astype(np.float64) - (Y / pitch - 0.5))
             # the kernel's band for the run, in cells
             pt_err = 6.0 * np.maximum(ax, ay) + 3.0 * (np.abs(wx) + np.abs(wy) + np.abs(wz)) + \
                 3.0 * max(tile_x, tile_y) * pitch
@@ -127,7 +129,7 @@ def test_guard_band_bounds_tilted_fp32_binning_error():
             dx = X - ds * fsx - (c * ux + s * vx + wx) - n_a * fsx  # pass start - tile origin
             dy = Y - ds * fsy - (c * uy + s * vy + wy) - n_a * fsy
             c32, s32 = c.astype(f32), s.astype(f32)
-            rows = [(r / pitch).astype(f32) for r in (ux, vx, wx, uy, vy, wy)]
+            rows = [(r / pitch - h).astype(f32) for r, h in ((ux, 0), (vx, 0), (wx, 0.5), (uy, 0), (vy, 0), (wy, 0.5))]
 
             def pair(v):
                 hi = v.astype(f32)
@@ -144,8 +146,8 @@ def test_guard_band_bounds_tilted_fp32_binning_error():
                   fma32(c32, rows[0], fma32(s32, rows[1], rows[2]))).astype(f32)
             fy = (fma32(ds32, (fsy / pitch).astype(f32), dya) +
                   fma32(c32, rows[3], fma32(s32, rows[4], rows[5]))).astype(f32)
-            ex = np.abs(fx.astype(np.float64) - X / pitch)
-            ey = np.abs(fy.astype(np.float64) - Y / pitch)
+            ex = np.abs(fx.astype(np.float64) - (X / pitch - 0.5))
+            ey = np.abs(fy.astype(np.float64) - (Y / pitch - 0.5))
             pt_err = 6.0 * (aa + ab) + 3.0 * (np.abs(wx) + np.abs(wy) + np.abs(wz)) + \
                 3.0 * max(tile_x, tile_y) * pitch
             g = 1.5 * U24 * (pt_err + 2.0 * span * fs) / pitch + 3.0 * U24 * max(tile_x, tile_y) + 1e-6

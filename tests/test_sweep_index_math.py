@@ -138,10 +138,11 @@ def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
     ds_k = d0 + k S steps after the run's first item, at tile-local x (cells)
     fma(ds_k, fs, dxA) + px in FP32. The kernel visits k in
     [max(kb, ceil((lo - x0) / (S fs))), min(ke, floor((hi - x0) / (S fs)))],
-    x0 = fma(d0, fs, dxA) + px, with (lo, hi) = (-(M + 1/2), txc + M + 1/2)
-    (swapped on a return pass, fs < 0), in FP32. Every revolution whose
-    FP32 x lies within the tile widened by M cells, [-M, txc + M), must be
-    visited, for both feed directions."""
+    x0 = fma(d0, fs, dxA) + px, with (lo, hi) = (-(M + 1), txc + M) (swapped
+    on a return pass, fs < 0), in FP32. Coordinates are centred on cells
+    (the cell is the nearest integer), so every revolution whose FP32 x
+    rounds into the tile widened by M cells -- x in [-M - 1/2, txc - 1 + M
+    + 1/2] -- must be visited, for both feed directions."""
     rng = np.random.default_rng(61)
     hit = 0
     for _ in range(4000):
@@ -158,7 +159,7 @@ def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
         k_mid = rng.uniform(kb, ke + 1)
         dxa = f32(rng.uniform(-M - 2, txc + M + 2) - float(px) - (float(d0) + k_mid * S) * float(fs))
         back = fs < 0
-        lo, hi = f32(-(M + 0.5)), f32(txc + M + 0.5)
+        lo, hi = f32(-(M + 1.0)), f32(txc + M)
         k_lo, k_hi = (hi, lo) if back else (lo, hi)
         inv_rev = f32(1.0) / (f32(S) * fs)
         x0 = (fma32(np.array([d0]), np.array([fs]), np.array([dxa]))[0] + px).astype(f32)
@@ -167,7 +168,7 @@ def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
         ks = np.arange(kb, ke + 1)
         ds = (f32(d0) + ks.astype(np.float64) * S).astype(f32)
         xs = (fma32(ds, np.full(ks.size, fs, f32), np.full(ks.size, dxa, f32)) + px).astype(f32).astype(np.float64)
-        over = ks[(xs >= -M) & (xs < txc + M)]
+        over = ks[(xs >= -M - 0.5) & (xs <= txc - 1 + M + 0.5)]
         hit += over.size
         ok = over.size == 0 or (over.min() >= k0 and over.max() <= k1)
         assert ok, (S, fs, float(x0), over, k0, k1)
