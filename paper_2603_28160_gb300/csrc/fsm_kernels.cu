@@ -1041,32 +1041,38 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         divmod_small(U * L, len, inv_len, &dUL, &rUL);
         divmod_small(L, len, inv_len, &dl, &rl);
         divmod_small(hl + r.first_off, len, inv_len, &q0, &o0);
-        int32_t oi[U], qi[U];
+        // chain k's next item: its phase index mn (< 2S: the table holds two
+        // turns) and its steps after the run's first item dn; both advance by
+        // U L items per iteration, the phase wrapping within the run's arc
+        int32_t mn[U], dn[U];
         float2 cn[U];  // phase-table entries of the next iteration, loaded one iteration ahead
+        {
+            int32_t o = o0, q = q0;
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            if (k == 0) {
-                oi[0] = o0;
-                qi[0] = q0;
-            } else {
-                oi[k] = oi[k - 1] + rl;
-                qi[k] = qi[k - 1] + dl;
-                if (oi[k] >= len) { oi[k] -= len; ++qi[k]; }
+            for (int k = 0; k < U; ++k) {
+                if (k > 0) {
+                    o += rl;
+                    q += dl;
+                    if (o >= len) { o -= len; ++q; }
+                }
+                mn[k] = r.m0 + o;
+                dn[k] = hl + k * L + q * gap;
+                cn[k] = __ldg(ph32 + mn[k]);
             }
-            cn[k] = __ldg(ph32 + r.m0 + oi[k]);
         }
+        const int32_t m_end = r.m0 + len, dn_step = U * L + dUL * gap;
         for (int base = 0; base < tmax; base += U * L) {
             int32_t ds[U], mi[U];
             float2 cs[U];
 #pragma unroll
             for (int k = 0; k < U; ++k) {
-                ds[k] = base + hl + k * L + qi[k] * gap;  // steps after the run's first item
-                mi[k] = r.m0 + oi[k];                      // < 2S: the table holds two turns
+                ds[k] = dn[k];
+                mi[k] = mn[k];
                 cs[k] = cn[k];
-                oi[k] += rUL;
-                qi[k] += dUL;
-                if (oi[k] >= len) { oi[k] -= len; ++qi[k]; }
-                cn[k] = __ldg(ph32 + r.m0 + oi[k]);
+                mn[k] += rUL;
+                dn[k] += dn_step;
+                if (mn[k] >= m_end) { mn[k] -= len; dn[k] += gap; }
+                cn[k] = __ldg(ph32 + mn[k]);
             }
             bool push_any = false;
             bool pk[U];

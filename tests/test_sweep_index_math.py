@@ -61,35 +61,47 @@ def divmod_small(v, ln, inv_len):
     return d, v - d * ln
 
 
-def item_walk(r, m0, ln, S):
-    """Steps and phases the item form visits, by item index."""
+def item_walk(r, m0, ln, S, U=2):
+    """Steps and phases the item form visits, by item index: lane hl's U
+    chains start at items hl, hl + L, ... (revolution q and phase offset o
+    from one division each), then carry their phase index mn (m0 + o, below
+    2S: the table holds two turns) and their steps after the run's first item
+    dn, both advanced by U L items per iteration, the phase wrapping within
+    the run's arc (and adding the arc's gap to the steps)."""
     inv_len = f32(1.0) / f32(ln)
     gap = S - ln
     s_a = r["occ0"] + r["first_off"]
-    d2l, r2l = divmod_small(2 * L, ln, inv_len)
+    dul, rul = divmod_small(U * L, ln, inv_len)
     dl, rl = divmod_small(L, ln, inv_len)
     out = {}
     tot = r["total"]
+    m_end, dn_step = m0 + ln, U * L + dul * gap
     for hl in range(L):
-        qa, oa = divmod_small(hl + r["first_off"], ln, inv_len)
+        q, o = divmod_small(hl + r["first_off"], ln, inv_len)
+        mn, dn = [], []
+        for k in range(U):
+            if k > 0:
+                o += rl
+                q += dl
+                if o >= ln:
+                    o -= ln
+                    q += 1
+            mn.append(m0 + o)
+            dn.append(hl + k * L + q * gap)
         base = 0
         while base < tot:
-            ta, tb = base + hl, base + hl + L
-            ob, qb = oa + rl, qa + dl
-            if ob >= ln:
-                ob -= ln
-                qb += 1
-            for t, q, o in ((ta, qa, oa), (tb, qb, ob)):
+            for k in range(U):
+                t = base + hl + k * L
+                assert mn[k] < 2 * S
                 if t < tot:
-                    m = m0 + o
-                    m = m - S if m >= S else m
-                    out[t] = (s_a + t + q * gap, m)
-            oa += r2l
-            qa += d2l
-            if oa >= ln:
-                oa -= ln
-                qa += 1
-            base += 2 * L
+                    m = mn[k] - S if mn[k] >= S else mn[k]
+                    out[t] = (s_a + dn[k], m)
+                mn[k] += rul
+                dn[k] += dn_step
+                if mn[k] >= m_end:
+                    mn[k] -= ln
+                    dn[k] += gap
+            base += U * L
     return out
 
 
@@ -119,10 +131,11 @@ def test_run_items_and_phases_match_brute_force():
             assert not brute
             continue
         assert r["total"] == len(brute)
-        items = item_walk(r, m0, ln, S)
-        assert sorted(items) == list(range(r["total"]))
-        assert [items[t][0] for t in range(r["total"])] == brute      # item t is the t-th step of the run
-        assert all(m == s % S for s, m in items.values())             # and its phase index
+        for U in (2, 3):
+            items = item_walk(r, m0, ln, S, U)
+            assert sorted(items) == list(range(r["total"]))
+            assert [items[t][0] for t in range(r["total"])] == brute  # item t is the t-th step of the run
+            assert all(m == s % S for s, m in items.values())         # and its phase index
         assert phase_walk(r, ln, S) == brute
         checked += len(brute)
     assert checked > 10**6
