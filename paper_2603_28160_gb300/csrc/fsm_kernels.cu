@@ -431,6 +431,7 @@ struct TileShared {
     float dy[kPassCache];                     // pass line - tile origin y, in cells (tilted: pass start y, hi)
     float dy_lo[kPassCache];                  // tilted: pass start y - tile origin y, lo part (cells)
     float dxp_hi[kPassCache], dxp_lo[kPassCache];  // tilted: pass start x - tile origin x (cells)
+    uint8_t order[kPassCache];                // passes nearest the tile first (tasks are handed out in this order)
     float dx_hi, dx_lo;  // pass_x0 - tile origin x in cells, as a float pair
     float xlo, xhi;      // tile x extent relative to pass_x0, margins included (tilted: along the feed)
     float zhi;           // stock - z_ref + margin
@@ -1349,6 +1350,23 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cells[c] = init;
         fill_tile_shared<kTilt>(sf, tc, ts);
         __syncthreads();
+        // Task order: the passes whose line runs nearest the tile's centre
+        // (|centre of the y band|, relative to the pass line) first -- their
+        // tasks carry the most runs, so the warps' last tasks are short ones
+        // and the wait at the end of the tile shrinks. Passes beyond the
+        // cached ones keep their index order.
+        const int n_cached = min(sf.n_passes, kPassCache);
+        if (threadIdx.x < n_cached) {
+            const int q = threadIdx.x;
+            const float dq = fabsf(ts.ylo[q] + ts.yhi[q]);
+            int rank = 0;
+            for (int o = 0; o < n_cached; ++o) {
+                const float d = fabsf(ts.ylo[o] + ts.yhi[o]);
+                rank += (d < dq || (d == dq && o < q)) ? 1 : 0;
+            }
+            ts.order[rank] = (uint8_t)q;
+        }
+        __syncthreads();
 
         const int G = (sf.E + 31) / 32;
         const int n_tasks = sf.n_passes * sf.n_teeth * G;
@@ -1360,8 +1378,9 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             const int t = w0 + lane;
             bool ok = false;
             if (t < n_bits) {
-                const int p = t / (sf.n_teeth * G);
-                const int rem = t - p * sf.n_teeth * G;
+                const int pi = t / (sf.n_teeth * G);
+                const int rem = t - pi * sf.n_teeth * G;
+                const int p = pi < kPassCache ? (int)ts.order[pi] : pi;
                 PassFrame pf;
                 pass_band<kTilt>(sf, tc, ts, p, pf);
                 const float4 gb = sf.groups[rem];  // rem = K * G + g
@@ -1383,8 +1402,9 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             if (lane == 0) task = atomicAdd(&s_task, 1);
             task = __shfl_sync(0xffffffffu, task, 0);
             if (task >= n_tasks) break;
-            const int p = task / (sf.n_teeth * G);
-            const int rem = task - p * sf.n_teeth * G;
+            const int pi = task / (sf.n_teeth * G);
+            const int rem = task - pi * sf.n_teeth * G;
+            const int p = pi < kPassCache ? (int)ts.order[pi] : pi;
             const int K = rem / G, g = rem - K * G;
             if (task < kTaskBits && !((ts.accept[task >> 5] >> (task & 31)) & 1u)) continue;  // warp-uniform
             PassFrame pf;
