@@ -427,6 +427,7 @@ constexpr int kTaskBits = 4096;
 
 struct TileShared {
     uint32_t accept[kTaskBits / 32];          // task t may have runs here (group reject passed)
+    uint16_t acc_pre[kTaskBits / 32 + 1];     // accepted tasks in the words before word w
     float ylo[kPassCache], yhi[kPassCache];  // mm, for the enumeration (tilted: across the feed)
     float dy[kPassCache];                     // pass line - tile origin y, in cells (tilted: pass start y, hi)
     float dy_lo[kPassCache];                  // tilted: pass start y - tile origin y, lo part (cells)
@@ -1289,6 +1290,25 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
     drain_queues<F64>(sf, tc, ws, aq, p, an, qn, cnt);
 }
 
+// Position of the n-th set bit (0-based) of x, for n < popc(x): halve the
+// word five times, keeping the half that holds it.
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const uint32_t low = (1u << sh) - 1u;
+        const int c = __popc(x & low);
+        if (n >= c) {
+            n -= c;
+            x >>= sh;
+            pos += sh;
+        } else {
+            x &= low;
+        }
+    }
+    return pos;
+}
+
 __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1390,6 +1410,35 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             if (lane == 0) ts.accept[w0 >> 5] = bits;
         }
         __syncthreads();
+        // prefix counts of the accept words (warp 0; at most 128 words, four
+        // per lane): the accepted tasks are handed out by rank, so no warp
+        // takes a rejected one
+        const int n_words = (n_bits + 31) >> 5;
+        if (warp == 0) {
+            int c[4], sum = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int w = lane * 4 + k;
+                c[k] = w < n_words ? __popc(ts.accept[w]) : 0;
+                sum += c[k];
+            }
+            int incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int run = incl - sum;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int w = lane * 4 + k;
+                if (w < n_words) ts.acc_pre[w] = (uint16_t)run;
+                run += c[k];
+            }
+            if (lane == 31) ts.acc_pre[n_words] = (uint16_t)incl;
+        }
+        __syncthreads();
+        const int n_acc = ts.acc_pre[n_words];
+        const float inv_ng = 1.0f / (float)(sf.n_teeth * G), inv_g = 1.0f / (float)G;
         const double tile_x1 = tc.X0 + (double)tc.txc * sf.pitch;
         const double pass_x1 = sf.pass_x0 + (double)(sf.steps_per_pass - 1) * sf.fs;
         bool x_miss = (pass_x1 + sf.reach_x < tc.X0 - 1e-3) || (sf.pass_x0 - sf.reach_x > tile_x1 + 1e-3);
@@ -1398,15 +1447,38 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
             x_miss = ((double)ts.xlo > len + sf.reach_x + 1e-3) || ((double)ts.xhi < -sf.reach_x - 1e-3);
         }
         while (!x_miss) {
-            int task = 0;
-            if (lane == 0) task = atomicAdd(&s_task, 1);
-            task = __shfl_sync(0xffffffffu, task, 0);
-            if (task >= n_tasks) break;
-            const int pi = task / (sf.n_teeth * G);
-            const int rem = task - pi * sf.n_teeth * G;
+            int r = 0;
+            if (lane == 0) r = atomicAdd(&s_task, 1);
+            r = __shfl_sync(0xffffffffu, r, 0);
+            int task;
+            if (r < n_acc) {  // the r-th accepted task: its word, then its bit
+                bool hit = false;
+                int wl = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int w = lane * 4 + k;
+                    if (w < n_words && (int)ts.acc_pre[w] <= r && r < (int)ts.acc_pre[w + 1]) {
+                        hit = true;
+                        wl = w;
+                    }
+                }
+                const unsigned who = __ballot_sync(0xffffffffu, hit);
+                if (who == 0u) break;  // (not reached: the prefix counts cover every rank below n_acc)
+                const int w = __shfl_sync(0xffffffffu, wl, __ffs(who) - 1);
+                task = w * 32 + nth_set_bit(ts.accept[w], r - (int)ts.acc_pre[w]);
+            } else {  // tasks beyond the tabulated ones, tested as they are taken
+                task = n_bits + (r - n_acc);
+                if (task >= n_tasks) break;
+            }
+            int pi, rem, K, g;  // task = (pi N + K) G + g; float-reciprocal divisions (exact below 2^24)
+            if (task < (1 << 24)) {
+                divmod_small(task, sf.n_teeth * G, inv_ng, &pi, &rem);
+            } else {
+                pi = task / (sf.n_teeth * G);
+                rem = task - pi * sf.n_teeth * G;
+            }
+            divmod_small(rem, G, inv_g, &K, &g);  // rem < N G <= 2^21
             const int p = pi < kPassCache ? (int)ts.order[pi] : pi;
-            const int K = rem / G, g = rem - K * G;
-            if (task < kTaskBits && !((ts.accept[task >> 5] >> (task & 31)) & 1u)) continue;  // warp-uniform
             PassFrame pf;
             pass_band<kTilt>(sf, tc, ts, p, pf);
             if (task >= kTaskBits) {
