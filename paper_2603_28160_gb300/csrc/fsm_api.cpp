@@ -126,20 +126,20 @@ static int feed_aligned_width(const fsm_process_desc& p, int n_teeth) {
 Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm_process_desc* const* group,
                  int n_group, int sm_count, const fsm_tool_desc* const* tools) {
     // Default ladder, measured on GB300: 16 warps sharing one large, wide
-    // tile amortise the per-tile enumeration best (5x5 mm, 1 um ball raster:
-    // FP32 512x56 1.38 ms vs 512x48 1.43 ms and, earlier, 512x48 1.62 ms vs
-    // 256x48 with 8 warps 2.19 ms; FP64 640x27 3.07 ms vs 512x32 3.34 ms vs
-    // 256x64 4.55 ms; 8 mm flat-end floor FP32 512x56 30.8 ms vs 512x48
-    // 32.5 ms, FP64 640x27 37.1 ms vs 512x32 37.7 ms; FP64 side wall 640x27
-    // 2.89 ms vs 512x32 3.53 ms), while wide, short tiles keep per-arc x
-    // ranges tight. 512x56 FP32 cells (112 KB) and 640x27 FP64 cells (135 KB)
-    // nearly fill the shared memory beside the 16 warps' scratch. A step
-    // down is taken while the surfaces have fewer tiles than there are
+    // tile amortise the per-tile work best, and the tile takes all the
+    // shared memory the 16 warps' scratch leaves: 512x76 FP32 cells
+    // (152 KB) and 640x34 FP64 cells (170 KB). Measured on the 5x5 mm, 1 um
+    // ball raster in feed-aligned widths: FP32 636x61 0.985 ms vs 636x45
+    // 1.06 ms, 636x36 1.18 ms; FP64 632x34 2.09 ms vs 632x27 2.32 ms; more
+    // warps on smaller tiles were slower (20 warps, 636x36: 1.31 ms), fewer
+    // warps on larger ones too (12 warps, 636x57: 1.12 ms). Wide, short
+    // tiles keep per-arc x ranges tight. A step down to 8-warp CTAs, two
+    // per SM, is taken while the surfaces have fewer tiles than there are
     // resident CTAs (small maps: the 2 Mcell face-milled patch runs 0.33 ms
     // at 128x32 against 0.99 ms at 512x48).
     struct Level { int tx, ty, threads, ctas; };
-    static const Level l32[] = {{512, 56, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
-    static const Level l64[] = {{640, 27, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
+    static const Level l32[] = {{512, 76, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
+    static const Level l64[] = {{640, 34, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
     const Level* lv = p.precision == FSM_FP64 ? l64 : l32;
     int pick = 0;
     if (group && n_group > 0 && sm_count > 0) {
@@ -633,10 +633,10 @@ extern "C" fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm
     cudaStream_t st = (cudaStream_t)stream;
     // candidates (tile_x, tile_y, threads): wide, short tiles shared by many
     // warps first (they amortise the enumeration and keep x ranges tight)
-    static const int c32[][3] = {{512, 56, 512}, {640, 44, 512}, {512, 48, 512}, {576, 48, 512}, {512, 24, 256},
-                                 {384, 64, 512}, {768, 32, 512}, {256, 96, 512}, {256, 48, 256}, {256, 64, 256},
+    static const int c32[][3] = {{512, 76, 512}, {640, 60, 512}, {768, 50, 512}, {1024, 38, 512}, {384, 100, 512},
+                                 {512, 56, 512}, {256, 150, 512}, {512, 24, 256}, {256, 48, 256}, {256, 64, 256},
                                  {128, 48, 256}, {128, 32, 256}, {64, 32, 256}};
-    static const int c64[][3] = {{512, 32, 512}, {640, 27, 512}, {576, 30, 512}, {256, 64, 512}, {512, 24, 384},
+    static const int c64[][3] = {{640, 34, 512}, {512, 42, 512}, {768, 28, 512}, {256, 84, 512}, {512, 24, 384},
                                  {256, 32, 256}, {128, 64, 256}, {128, 32, 256}, {64, 64, 256}, {64, 32, 256}};
     const bool f64 = proc->d.precision == FSM_FP64;
     const int nlist = f64 ? 10 : 13;

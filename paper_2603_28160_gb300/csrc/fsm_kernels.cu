@@ -411,11 +411,17 @@ __device__ __forceinline__ bool phase_form_task(int items, int phases) {
 }
 
 // One warp's scratch: runs of 32 edge points and the FP64 re-binning queue.
+// A point has up to kMaxArcs runs but rarely more than one (0.8 on
+// average on the ball raster), so each lane keeps kRunSlots of them per
+// round: a task whose points have more is walked in further rounds, each
+// re-enumerating and keeping the next slots. The shared memory saved goes
+// to the tile.
+constexpr int kRunSlots = 2;
 struct WarpScratch {
-    RunRec run[32][kMaxArcs];
+    RunRec run[32][kRunSlots];
     int32_t n[32];
     int32_t q_s[kRebinCap], q_m[kRebinCap], q_idx[kRebinCap];
-    uint8_t flat[32 * kMaxArcs];  // run list of the task: (point << 2) | arc
+    uint8_t flat[32 * kRunSlots];  // run list of the round: (point << 1) | slot
 };
 
 constexpr int kPassCache = 64;
@@ -593,17 +599,21 @@ __device__ __forceinline__ void pass_band(const Surface& sf, const TileCtx<Cell>
 }
 
 // Phase 1 of a warp task: lane = edge point j = 32 g + lane of tooth K. Each
-// lane enumerates its runs for pass p and stores them with their iteration
-// bookkeeping, its FP32 anchor and guard band. t4 and zb (the FP32 height
-// base z_ref - stock + w_z) stay in the lane's registers for phase 2.
-// Returns whether any lane has work.
+// lane enumerates its runs for pass p and stores those of round `round`
+// (its runs kRunSlots round .. kRunSlots (round + 1) - 1) with their
+// iteration bookkeeping, FP32 anchor and guard band. t4 and zb (the FP32
+// height base z_ref - stock + w_z) stay in the lane's registers for phase 2.
+// Returns whether any lane has work this round; *more: some lane has runs
+// beyond it.
 template <bool kTilt>
 __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& ts, const PassFrame& pf, int K,
-                                          int g, int p, WarpScratch& ws, float4 (&t4)[3], float& zb) {
+                                          int g, int p, WarpScratch& ws, float4 (&t4)[3], float& zb, int round,
+                                          bool* more, int* items, int* phases) {
     const int lane = threadIdx.x & 31;
     const int E = sf.E;
     const int j = g * 32 + lane;
-    int nr = 0;
+    const int v0 = kRunSlots * round;  // this round's first run index
+    int nr = 0, nv = 0;                 // runs kept this round, valid runs of the point
     t4[0] = t4[1] = t4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     zb = 0.f;
     if (j < E) {
@@ -652,6 +662,10 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         for (int a = 0; a < n; ++a) {
             const RunIter it = run_iter(runs[a], sf.S);
             if (it.total <= 0) continue;
+            const int v = nv++;
+            *items += it.total;  // (all of the point's runs, whichever round keeps them)
+            *phases += runs[a].len;
+            if (v < v0 || v >= v0 + kRunSlots) continue;
             RunRec& r = ws.run[lane][nr++];
             r.m0 = runs[a].m0;
             r.len = runs[a].len;
@@ -677,8 +691,9 @@ __device__ __forceinline__ bool warp_runs(const Surface& sf, const TileShared& t
         const int v = __shfl_up_sync(0xffffffffu, pre, o);
         if (lane >= o) pre += v;
     }
-    for (int a = 0; a < nr; ++a) ws.flat[pre - nr + a] = (uint8_t)((lane << 2) | a);
+    for (int a = 0; a < nr; ++a) ws.flat[pre - nr + a] = (uint8_t)((lane << 1) | a);
     __syncwarp();
+    *more = __any_sync(0xffffffffu, nv > v0 + kRunSlots);
     return __any_sync(0xffffffffu, nr > 0);
 }
 
@@ -1000,7 +1015,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         const int ri = q + grp;
         const bool has = ri < R;
         const int code = has ? (int)ws.flat[ri] : 0;
-        const int o = code >> 2, a = code & 3;
+        const int o = code >> 1, a = code & 1;
         RunRec r = ws.run[o][a];
         if (!has) {  // a well-formed empty run: its (unused) item indices stay at phase 0
             r.m0 = 0; r.len = 1; r.occ0 = 0; r.first_off = 0; r.len0 = 1; r.k_last = 0; r.len_last = 0;
@@ -1176,7 +1191,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         const int ri = q + grp;
         const bool has = ri < R;
         const int code = has ? (int)ws.flat[ri] : 0;
-        const int o = code >> 2, a = code & 3;
+        const int o = code >> 1, a = code & 1;
         RunRec r = ws.run[o][a];
         if (!has) {  // a well-formed empty run (no offsets; its fields stay in range)
             r.m0 = 0; r.len = 0; r.occ0 = 0; r.first_off = 0; r.len0 = 0; r.k_last = 0; r.len_last = 0;
@@ -1485,37 +1500,41 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                 const float4 gb = sf.groups[K * G + g];
                 if (gb.y < pf.ylo || gb.x > pf.yhi || gb.z >= ts.zhi) continue;  // warp-uniform
             }
-            float4 t4[3];
-            float zb;
-            if (!warp_runs<kTilt>(sf, ts, pf, K, g, p, ws, t4, zb)) continue;
             AmbQueue* aq = FP64 ? nullptr : aqs + warp;
-            // runs that come back for many revolutions share their per-phase
-            // work (phase form); others are walked item by item
             bool by_phase = false;
-            if constexpr (kPhases) {
-                if (sf.form == FSM_FORM_PHASE) {
-                    by_phase = true;
-                } else if (sf.form != FSM_FORM_ITEM) {
-                    int tot = 0, phases = 0;
-                    for (int a = 0; a < ws.n[lane]; ++a) {
-                        tot += rec_total(ws.run[lane][a]);
-                        phases += ws.run[lane][a].len;
+            for (int round = 0;; ++round) {  // (a second round is rare: points with more than kRunSlots runs)
+                float4 t4[3];
+                float zb;
+                bool more = false;
+                int items = 0, phases = 0;
+                const bool any = warp_runs<kTilt>(sf, ts, pf, K, g, p, ws, t4, zb, round, &more, &items, &phases);
+                if (any) {
+                    if (round == 0) {
+                        // runs that come back for many revolutions share their
+                        // per-phase work (phase form); others are walked item by item
+                        if constexpr (kPhases) {
+                            if (sf.form == FSM_FORM_PHASE) {
+                                by_phase = true;
+                            } else if (sf.form != FSM_FORM_ITEM) {
+                                for (int o = 16; o > 0; o >>= 1) {
+                                    items += __shfl_xor_sync(0xffffffffu, items, o);
+                                    phases += __shfl_xor_sync(0xffffffffu, phases, o);
+                                }
+                                by_phase = phase_form_task<FP64>(items, phases);
+                            }
+                        }
+                        if (sf.form_tasks && lane == 0) atomicAdd(sf.form_tasks + (by_phase ? 1 : 0), 1ull);
                     }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                        phases += __shfl_xor_sync(0xffffffffu, phases, o);
-                    }
-                    by_phase = phase_form_task<FP64>(tot, phases);
+                    if (by_phase)
+                        sweep_phases<FP64>(sf, tc, pf.dy, K, g, p, ws, aq, t4, zb, cnt);
+                    else if (kTilt && sf.tilted)
+                        sweep_items<FP64, kItemChains, kTilt>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
+                    else
+                        sweep_items<FP64>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
+                    __syncwarp();
                 }
+                if (!more) break;
             }
-            if (sf.form_tasks && lane == 0) atomicAdd(sf.form_tasks + (by_phase ? 1 : 0), 1ull);
-            if (by_phase)
-                sweep_phases<FP64>(sf, tc, pf.dy, K, g, p, ws, aq, t4, zb, cnt);
-            else if (kTilt && sf.tilted)
-                sweep_items<FP64, kItemChains, kTilt>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
-            else
-                sweep_items<FP64>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
-            __syncwarp();
         }
         __syncthreads();
 
