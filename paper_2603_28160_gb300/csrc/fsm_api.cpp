@@ -109,18 +109,23 @@ static fsm_status check_process(const fsm_process_desc* p) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Tile width for a surface whose feed per revolution spans rev_cells cells:
-// a whole number k of revolutions (k near 480 / rev) less the visits'
-// margins (two cells and a half each side), so that every spindle phase
-// brings a point over the tile on the same number k of revolutions -- the
-// phase form's visit count is then the same on nearly every lane. 0 when
-// the feed per revolution is too long for tiles of at most 720 cells.
+// Tile width for a surface whose feed per revolution spans rev cells: a
+// whole number k of revolutions, less the visits' margins (two cells each
+// side), so that every spindle phase brings a point over the tile on the
+// same number k of revolutions -- the phase form's visit count is then the
+// same on nearly every lane. k is near target / rev: 480 cells, or 1280 for
+// FP64 floors, whose phase form computes the FP64 height once per phase and
+// gains from more revolutions per tile (measured, 5 mm ball raster FP64:
+// 1276x17 1.91 ms vs 636x34 2.09 ms; 8 mm flat floor FP64 1296x16 28.6 ms vs
+// 468x46 28.9 ms; the FP64 wall is fastest at 468x46). 0 when the feed per
+// revolution is too long for the widths allowed (64 .. 1.5 target).
 static int feed_aligned_width(const fsm_process_desc& p, int n_teeth) {
+    const double target = (p.precision == FSM_FP64 && p.surface == FSM_SURFACE_FLOOR) ? 1280.0 : 480.0;
     const double rev = (double)n_teeth * p.fz / p.pitch;
-    if (!(rev > 0.0) || rev > 720.0) return 0;
-    const int k = std::max(1, (int)llround(480.0 / rev));
+    if (!(rev > 0.0) || rev > 1.5 * target) return 0;
+    const int k = std::max(1, (int)llround(target / rev));
     const int w = ((int)floor((double)k * rev) - 4) & ~3;
-    return (w >= 64 && w <= 720) ? w : 0;
+    return (w >= 64 && w <= (int)(1.5 * target)) ? w : 0;
 }
 
 Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm_process_desc* const* group,
@@ -135,8 +140,10 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
     // warps on larger ones too (12 warps, 636x57: 1.12 ms). Wide, short
     // tiles keep per-arc x ranges tight. A step down to 8-warp CTAs, two
     // per SM, is taken while the surfaces have fewer tiles than there are
-    // resident CTAs (small maps: the 2 Mcell face-milled patch runs 0.33 ms
-    // at 128x32 against 0.99 ms at 512x48).
+    // resident CTAs by more than half (small maps: the 2 Mcell face-milled
+    // patch runs 0.33 ms at 128x32 against 0.99 ms at 512x48; the 20x1 mm
+    // wall's 140 tiles of 468x83 fill 152 SMs well: 0.63 ms against 6.3 ms
+    // at 256x48).
     struct Level { int tx, ty, threads, ctas; };
     static const Level l32[] = {{512, 76, 512, 1}, {256, 48, 256, 2}, {128, 32, 256, 2}};
     static const Level l64[] = {{640, 34, 512, 1}, {256, 32, 256, 2}, {128, 32, 256, 2}};
@@ -149,7 +156,7 @@ Shape pick_shape(const fsm_process_desc& p, const fsm_predict_opts* o, const fsm
                 if (group[i]->precision == p.precision)
                     tiles += (long long)((group[i]->nx + lv[pick].tx - 1) / lv[pick].tx) *
                              ((group[i]->ny + lv[pick].ty - 1) / lv[pick].ty);
-            if (tiles >= (long long)sm_count * lv[pick].ctas) break;
+            if (2 * tiles >= (long long)sm_count * lv[pick].ctas) break;
         }
     }
     Shape s;

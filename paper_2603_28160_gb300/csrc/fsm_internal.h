@@ -35,10 +35,11 @@ inline bool feed_tilted(const fsm_process_desc& p) { return fmod(p.feed_dir_deg,
 
 // Whether the sweep is launched in the instantiation that chooses between
 // the item and the phase form per task (otherwise every task takes the item
-// form). FP32 maps: when a tile is three or more feeds per revolution wide,
-// so that the runs of one tile come back for several revolutions (measured
-// on GB300: the ball raster, under one feed per tile, is faster item by
-// item; the side wall and the flat-end floor, at two to four, by phase).
+// form). FP32 maps: when a tile is at least one and a half feeds per
+// revolution wide, so that the runs of one tile come back for more than one
+// revolution (measured on GB300 with 16 warps on 152 KB tiles: the ball
+// raster at two feeds per tile 0.967 ms against 0.983 ms item by item; the
+// side wall and the flat-end floor, at two to four, are faster by phase).
 // FP64 maps always: their FP64 height is computed once per phase in the
 // phase form, and the per-task choice keeps runs of few revolutions item by
 // item (ball raster FP64 4.55 -> 3.57 ms with 512x32 tiles, 8 mm floor
@@ -49,7 +50,7 @@ inline bool phase_form_pays(const fsm_tool_desc& t, const fsm_process_desc& p, i
     if (form == FSM_FORM_ITEM) return false;
     if (p.precision == FSM_FP64) return true;
     const double feeds = (double)tile_x * p.pitch / ((double)t.n_teeth * p.fz);
-    return feeds >= 3.0;
+    return feeds >= 1.5;
 }
 
 // Trajectory map of one planned surface: argmin table d_jmin (S * n_teeth

@@ -401,13 +401,14 @@ __device__ __forceinline__ int32_t rec_total(const RunRec& r) {
 
 constexpr int kRebinCap = 64;
 // Mean revolutions per run phase from which a task takes the phase form of
-// phase 2, as a fraction num/den: 3 for FP32 maps (measured: the ball raster
-// averages 1.7 and is fastest item by item; floors and walls come back 4-20
-// times); 1.2 for FP64 maps, where the phase form also computes the FP64
-// height once per phase instead of once per item.
+// phase 2: 1.5 for FP32 maps (measured on the ball raster, ~1.7 on its
+// feed-aligned tiles: 0.967 ms against 0.983 ms with a threshold of 3, which
+// kept it item by item; floors and walls come back 4-20 times); 1.2 for
+// FP64 maps, where the phase form also computes the FP64 height once per
+// phase instead of once per item.
 template <bool F64>
 __device__ __forceinline__ bool phase_form_task(int items, int phases) {
-    return F64 ? 5 * items >= 6 * phases : items >= 3 * phases;
+    return F64 ? 5 * items >= 6 * phases : 2 * items >= 3 * phases;
 }
 
 // One warp's scratch: runs of 32 edge points and the FP64 re-binning queue.
