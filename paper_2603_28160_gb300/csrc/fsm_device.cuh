@@ -33,7 +33,7 @@ namespace fsm {
 constexpr int kMaxTeeth = 16;
 constexpr int kMaxArcs = 4;        // per edge point and pass after merging
 constexpr float kMarginMm = 2e-5f; // enumeration slack in x, y, z (20 nm)
-constexpr int kPlanParts = 64;     // max planning blocks per surface
+constexpr int kPlanParts = 256;    // max planning blocks per surface
 
 // Per-surface plan. The host fills the inputs and table pointers; the plan
 // kernel fills the derived block and the tables.

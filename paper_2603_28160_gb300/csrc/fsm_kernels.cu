@@ -264,15 +264,21 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
     Surface* sf = surfs + sidx;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int N = sf->n_teeth, E = sf->E, S = sf->S;
+    // the planning blocks' partials, reduced by the whole block (maxima as
+    // minima of the negated values); cached tables keep the reduction of the
+    // launch that built them in part 0
+    __shared__ double shd[32];
+    const int np = sf->cached ? 1 : parts;
+    double zlo = 1e300, nrx = 0.0, nry = 0.0;
+    for (int q = tid; q < np; q += blockDim.x) {
+        zlo = fmin(zlo, sf->plan_part[4 * q]);
+        nrx = fmin(nrx, -sf->plan_part[4 * q + 1]);
+        nry = fmin(nry, -sf->plan_part[4 * q + 2]);
+    }
+    zlo = block_min_d(zlo, shd);
+    const double rx = -block_min_d(nrx, shd), ry = -block_min_d(nry, shd);
     if (tid == 0) {
         if (sf->tile_queue) *sf->tile_queue = 0;
-        // cached tables keep the reduction of the launch that built them in part 0
-        double zlo = 1e300, rx = 0.0, ry = 0.0;
-        for (int q = 0; q < (sf->cached ? 1 : parts); ++q) {
-            zlo = fmin(zlo, sf->plan_part[4 * q]);
-            rx = fmax(rx, sf->plan_part[4 * q + 1]);
-            ry = fmax(ry, sf->plan_part[4 * q + 2]);
-        }
         if (!sf->cached) {
             sf->plan_part[0] = zlo;
             sf->plan_part[1] = rx;
@@ -2460,15 +2466,19 @@ cudaError_t launch_plan(Surface* d_surfs, int n, const Surface* one, int max_wor
     Surface dummy;
     if (one) dummy = *one;
     else memset(&dummy, 0, sizeof dummy);
-    // the FP64 tables (edge points and the phase table: tens of thousands of
-    // phases at fine time steps) are spread over several blocks per surface
-    // as long as the grid stays within ~8 blocks per SM; large batches give
-    // each surface one block
+    // The FP64 tables (edge points, and the phase table: tens of thousands
+    // of phases at fine time steps) are built with FP64 transcendentals on
+    // GB300's 1/64-rate FP64 pipe, so a surface's work is spread over as many
+    // SMs as it fills: small blocks of 64 threads, about one item each, while
+    // the grid stays within ~16 blocks per SM; large batches give each
+    // surface one block (the 5 mm ball raster: 107 blocks, 34 us against
+    // 39 us for 27 blocks of 256).
+    constexpr int kPlanThreads = 64;
     if (one) max_work = one->n_teeth * one->E + one->S;
-    const int want = max(1, min(kPlanParts, (max_work + 255) / 256));
-    const int fit = max(1, 8 * max(sm_count, 1) / max(n, 1));
+    const int want = max(1, min(kPlanParts, (max_work + kPlanThreads - 1) / kPlanThreads));
+    const int fit = max(1, 16 * max(sm_count, 1) / max(n, 1));
     const int parts = one ? want : min(want, fit);
-    plan_kernel<<<dim3(n, parts), 256, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
+    plan_kernel<<<dim3(n, parts), kPlanThreads, 0, st>>>(d_surfs, n, dummy, one ? 1 : 0);
     plan_finish_kernel<<<n, 256, 0, st>>>(d_surfs, n, parts);
     return cudaGetLastError();
 }
