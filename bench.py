@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--batch-size", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="seconds of arrivals per served rate")
-    ap.add_argument("--serve-rates", default="40,80,160,320",
+    ap.add_argument("--serve-rates", default="40,80,160,320,640,960",
                     help="Poisson arrival rates (requests/s) of the served leg, comma separated")
     ap.add_argument("--serve-setups", type=int, default=64,
                     help="served requests draw tool and set-up from a catalogue of this many (0: all distinct)")
