@@ -118,9 +118,10 @@ typedef struct {
  *   precision FSM_FP64 (double heights: the FP64 height of every point and
  *   the cell its FP64 pose falls in, i.e. the map of an all-FP64 sweep; the
  *   cell is decided from FP32 tile-local coordinates where an error bound
- *   proves it, else from the FP64 pose) or FSM_FP32 (float heights; edge
- *   poses in FP32 tile-local coordinates, FP64 for the spindle phase, the
- *   path position and near-boundary re-binning).
+ *   proves it, else from the FP64 pose) or FSM_FP32 (float heights: the
+ *   FP32 height of every point in the cell its FP64 pose falls in, decided
+ *   the same way; FP64 for the spindle phase, the path position and
+ *   near-boundary re-binning). Neither map depends on the launch shape.
  *   surface FSM_SURFACE_FLOOR: the map covers x (columns) and y (rows) from
  *   (x0, y0), height z, un-machined at stock_z. FSM_SURFACE_WALL (an
  *   extension; the paper maps floors only): the side wall the flank leaves
@@ -315,14 +316,14 @@ fsm_status fsm_trajectory_records(const fsm_tool* tool, const fsm_process* proc,
  * shape (precision, tool kind, teeth, edge points, steps per revolution,
  * grid size and pitch) and no tile override use it. Synchronises the stream.
  * The map contents afterwards are those of the last candidate run (all
- * candidates compute the same map; FP32 maps may differ in the last
- * rounding between tile shapes). */
+ * candidates compute the same map, bit for bit, in either precision). */
 fsm_status fsm_autotune(fsm_ctx* ctx, const fsm_tool* tool, const fsm_process* proc, void* d_heights,
                         int32_t max_candidates, fsm_predict_opts* best, float* best_ms, void* stream);
 
 /* Roughness of a device height map (FSM_FP64 doubles or FSM_FP32 floats),
- * computed on the device in FP64 with a fixed reduction order (results do not
- * depend on launch timing). Writes one fsm_roughness_out to DEVICE memory
+ * computed on the device to FP64 accuracy (double-float sums on the FP32
+ * pipes; each deviation of an FP64 map formed in FP64) with a fixed
+ * reduction order (results do not depend on launch timing). Writes one fsm_roughness_out to DEVICE memory
  * d_out (caller-owned). 0 <= n_rows, n_cols <= 16. Asynchronous. */
 fsm_status fsm_roughness(fsm_ctx* ctx, const void* d_heights, int32_t precision, int32_t nx,
                          int32_t ny, int32_t n_rows, int32_t n_cols, fsm_roughness_out* d_out,

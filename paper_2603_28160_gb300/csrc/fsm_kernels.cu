@@ -8,9 +8,13 @@
 //                    map lives in shared memory, every edge point that can
 //                    land in the tile below the stock is evaluated, binned by
 //                    the sampling boundaries of Eq. eq_sampling_boundaries and
-//                    folded in with a shared-memory atomicMin on an
-//                    order-preserving integer encoding of its height
-//   moments / profiles  FP64 roughness reductions (Section 4.1.2)
+//                    folded in with a shared-memory atomic that keeps the
+//                    lowest height (FP32 maps: signed atomicMax on the raw
+//                    bits of a negative height; FP64 maps: atomicMin on an
+//                    order-preserving integer encoding)
+//   roughness        moments and profiles in a fixed reduction order, double-
+//                    float sums on the FP32 pipes (Section 4.1.2)
+//   trajectory       per step and tooth, the lowest edge point (Section 3.1)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
