@@ -113,14 +113,17 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // whole number k of revolutions, less the visits' margins (two cells each
 // side), so that every spindle phase brings a point over the tile on the
 // same number k of revolutions -- the phase form's visit count is then the
-// same on nearly every lane. k is near target / rev: 480 cells, or 1280 for
-// FP64 floors, whose phase form computes the FP64 height once per phase and
-// gains from more revolutions per tile (measured, 5 mm ball raster FP64:
-// 1276x17 1.91 ms vs 636x34 2.09 ms; 8 mm flat floor FP64 1296x16 28.6 ms vs
-// 468x46 28.9 ms; the FP64 wall is fastest at 468x46). 0 when the feed per
-// revolution is too long for the widths allowed (64 .. 1.5 target).
+// same on nearly every lane. k is near target / rev, the targets measured
+// on GB300: 700 cells for FP32 maps (8 mm flat floor 704x55 17.0 ms vs
+// 468x83 17.9 ms, side wall 704x55 0.60 ms vs 0.63 ms; the ball raster's
+// 320-cell revolutions give 636 either way), 1280 for FP64 floors, whose
+// phase form computes the FP64 height once per phase and gains from more
+// revolutions per tile (ball raster 1276x17 1.91 ms vs 636x34 2.09 ms; flat
+// floor 1296x16 28.6 ms vs 468x46 28.9 ms), 480 for FP64 walls (468x46
+// 1.52 ms vs 940x23 2.36 ms). 0 when the feed per revolution is too long
+// for the widths allowed (64 .. 1.5 target).
 static int feed_aligned_width(const fsm_process_desc& p, int n_teeth) {
-    const double target = (p.precision == FSM_FP64 && p.surface == FSM_SURFACE_FLOOR) ? 1280.0 : 480.0;
+    const double target = p.precision == FSM_FP32 ? 700.0 : (p.surface == FSM_SURFACE_FLOOR ? 1280.0 : 480.0);
     const double rev = (double)n_teeth * p.fz / p.pitch;
     if (!(rev > 0.0) || rev > 1.5 * target) return 0;
     const int k = std::max(1, (int)llround(target / rev));
