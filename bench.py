@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--skip-paper", action="store_true")
     ap.add_argument("--skip-trajectory", action="store_true")
     ap.add_argument("--skip-wall", action="store_true")
+    ap.add_argument("--skip-tilted", action="store_true")
     ap.add_argument("--skip-filter", action="store_true")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the single-surface FP32 and FP64 steps (profiling runs)")
@@ -74,10 +75,10 @@ def parse():
                     help="patch width in mm (5.0 = the measured configuration; smaller for profiling)")
     args = ap.parse_args()
     if args.skip_extras:
-        for k in ("cpu_baseline", "batch", "large", "serve", "paper", "trajectory", "wall", "filter"):
+        for k in ("cpu_baseline", "batch", "large", "serve", "paper", "trajectory", "wall", "filter", "tilted"):
             setattr(args, "skip_" + k, True)
     if args.serve_only:
-        for k in ("cpu_baseline", "batch", "large", "paper", "trajectory", "wall", "filter", "fp64"):
+        for k in ("cpu_baseline", "batch", "large", "paper", "trajectory", "wall", "filter", "fp64", "tilted"):
             setattr(args, "skip_" + k, True)
     global WIDTH
     WIDTH = args.width
@@ -399,6 +400,35 @@ def large_grid_leg(ctx, F, flush, steps=2):
             "cells": w.process.cells, "trajectory_points": w.trajectory_points, "cutting": cutting,
             "steps": steps, "ms_per_step": ms, "sweep_ms": sum(sweep_ms) / len(sweep_ms),
             "value": cutting / (ms / 1e3), "unit": UNIT, "surfaces_per_s": 1e3 / ms}
+
+
+def tilted_feed_leg(ctx, F, flush, steps=3):
+    """The bench's ball raster fed at 30 degrees from +X (the tool path and
+    tool turned; passes enough to cross the 5 x 5 mm patch at 1 um), FP32,
+    one surface per step (planning, sweep, roughness), beside the same tool
+    on the +X path of the same generator."""
+    import torch
+    from paper_2603_28160_gb300 import workloads as W
+    res = {}
+    for deg in (30.0, 0.0):
+        w = W.raster_ball_tilted(precision="fp32", feed_dir_deg=deg)
+        t, p = ctx.tool(w.tool), ctx.process(w.process)
+        out = F.heights_tensor(w.process)
+        rough = torch.zeros(F.ROUGH_BYTES, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ctx.predict_surface(t, p, out, counters=cnt)
+        torch.cuda.synchronize()
+        cutting, evaluated = int(cnt[1].item()), int(cnt[0].item())
+        step_ms, sweep_ms = time_steps(ctx, F, t, p, out, rough, steps, flush, "fp32")
+        ms = sum(step_ms) / len(step_ms)
+        res["feed_%g_deg" % deg] = {"passes": w.process.n_passes, "trajectory_points": w.trajectory_points,
+                                    "cutting": cutting, "evaluated": evaluated, "ms_per_step": ms,
+                                    "sweep_ms": sum(sweep_ms) / len(sweep_ms), "value": cutting / (ms / 1e3),
+                                    "unit": UNIT, "surfaces_per_s": 1e3 / ms}
+        del out
+    res["workload"] = ("raster_ball_tilted: the ball raster's tool and conditions fed at 30 deg (and 0 deg) from +X, "
+                       "passes ae=0.3 crossing the 5x5 mm patch at 1 um")
+    return res
 
 
 def side_wall_leg(ctx, F, flush, steps=3):
@@ -908,6 +938,9 @@ def gb300_arm(args):
     side = None
     if not args.skip_wall and rank == 0:
         side = side_wall_leg(ctx, F, flush)
+    tilted = None
+    if not args.skip_tilted and rank == 0:
+        tilted = tilted_feed_leg(ctx, F, flush)
     traj = None
     if not args.skip_trajectory and rank == 0:
         traj = trajectory_leg(ctx, F, flush, peaks)
@@ -972,6 +1005,7 @@ def gb300_arm(args):
         "paper_case2": paper,
         "trajectory": traj,
         "side_wall": side,
+        "tilted_feed": tilted,
         "iso_filter": filt,
         "batched": batched,
         "served": served,
