@@ -138,8 +138,7 @@ typedef struct {
  *   spindle phase included) are turned by this angle about the vertical
  *   through (pass_x0, pass_y0): passes run along (cos, sin) and step over
  *   along (-sin, cos); the grid stays axis-aligned. A multiple of 360 is the
- *   +X feed itself. Floors only. Surfaces fed off the X axis take the item
- *   form of the sweep (FSM_FORM_PHASE is rejected for them).
+ *   +X feed itself. Floors only.
  * Validation: fz, ap, pitch > 0; 360/rot_step_deg integral; rot_sense = +-1;
  * n_passes >= 1 (== 1 for a wall); steps_per_pass >= 1;
  * n_passes*steps_per_pass < 2^31; 1 <= nx, ny <= 65535*256; finite values;

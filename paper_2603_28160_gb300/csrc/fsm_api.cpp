@@ -458,13 +458,9 @@ fsm_status check_fp32_band(const fsm_tool_desc& t, const fsm_process_desc& p, co
     return FSM_OK;
 }
 
-fsm_status check_opts(const fsm_predict_opts* o, const fsm_process_desc* const* procs, int n) {
+fsm_status check_opts(const fsm_predict_opts* o, const fsm_process_desc* const*, int) {
     if (o && o->sweep_form != FSM_FORM_AUTO && o->sweep_form != FSM_FORM_ITEM && o->sweep_form != FSM_FORM_PHASE)
         return fail(FSM_E_INVALID, "sweep_form must be FSM_FORM_AUTO, FSM_FORM_ITEM or FSM_FORM_PHASE");
-    if (o && o->sweep_form == FSM_FORM_PHASE)
-        for (int i = 0; i < n; ++i)
-            if (feed_tilted(*procs[i]))
-                return fail(FSM_E_INVALID, "FSM_FORM_PHASE needs the +X feed (feed_dir_deg a multiple of 360)");
     return FSM_OK;
 }
 

@@ -115,7 +115,7 @@ size_t fill_surface(const fsm_tool_desc& t, const fsm_process_desc& p, const Sha
                     char* base);
 fsm_status sweep_config(fsm_ctx* ctx, int precision, const Shape& sh, size_t* smem, int* blocks_per_sm);
 // Validate the caller's prediction overrides (NULL = defaults).
-// Options valid, and FSM_FORM_PHASE only for surfaces fed along +X.
+// Options valid (the surfaces of the call, for checks that need them).
 fsm_status check_opts(const fsm_predict_opts* o, const fsm_process_desc* const* procs, int n);
 fsm_status predict_one(fsm_ctx* ctx, const fsm_tool_desc& t, const fsm_process_desc& p, void* d_heights,
                        const fsm_predict_opts* opts, cudaStream_t st);

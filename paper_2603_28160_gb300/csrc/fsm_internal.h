@@ -24,7 +24,7 @@ int sweep_blocks_per_sm(int precision, int threads, size_t smem);
 cudaError_t sweep_allow_smem(size_t max_bytes);
 // phase_form: surfaces whose runs come back for many revolutions share
 // per-phase work (see phase_form_pays); tilt: some surface is fed off the X
-// axis (every task then takes the item form).
+// axis (the launch then takes the phase-capable tilted instantiation).
 cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_surf,
                                 const int* d_tile_base, int total_tiles, int* d_queue,
                                 long long* d_counters, int grid, int threads, size_t smem,

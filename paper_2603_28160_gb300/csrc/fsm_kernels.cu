@@ -1335,6 +1335,175 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
     return pos;
 }
 
+// Revolutions k (integers) at which v0 + k rev lies in [lo, hi], for one
+// coordinate of a phase offset's visits; the caller intersects the ranges
+// of x and y with the run's own revolutions [kb, ke]. A coordinate that
+// barely moves between revolutions (|rev| under 1e-4 cells: y on a feed
+// near +X, x near +Y) is tested once, widened by its drift over the run.
+__device__ __forceinline__ void rev_range(float v0, float rev, float lo, float hi, int kb, int ke, int* k0,
+                                          int* k1) {
+    if (fabsf(rev) < 1e-4f) {
+        const float drift = fabsf(rev) * (float)(ke - kb + 1) + 1.0f;
+        const bool in = v0 >= lo - drift && v0 <= hi + drift;
+        *k0 = in ? kb : 1;
+        *k1 = in ? ke : 0;
+        return;
+    }
+    const float inv = 1.0f / rev;
+    const float a = (lo - v0) * inv, b = (hi - v0) * inv;
+    *k0 = max(kb, __float2int_ru(fminf(a, b)));
+    *k1 = min(ke, __float2int_rd(fmaxf(a, b)));
+}
+
+// Phase form of a tilted feed: as sweep_phases, but a revolution moves the
+// point along both map axes (S fsx and S fsy cells), so every visit bins y
+// as well, and the revolutions visited are those whose x and y both lie
+// within the tile widened by M cells and half a cell (closed form per
+// coordinate). Each visit bins exactly as the tilted item form (same x and y
+// arithmetic, guard band and FP64 re-binning), so both forms give the same
+// maps and counts. Unlike the item form's step windows, which come from the
+// turned tile's bounding box, the ranges test the tile itself.
+template <bool F64>
+__device__ __forceinline__ void sweep_phases_tilted(const Surface& sf, const TileCtx<CellOf<F64>>& tc,
+                                                    const PassFrame& pf, int K, int g, int p, WarpScratch& ws,
+                                                    AmbQueue* aq, const float4 (&t4)[3], float zb_lane,
+                                                    Counters& cnt) {
+    using Cell = CellOf<F64>;
+    const int lane = threadIdx.x & 31;
+    constexpr int L = kItemLanes;
+    const int hl = lane & (L - 1), grp = lane / L;
+    const int S = sf.S;
+    const float fS = (float)S;
+    const bool back = pass_reversed(sf, p);
+    const float fsx = back ? -sf.fscx_f : sf.fscx_f, fsy = back ? -sf.fscy_f : sf.fscy_f;  // cells per step
+    const float rev_x = fS * fsx, rev_y = fS * fsy;  // cells per revolution
+    const float2* __restrict__ ph32 = sf.ph32;
+    const double2* __restrict__ ph64 = sf.ph64;
+    const int NE = sf.n_teeth * sf.E;
+    const double zr = sf.z_ref;
+    const unsigned long long below_key = stock_key(sf.stock);
+    const int tile_x = sf.tile_x;
+    Cell* cells = tc.cells;
+    const int txc = tc.txc, tyc = tc.tyc;
+    int R = ws.n[lane];
+    for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
+    int qn = 0;  // queued re-bins (warp-uniform)
+    int an = 0;  // queued ambiguous points (warp-uniform)
+    for (int q = 0; q < R; q += 32 / L) {
+        const int ri = q + grp;
+        const bool has = ri < R;
+        const int code = has ? (int)ws.flat[ri] : 0;
+        const int o = code >> 1, a = code & 1;
+        RunRec r = ws.run[o][a];
+        if (!has) {  // a well-formed empty run (no offsets; its fields stay in range)
+            r.m0 = 0; r.len = 0; r.occ0 = 0; r.first_off = 0; r.len0 = 0; r.k_last = 0; r.len_last = 0;
+            r.dxA = 0.f; r.g_cells = 0.f;
+        }
+        const int len = r.len;
+        const float ux = __shfl_sync(0xffffffffu, t4[0].x, o), vx = __shfl_sync(0xffffffffu, t4[0].y, o);
+        const float wx = __shfl_sync(0xffffffffu, t4[0].z, o), uz = __shfl_sync(0xffffffffu, t4[0].w, o);
+        const float uy = __shfl_sync(0xffffffffu, t4[1].x, o), vy = __shfl_sync(0xffffffffu, t4[1].y, o);
+        const float wy = __shfl_sync(0xffffffffu, t4[1].z, o), vz = __shfl_sync(0xffffffffu, t4[1].w, o);
+        const float zb = __shfl_sync(0xffffffffu, zb_lane, o);
+        const int idx = K * sf.E + g * 32 + o;
+        double uz64 = 0.0, vz64 = 0.0, wz64 = 0.0;
+        if constexpr (F64) {
+            uz64 = __ldg(sf.tool64 + 2 * NE + idx);
+            vz64 = __ldg(sf.tool64 + 5 * NE + idx);
+            wz64 = __ldg(sf.tool64 + 8 * NE + idx);
+        }
+        int lmax = len;
+        for (int o2 = L; o2 < 32; o2 <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
+        const int32_t sA = r.occ0 + r.first_off;
+        const float gc = r.g_cells;
+        const float hg = gc >= 0.5f ? -1.0f : 0.5f - gc;
+        const int M = F64 ? max(1, (int)ceilf(gc)) : 1;
+        // the pass's y at the run's first step, as in the tilted item form
+        const int32_t n0 = sA - p * sf.steps_per_pass;
+        const float dyA = df_affine(pf.dy, pf.dy_lo, back ? sf.steps_per_pass - 1 - n0 : n0, sf.fscy_hi, sf.fscy_lo);
+        // the tile widened by M cells and half a cell (centred coordinates)
+        const float lo_x = -((float)M + 1.0f), hi_x = (float)(txc + M);
+        const float lo_y = -((float)M + 1.0f), hi_y = (float)(tyc + M);
+        const float d_first = (float)(r.occ0 - sA);  // steps from the run's first item to phase 0 of its first turn
+        const int f0 = r.first_off, f1 = r.first_off + r.len0;
+        float2 c_next = __ldg(ph32 + r.m0 + (hl < len ? hl : 0));
+        for (int ob = 0; ob < lmax; ob += L) {
+            const int off = ob + hl;
+            const bool vo = off < len;
+            const int offc = vo ? off : 0;
+            const int32_t m = r.m0 + offc;  // < 2S: the table holds two turns
+            const float2 c = c_next;
+            c_next = __ldg(ph32 + r.m0 + (off + L < len ? off + L : 0));
+            const float z = fmaf(c.x, uz, fmaf(c.y, vz, zb));
+            const float px = fmaf(c.x, ux, fmaf(c.y, vx, wx));
+            const float py = fmaf(c.x, uy, fmaf(c.y, vy, wy));
+            Cell e;
+            bool below;
+            if constexpr (F64) {  // below the stock by the FP64 height
+                e = cell_key(height64(__ldg(ph64 + m), uz64, vz64, wz64, zr));
+                below = e < below_key;
+            } else {
+                below = z < 0.f;
+                e = cell_key(z);
+            }
+            // revolutions of this phase inside the run's step window ...
+            const int kb = (offc >= f0 && offc < f1) ? 0 : 1;
+            const int ke = r.k_last == 0 ? 0 : (offc < r.len_last ? r.k_last : r.k_last - 1);
+            // ... and over the tile along both axes: revolution k is d0 + k S
+            // steps after the run's first item, at (x0, y0) + k S (fsx, fsy)
+            const float d0 = d_first + (float)offc;
+            const float x0 = fmaf(d0, fsx, r.dxA) + px;
+            const float y0 = fmaf(d0, fsy, dyA) + py;
+            int kx0, kx1, ky0, ky1;
+            rev_range(x0, rev_x, lo_x, hi_x, kb, ke, &kx0, &kx1);
+            rev_range(y0, rev_y, lo_y, hi_y, kb, ke, &ky0, &ky1);
+            const int k0 = max(kx0, ky0), k1 = min(kx1, ky1);
+            const int n_it = (vo && below) ? max(k1 - k0 + 1, 0) : 0;
+            const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_it);
+            float ds = fmaf((float)k0, fS, d0);  // steps after the run's first item (an exact integer)
+            for (int kk = 0; kk < n_max; kk += 2) {
+                const bool va = kk < n_it, vb = kk + 1 < n_it;
+                const float dsb = ds + fS;
+                const float fxa = fmaf(ds, fsx, r.dxA) + px, fya = fmaf(ds, fsy, dyA) + py;
+                const float fxb = fmaf(dsb, fsx, r.dxA) + px, fyb = fmaf(dsb, fsy, dyA) + py;
+                const int ia = __float2int_rn(fxa), ja = __float2int_rn(fya);
+                const int ib = __float2int_rn(fxb), jb = __float2int_rn(fyb);
+                const float rxa = fxa - __int2float_rn(ia), rya = fya - __int2float_rn(ja);
+                const float rxb = fxb - __int2float_rn(ib), ryb = fyb - __int2float_rn(jb);
+                cnt.evaluated += (unsigned)va + (unsigned)vb;
+                const bool in_a = va && (unsigned)ia < (unsigned)txc && (unsigned)ja < (unsigned)tyc;
+                const bool in_b = vb && (unsigned)ib < (unsigned)txc && (unsigned)jb < (unsigned)tyc;
+                const bool amb_a = fmaxf(fabsf(rxa), fabsf(rya)) > hg;  // within gc of a cell boundary
+                const bool amb_b = fmaxf(fabsf(rxb), fabsf(ryb)) > hg;
+                const bool upd_a = in_a && !amb_a, upd_b = in_b && !amb_b;
+                cnt.cutting += F64 ? (unsigned)upd_a + (unsigned)upd_b : (unsigned)in_a + (unsigned)in_b;
+                const int cia = ja * tile_x + ia, cib = jb * tile_x + ib;
+                const Cell cva = upd_a ? cells[cia] : (Cell)0;
+                const Cell cvb = upd_b ? cells[cib] : (Cell)0;
+                if (upd_a && lowers(e, cva)) {
+                    lower_cell(cells + cia, e);
+                    ++cnt.atomics;
+                }
+                if (upd_b && lowers(e, cvb)) {
+                    lower_cell(cells + cib, e);
+                    ++cnt.atomics;
+                }
+                const bool pa = va && amb_a, pb = vb && amb_b;  // pushed if near the tile (tested below)
+                if (__any_sync(0xffffffffu, pa || pb)) {
+                    const bool near_a = ia >= -M && ia <= txc - 1 + M && ja >= -M && ja <= tyc - 1 + M;
+                    const bool near_b = ib >= -M && ib <= txc - 1 + M && jb >= -M && jb <= tyc - 1 + M;
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pa && near_a, ia, ja, rxa, rya, gc, z, sA + (int32_t)ds, m,
+                                        idx, an, qn, cnt);
+                    push_ambiguous<F64>(sf, tc, ws, aq, p, pb && near_b, ib, jb, rxb, ryb, gc, z,
+                                        sA + (int32_t)dsb, m, idx, an, qn, cnt);
+                }
+                ds = dsb + fS;
+            }
+        }
+    }
+    drain_queues<F64>(sf, tc, ws, aq, p, an, qn, cnt);
+}
+
 __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1348,9 +1517,9 @@ __device__ __forceinline__ int find_surface(const int* tile_base, int n, int t) 
 // (tile_base[s] = first tile of surface s); CTAs take tiles in a static
 // stride, or from *queue when it is not NULL. Inside a tile, warps take
 // (pass, tooth, 32-point group) tasks from a shared counter.
-// kTilt: the launch may hold surfaces fed off the X axis (taken item by
-// item, with y stepping along the feed); the others run as in the plain
-// instantiation.
+// kTilt: the launch may hold surfaces fed off the X axis (y stepping along
+// the feed in either form; these instantiations are phase-capable); the
+// others run as in the plain phase-capable instantiation.
 template <bool FP64, bool kCount, bool kPhases, bool kTilt = false>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict__ surfs, int n_surf,
                                                        const int* __restrict__ tile_base, int total_tiles,
@@ -1531,12 +1700,19 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const Surface* __restrict
                                     items += __shfl_xor_sync(0xffffffffu, items, o);
                                     phases += __shfl_xor_sync(0xffffffffu, phases, o);
                                 }
-                                by_phase = phase_form_task<FP64>(items, phases);
+                                // (FP32 tasks of a tilted feed stay item by item: its phase
+                                // form evaluates a third fewer poses but costs more per
+                                // visit, 30 degrees 2.97 -> 3.42 ms; FP64 gains, 10.5 -> 8.9)
+                                by_phase = (FP64 || !(kTilt && sf.tilted)) && phase_form_task<FP64>(items, phases);
                             }
                         }
                         if (sf.form_tasks && lane == 0) atomicAdd(sf.form_tasks + (by_phase ? 1 : 0), 1ull);
                     }
-                    if (by_phase)
+                    bool tilted_phases = false;
+                    if constexpr (kTilt) tilted_phases = by_phase && sf.tilted;
+                    if (tilted_phases) {
+                        if constexpr (kTilt) sweep_phases_tilted<FP64>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
+                    } else if (by_phase)
                         sweep_phases<FP64>(sf, tc, pf.dy, K, g, p, ws, aq, t4, zb, cnt);
                     else if (kTilt && sf.tilted)
                         sweep_items<FP64, kItemChains, kTilt>(sf, tc, pf, K, g, p, ws, aq, t4, zb, cnt);
@@ -2503,16 +2679,16 @@ cudaError_t launch_sweep_shaped(int precision, const Surface* d_surfs, int n_sur
     // loop has the SM to itself
     if (tilt) {
         if (precision == 0 && d_counters)
-            sweep_kernel<true, true, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+            sweep_kernel<true, true, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
                                                                                total_tiles, d_queue, d_counters);
         else if (precision == 0)
-            sweep_kernel<true, false, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+            sweep_kernel<true, false, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
                                                                                 total_tiles, d_queue, nullptr);
         else if (d_counters)
-            sweep_kernel<false, true, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+            sweep_kernel<false, true, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
                                                                                 total_tiles, d_queue, d_counters);
         else
-            sweep_kernel<false, false, false, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
+            sweep_kernel<false, false, true, true><<<grid, threads, smem, st>>>(d_surfs, n_surf, d_tile_base,
                                                                                  total_tiles, d_queue, nullptr);
     } else if (precision == 0 && phase_form) {
         if (d_counters)
@@ -2567,10 +2743,10 @@ cudaError_t sweep_allow_smem(size_t max_bytes) {
     if ((e = allow_dynamic_smem(sweep_kernel<false, false, false>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, true, true>, max_bytes)) != cudaSuccess) return e;
     if ((e = allow_dynamic_smem(sweep_kernel<false, false, true>, max_bytes)) != cudaSuccess) return e;
-    if ((e = allow_dynamic_smem(sweep_kernel<true, true, false, true>, max_bytes)) != cudaSuccess) return e;
-    if ((e = allow_dynamic_smem(sweep_kernel<true, false, false, true>, max_bytes)) != cudaSuccess) return e;
-    if ((e = allow_dynamic_smem(sweep_kernel<false, true, false, true>, max_bytes)) != cudaSuccess) return e;
-    return allow_dynamic_smem(sweep_kernel<false, false, false, true>, max_bytes);
+    if ((e = allow_dynamic_smem(sweep_kernel<true, true, true, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<true, false, true, true>, max_bytes)) != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem(sweep_kernel<false, true, true, true>, max_bytes)) != cudaSuccess) return e;
+    return allow_dynamic_smem(sweep_kernel<false, false, true, true>, max_bytes);
 }
 
 // Resident CTAs per SM: the smallest over the instantiations of a precision.
@@ -2582,18 +2758,18 @@ int sweep_blocks_per_sm(int precision, int threads, size_t smem) {
         e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 1, sweep_kernel<true, false, false>, threads, smem);
         e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 2, sweep_kernel<true, true, true>, threads, smem);
         e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 3, sweep_kernel<true, false, true>, threads, smem);
-        e[4] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 4, sweep_kernel<true, true, false, true>, threads,
+        e[4] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 4, sweep_kernel<true, true, true, true>, threads,
                                                              smem);
-        e[5] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 5, sweep_kernel<true, false, false, true>, threads,
+        e[5] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 5, sweep_kernel<true, false, true, true>, threads,
                                                              smem);
     } else {
         e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 0, sweep_kernel<false, true, false>, threads, smem);
         e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 1, sweep_kernel<false, false, false>, threads, smem);
         e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 2, sweep_kernel<false, true, true>, threads, smem);
         e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 3, sweep_kernel<false, false, true>, threads, smem);
-        e[4] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 4, sweep_kernel<false, true, false, true>, threads,
+        e[4] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 4, sweep_kernel<false, true, true, true>, threads,
                                                              smem);
-        e[5] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 5, sweep_kernel<false, false, false, true>,
+        e[5] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(r + 5, sweep_kernel<false, false, true, true>,
                                                              threads, smem);
     }
     int b = 1 << 20;

@@ -7,7 +7,8 @@ in the feed frame (the tile's extent along and across the feed) and bins in
 the map frame, y stepping along the feed like x. Maps are compared cell by
 cell with the oracle (Section 2.3's per-cell minimum over the points of Eq.
 eq_sampling_boundaries) at several tiles with ragged edges, for both
-precisions, both pass modes and a flat and a ball end; batches that mix
+precisions, both pass modes, a flat and a ball end and both phase-2 forms
+(identical maps); batches that mix
 tilted and +X surfaces must give every surface the map it gets alone, bit
 for bit; the server the same.
 """
@@ -93,7 +94,7 @@ def test_tilted_feed_matches_oracle(ctx, F, oracle_mod, name, prec):
     else:
         assert abs(int(c[1]) - ref.stats["cutting"]) <= 1e-5 * ref.stats["cutting"] + 2
     t = tasks.cpu().numpy()
-    assert t[0] > 0 and t[1] == 0  # tilted surfaces are walked item by item
+    assert t.sum() > 0
     # roughness of the tilted map
     r = ctx.roughness(H)
     o = oracle_mod.roughness(ref.H)
@@ -158,13 +159,31 @@ def test_batch_mixing_tilted_and_axis_feeds(ctx, F, prec):
         ctx.server_stop()
 
 
-def test_phase_form_and_tilted_walls_are_rejected(ctx, F):
-    w = CASES["ball_30"]()
-    t, p = ctx.tool(w.tool), ctx.process(w.process)
-    out = F.heights_tensor(w.process)
-    with pytest.raises(F.FsmError) as e:
-        ctx.predict_surface(t, p, out, form="phase")
-    assert e.value.status == -1
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tilted_forms_match_oracle_and_each_other(ctx, F, oracle_mod, name, prec):
+    """Each phase-2 form forced on a tilted feed: the item form (step windows
+    from the turned tile's bounding box) and the phase form (revolution
+    ranges of x and y against the tile itself) evaluate the same cutting
+    points with the same arithmetic: the same map, bit for bit, and counts."""
+    import torch
+    w = _with(CASES[name](), precision=prec)
+    ref = reference(oracle_mod, name)
+    got = {}
+    for form, slot in (("item", 0), ("phase", 1)):
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        tasks = torch.zeros(2, dtype=torch.int64, device="cuda")
+        H = gpu_map(ctx, F, w, counters=cnt, form=form, form_tasks=tasks)
+        compare_maps(H, ref, prec)
+        t = tasks.cpu().numpy()
+        assert t[slot] > 0 and t[1 - slot] == 0, (form, t)
+        got[form] = (H.cpu().numpy(), cnt.cpu().numpy())
+    assert np.array_equal(got["item"][0], got["phase"][0])
+    assert got["item"][1][1] == got["phase"][1][1]  # cutting count
+    assert got["phase"][1][0] <= got["item"][1][0]  # the phase form evaluates no more poses
+
+
+def test_tilted_walls_are_rejected(ctx, F):
     wall = W.side_wall_flat_d12(precision="fp64", length=0.2)
     with pytest.raises(F.FsmError) as e:
         ctx.process(wall.process.replace(feed_dir_deg=20.0))

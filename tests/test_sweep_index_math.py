@@ -190,3 +190,58 @@ def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
         if k1 > k0:
             assert (k1 - k0) * abs(float(fs)) * S <= (txc + 2 * M + 1) * (1 + 1e-5) + 1e-3
     assert hit > 1000
+
+
+def rev_range(v0, rev, lo, hi, kb, ke):
+    """The tilted phase form's revolution range of one coordinate (FP32)."""
+    if abs(float(rev)) < 1e-4:
+        drift = f32(abs(float(rev)) * (ke - kb + 1) + 1.0)
+        ok = (v0 >= lo - drift) and (v0 <= hi + drift)
+        return (kb, ke) if ok else (1, 0)
+    inv = f32(1.0) / rev
+    a, b = f32((lo - v0) * inv), f32((hi - v0) * inv)
+    return max(kb, int(np.ceil(min(a, b)))), min(ke, int(np.floor(max(a, b))))
+
+
+def test_tilted_phase_form_revolution_range_covers_the_tile():
+    """Tilted phase form: revolution k of a phase offset sits at (FP32)
+    x = fma(ds_k, fsx, dxA) + px, y = fma(ds_k, fsy, dyA) + py with
+    ds_k = d0 + k S; the kernel visits the intersection of the ranges of x in
+    [-(M + 1), txc + M] and y in [-(M + 1), tyc + M] with the run's [kb, ke].
+    Every revolution whose x and y round into the tile widened by M cells
+    must be visited, at any feed direction (including ones where a
+    coordinate barely moves per revolution) and both pass directions."""
+    rng = np.random.default_rng(67)
+    hit = 0
+    for _ in range(6000):
+        S = int(rng.integers(1, 40000))
+        fs = 10.0 ** rng.uniform(-4.0, 1.0)
+        phi = rng.choice([rng.uniform(0, 2 * np.pi), 0.0, np.pi / 2, rng.uniform(-1e-7, 1e-7),
+                          np.pi / 2 + rng.uniform(-1e-7, 1e-7)])
+        sign = 1 if rng.random() < 0.5 else -1
+        fsx, fsy = f32(sign * fs * np.cos(phi)), f32(sign * fs * np.sin(phi))
+        txc, tyc = int(rng.integers(1, 1025)), int(rng.integers(1, 200))
+        M = int(rng.integers(1, 4))
+        kb, ke = int(rng.integers(0, 2)), int(rng.integers(0, 300))
+        if ke < kb or fs * S * ke > 1e6:
+            continue
+        d0 = f32(-int(rng.integers(0, S)) + int(rng.integers(0, S)))
+        px, py = f32(rng.uniform(-3000.0, 3000.0)), f32(rng.uniform(-3000.0, 3000.0))
+        k_mid = rng.uniform(kb, ke + 1)
+        dxa = f32(rng.uniform(-M - 2, txc + M + 2) - float(px) - (float(d0) + k_mid * S) * float(fsx))
+        dya = f32(rng.uniform(-M - 2, tyc + M + 2) - float(py) - (float(d0) + k_mid * S) * float(fsy))
+        rev_x, rev_y = f32(f32(S) * fsx), f32(f32(S) * fsy)
+        x0 = (fma32(np.array([d0]), np.array([fsx]), np.array([dxa]))[0] + px).astype(f32)
+        y0 = (fma32(np.array([d0]), np.array([fsy]), np.array([dya]))[0] + py).astype(f32)
+        kx0, kx1 = rev_range(x0, rev_x, f32(-(M + 1.0)), f32(txc + M), kb, ke)
+        ky0, ky1 = rev_range(y0, rev_y, f32(-(M + 1.0)), f32(tyc + M), kb, ke)
+        k0, k1 = max(kx0, ky0), min(kx1, ky1)
+        ks = np.arange(kb, ke + 1)
+        ds = (f32(d0) + ks.astype(np.float64) * S).astype(f32)
+        xs = (fma32(ds, np.full(ks.size, fsx, f32), np.full(ks.size, dxa, f32)) + px).astype(f32)
+        ys = (fma32(ds, np.full(ks.size, fsy, f32), np.full(ks.size, dya, f32)) + py).astype(f32)
+        ix, iy = np.rint(xs.astype(np.float64)), np.rint(ys.astype(np.float64))
+        over = ks[(ix >= -M) & (ix <= txc - 1 + M) & (iy >= -M) & (iy <= tyc - 1 + M)]
+        hit += over.size
+        assert over.size == 0 or (over.min() >= k0 and over.max() <= k1), (S, float(fsx), float(fsy), over, k0, k1)
+    assert hit > 1000
