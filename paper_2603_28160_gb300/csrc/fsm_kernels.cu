@@ -866,6 +866,7 @@ __device__ __forceinline__ void amb_push(AmbQueue& aq, bool want, int i, int k, 
                                          float z, int32_t s, int32_t m, int idx, int& an) {
     const int lane = threadIdx.x & 31;
     const unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (!bal) return;
     if (want) {
         const int pos = an + __popc(bal & ((1u << lane) - 1u));
         const int dx = rx < g - 0.5f ? -1 : (rx > 0.5f - g ? 1 : 0);  // (rx, ry from the cell's centre)
@@ -1234,6 +1235,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         const float x_near = -((float)M + 1.0f), x_far = (float)(txc + M);  // (centred coordinates)
         const float xk_lo = back ? x_far : x_near, xk_hi = back ? x_near : x_far;
         const float d_first = (float)(r.occ0 - sA);  // steps from the run's first item to phase 0 of its first turn
+        const float klo_c = xk_lo * inv_rev, khi_c = xk_hi * inv_rev;
         const int f0 = r.first_off, f1 = r.first_off + r.len0;
         // the phase-table entry of the next offset is loaded one round ahead
         // (the table does not stay in the L1 left beside a large tile)
@@ -1262,14 +1264,14 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             const bool row = vo && below && ky >= -M && ky <= tyc - 1 + M;
             // revolutions of this phase inside the run's step window: the
             // first only for offsets it covers, the last only below its length
-            const int kb = (offc >= f0 && offc < f1) ? 0 : 1;
-            const int ke = r.k_last == 0 ? 0 : (offc < r.len_last ? r.k_last : r.k_last - 1);
+            const int kb = (unsigned)(offc - f0) < (unsigned)(f1 - f0) ? 0 : 1;
+            const int ke = r.k_last - ((offc >= r.len_last && r.k_last != 0) ? 1 : 0);
             // ... and within the x range: revolution k is d0 + k S steps after
             // the run's first item, at x ~ x0 + k S fs
             const float d0 = d_first + (float)offc;
             const float x0 = fmaf(d0, fs32, r.dxA) + px;
-            const int k0 = max(kb, __float2int_ru((xk_lo - x0) * inv_rev));
-            const int k1 = min(ke, __float2int_rd((xk_hi - x0) * inv_rev));
+            const int k0 = max(kb, __float2int_ru(fmaf(-x0, inv_rev, klo_c)));
+            const int k1 = min(ke, __float2int_rd(fmaf(-x0, inv_rev, khi_c)));
             const int n_it = row ? max(k1 - k0 + 1, 0) : 0;
             const int n_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_it);
             const bool ky_in = (unsigned)ky < (unsigned)tyc;

@@ -150,9 +150,9 @@ def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
     """Phase form: for one phase offset, revolution k of a run is
     ds_k = d0 + k S steps after the run's first item, at tile-local x (cells)
     fma(ds_k, fs, dxA) + px in FP32. The kernel visits k in
-    [max(kb, ceil((lo - x0) / (S fs))), min(ke, floor((hi - x0) / (S fs)))],
-    x0 = fma(d0, fs, dxA) + px, with (lo, hi) = (-(M + 1), txc + M) (swapped
-    on a return pass, fs < 0), in FP32. Coordinates are centred on cells
+    [max(kb, ceil(fma(-x0, r, lo r))), min(ke, floor(fma(-x0, r, hi r)))],
+    r = 1 / (S fs), x0 = fma(d0, fs, dxA) + px, with (lo, hi) = (-(M + 1),
+    txc + M) (swapped on a return pass, fs < 0), in FP32. Coordinates are centred on cells
     (the cell is the nearest integer), so every revolution whose FP32 x
     rounds into the tile widened by M cells -- x in [-M - 1/2, txc - 1 + M
     + 1/2] -- must be visited, for both feed directions."""
@@ -176,8 +176,9 @@ def test_phase_form_revolution_range_contains_every_revolution_over_the_tile():
         k_lo, k_hi = (hi, lo) if back else (lo, hi)
         inv_rev = f32(1.0) / (f32(S) * fs)
         x0 = (fma32(np.array([d0]), np.array([fs]), np.array([dxa]))[0] + px).astype(f32)
-        k0 = max(kb, int(np.ceil(f32((k_lo - x0) * inv_rev))))
-        k1 = min(ke, int(np.floor(f32((k_hi - x0) * inv_rev))))
+        klo_c, khi_c = f32(k_lo * inv_rev), f32(k_hi * inv_rev)
+        k0 = max(kb, int(np.ceil(fma32(np.array([-x0]), np.array([inv_rev]), np.array([klo_c]))[0])))
+        k1 = min(ke, int(np.floor(fma32(np.array([-x0]), np.array([inv_rev]), np.array([khi_c]))[0])))
         ks = np.arange(kb, ke + 1)
         ds = (f32(d0) + ks.astype(np.float64) * S).astype(f32)
         xs = (fma32(ds, np.full(ks.size, fs, f32), np.full(ks.size, dxa, f32)) + px).astype(f32).astype(np.float64)
