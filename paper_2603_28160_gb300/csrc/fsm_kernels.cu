@@ -510,11 +510,14 @@ __device__ __forceinline__ double path_y(const Surface& sf, int p, int32_t n) {
     }
     return path_y(sf, p);
 }
+// The z row takes the tool reference height into the point's constant first
+// (w_z + z_ref), so the sweeps add it once per run and every FP64 height --
+// sweep, re-bin, trajectory -- comes from the same three operations.
 __device__ __forceinline__ Pose64 pose64(const Vec9& v, double2 cs, double xc, double yc, double zr) {
     Pose64 P;
     P.x = __dadd_rn(xc, __fma_rn(cs.x, v.ux, __fma_rn(cs.y, v.vx, v.wx)));
     P.y = __dadd_rn(yc, __fma_rn(cs.x, v.uy, __fma_rn(cs.y, v.vy, v.wy)));
-    P.z = __dadd_rn(zr, __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, v.wz)));
+    P.z = __fma_rn(cs.x, v.uz, __fma_rn(cs.y, v.vz, __dadd_rn(v.wz, zr)));
     return P;
 }
 __device__ __forceinline__ long long bin64(double coord, double origin, double inv_pitch) {
@@ -745,9 +748,9 @@ __device__ __forceinline__ unsigned long long stock_key(double stock) {
 }
 
 // FP64 height of edge point (u, v, w) at phase (cos, sin): the z row of the
-// FP64 pose.
-__device__ __forceinline__ double height64(double2 cs, double uz, double vz, double wz, double zr) {
-    return __dadd_rn(zr, __fma_rn(cs.x, uz, __fma_rn(cs.y, vz, wz)));
+// FP64 pose, with wzr = w_z + z_ref formed once per run (as pose64 forms it).
+__device__ __forceinline__ double height64(double2 cs, double uz, double vz, double wzr) {
+    return __fma_rn(cs.x, uz, __fma_rn(cs.y, vz, wzr));
 }
 
 // FP32 height of an FP32 map's point relative to the stock: the FP32 pose's
@@ -1043,7 +1046,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
         if constexpr (F64) {
             uz64 = __ldg(sf.tool64 + 2 * NE + idx);
             vz64 = __ldg(sf.tool64 + 5 * NE + idx);
-            wz64 = __ldg(sf.tool64 + 8 * NE + idx);
+            wz64 = __dadd_rn(__ldg(sf.tool64 + 8 * NE + idx), zr);  // w_z + z_ref
         }
         const int tot = has ? rec_total(r) : 0;
         int tmax = tot;
@@ -1124,7 +1127,7 @@ __device__ __forceinline__ void sweep_items(const Surface& sf, const TileCtx<Cel
                 Cell e;
                 bool cut;
                 if constexpr (F64) {  // below the stock by the FP64 height
-                    e = cell_key(height64(__ldg(ph64 + mi[k]), uz64, vz64, wz64, zr));
+                    e = cell_key(height64(__ldg(ph64 + mi[k]), uz64, vz64, wz64));
                     cut = v && e < below_key;
                 } else {
                     cut = v && z < 0.f;
@@ -1220,7 +1223,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
         if constexpr (F64) {
             uz64 = __ldg(sf.tool64 + 2 * NE + idx);
             vz64 = __ldg(sf.tool64 + 5 * NE + idx);
-            wz64 = __ldg(sf.tool64 + 8 * NE + idx);
+            wz64 = __dadd_rn(__ldg(sf.tool64 + 8 * NE + idx), zr);  // w_z + z_ref
         }
         int lmax = len;
         for (int o2 = L; o2 < 32; o2 <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
@@ -1255,7 +1258,7 @@ __device__ __forceinline__ void sweep_phases(const Surface& sf, const TileCtx<Ce
             Cell e;
             bool below;
             if constexpr (F64) {  // below the stock by the FP64 height
-                e = cell_key(height64(__ldg(ph64 + m), uz64, vz64, wz64, zr));
+                e = cell_key(height64(__ldg(ph64 + m), uz64, vz64, wz64));
                 below = e < below_key;
             } else {
                 below = z < 0.f;
@@ -1412,7 +1415,7 @@ __device__ __forceinline__ void sweep_phases_tilted(const Surface& sf, const Til
         if constexpr (F64) {
             uz64 = __ldg(sf.tool64 + 2 * NE + idx);
             vz64 = __ldg(sf.tool64 + 5 * NE + idx);
-            wz64 = __ldg(sf.tool64 + 8 * NE + idx);
+            wz64 = __dadd_rn(__ldg(sf.tool64 + 8 * NE + idx), zr);  // w_z + z_ref
         }
         int lmax = len;
         for (int o2 = L; o2 < 32; o2 <<= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o2));
@@ -1442,7 +1445,7 @@ __device__ __forceinline__ void sweep_phases_tilted(const Surface& sf, const Til
             Cell e;
             bool below;
             if constexpr (F64) {  // below the stock by the FP64 height
-                e = cell_key(height64(__ldg(ph64 + m), uz64, vz64, wz64, zr));
+                e = cell_key(height64(__ldg(ph64 + m), uz64, vz64, wz64));
                 below = e < below_key;
             } else {
                 below = z < 0.f;
