@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         }
         float amp[3], mph[3];
         double a64[3];
+#pragma unroll 1  // one copy of the FP64 sqrt/atan2/fmod code: it runs once, from a cold cache
         for (int d = 0; d < 3; ++d) {
             const double a = sqrt(u[d] * u[d] + v[d] * v[d]);
             a64[d] = a;
@@ -346,25 +347,34 @@ __global__ void __launch_bounds__(256) plan_finish_kernel(Surface* surfs, int n,
     // below the stock (the tile-independent z limit of the enumeration), and
     // their lowest z. A group outside a tile's y band has no runs there.
     // (Cached tables keep theirs: the limit, stock - z_ref, is ap plus the
-    // tables' lowest z, a function of the cached inputs.)
-    __syncthreads();
-    if (sf->cached) return;
+    // tables' lowest z, a function of the cached inputs.) Warps 1.. take
+    // the groups while warp 0 runs the scalar section above, so the scalars
+    // they need are formed here by the same operations (launched with 256
+    // threads: seven group warps).
+    if (sf->cached || warp == 0) return;
+    const double dth_l = deg2rad(sf->rot_step_deg);
+    const double zr_l = sf->surface == 1 ? -sf->pass_y0 : sf->stock_z - sf->ap - zlo;
+    const double stock_l = sf->surface == 1 ? -sf->wall_y : sf->stock_z;
+    const float inv_dth_f = (float)(1.0 / dth_l), dth_f = (float)dth_l, pitch_f = (float)sf->pitch;
+    double fsn_l = 0.0, fc_l = 1.0;
+    if (sf->tilted) sincos(deg2rad(sf->feed_dir_deg), &fsn_l, &fc_l);
+    const float feed_cf = (float)fc_l, feed_sf = (float)fsn_l;
     const int G = (E + 31) / 32;
-    const float zhi = (float)(sf->stock - sf->z_ref) + kMarginMm;
+    const float zhi = (float)(stock_l - zr_l) + kMarginMm;
     const float fS = (float)S;
-    for (int gi = warp; gi < N * G; gi += nw) {
+    for (int gi = warp - 1; gi < N * G; gi += nw - 1) {
         const int K = gi / G, g = gi - K * G;
         const int j = g * 32 + lane;
         float ymin = 3.0e38f, ymax = -3.0e38f, zmin = 3.0e38f;
         if (j < E) {
-            PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), sf->pitch_f);
-            if (sf->tilted) to_feed_frame(geo, sf->feed_cf, sf->feed_sf);
+            PointGeom geo = load_geom(sf->tool32 + 4 * (size_t)(K * E + j), pitch_f);
+            if (sf->tilted) to_feed_frame(geo, feed_cf, feed_sf);
             zmin = geo.wz - geo.amp_z;
             ArcF za;
             ArcI ia[kMaxArcs];
-            if (below_arc(geo.wz, geo.amp_z, geo.mph_z, zhi, sf->inv_dth_f, fS, &za) > 0 &&
+            if (below_arc(geo.wz, geo.amp_z, geo.mph_z, zhi, inv_dth_f, fS, &za) > 0 &&
                 to_int_arcs(&za, 1, S, ia) > 0) {
-                sinus_range(geo.wy, geo.amp_y, geo.mph_y, ia[0], sf->dth_f, S, &ymin, &ymax);
+                sinus_range(geo.wy, geo.amp_y, geo.mph_y, ia[0], dth_f, S, &ymin, &ymax);
                 const float slack = 1e-5f * geo.amp_y + kMarginMm;
                 ymin -= slack;
                 ymax += slack;
