@@ -243,8 +243,13 @@ __global__ void __launch_bounds__(256) plan_kernel(Surface* surfs, int n, Surfac
         t32[2] = make_float4((float)w[2], amp[1], mph[1], amp[2]);
         t32[3] = make_float4(mph[2], amp[0], mph[0], 0.f);
     }
-    // phase table, two turns (entry m + S repeats entry m)
-    for (int m = first; m < S; m += stride) {
+    // phase table, two turns (entry m + S repeats entry m); its entries
+    // continue the thread numbering after the edge points, so a grid sized
+    // for both gives each thread one item (every residue mod stride is taken
+    // by exactly one thread)
+    int m_first = first - NE % stride;
+    if (m_first < 0) m_first += stride;
+    for (int m = m_first; m < S; m += stride) {
         double th = deg2rad(sf.phase0_deg + sigma * ((double)m * sf.rot_step_deg));
         double sn, cs;
         sincos(th, &sn, &cs);
