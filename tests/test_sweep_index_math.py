@@ -246,3 +246,30 @@ def test_tilted_phase_form_revolution_range_covers_the_tile():
         hit += over.size
         assert over.size == 0 or (over.min() >= k0 and over.max() <= k1), (S, float(fsx), float(fsy), over, k0, k1)
     assert hit > 1000
+
+
+def test_plan_threads_take_each_point_and_phase_once():
+    """Planning: thread t of a grid of `stride` threads takes the edge points
+    t, t + stride, ... below NE, and the phase-table entries from
+    t - (NE mod stride) (plus stride where that is negative) in steps of
+    stride below S. Every point and every phase entry is built exactly once,
+    and a grid of at least NE + S threads gives each thread one item."""
+    rng = np.random.default_rng(5)
+    cases = [(800, 3600, 4416), (800, 3600, 64), (2, 5, 7), (1000, 300, 640), (3, 3, 64), (1, 1, 1)]
+    cases += [(int(rng.integers(1, 3000)), int(rng.integers(1, 8000)), int(rng.integers(1, 9000))) for _ in range(300)]
+    for NE, S, stride in cases:
+        points = np.zeros(NE, np.int64)
+        phases = np.zeros(S, np.int64)
+        per_thread = np.zeros(stride, np.int64)
+        for first in range(stride):
+            idx = np.arange(first, NE, stride)
+            points[idx] += 1
+            m0 = first - NE % stride
+            if m0 < 0:
+                m0 += stride
+            ms = np.arange(m0, S, stride)
+            phases[ms] += 1
+            per_thread[first] = idx.size + ms.size
+        assert (points == 1).all() and (phases == 1).all(), (NE, S, stride)
+        if stride >= NE + S:
+            assert per_thread.max() <= 1, (NE, S, stride)
